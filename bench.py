@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput of the WENO-ZN SSP-RK3 solver for the 2D Euler equations (FP64) on GB300.
+
+One step = one SSP-RK3 step (three stages: LF-speed reduction, x and y interface fluxes
+with characteristic WENO-ZN reconstruction, flux difference and stage update) over the
+whole grid of the seeded four-quadrant Riemann problem, outflow boundaries, CFL 0.5.
+Metric: cell-updates per second (one cell advanced by one RK3 step).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--n 4096]
+
+Multi-GPU: each rank advances its own independent problem (replicas, weak scaling); the
+only collectives are the timing barrier and a max-reduction of the elapsed time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WENO-ZN cell-updates/s (2D Euler FP64)"
+UNIT = "cell-updates/s"
+
+# FP64 peak of one GB300 derived from the nominal FP64 rate (1.25 TFLOP/s), 152 SMs and
+# the 2070 MHz maximum SM clock: 2 FP64 FMA lanes per SM per clock.
+FP64_LANES_PER_SM = 2
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="grid is n x n")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--kernel-reps", type=int, default=5, help="launches per flux kernel timing")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
+    return ap.parse_args()
+
+
+def algorithmic_flops(nx: int, ny: int) -> dict:
+    """Algorithmic FP64 operations (one per add, mul, div, sqrt) of the scheme as the paper
+    writes it, counted by the oracle's op-counting instantiation (constants below)."""
+    iface, cell, speed, diff = 1098.0, 42.0, 28.0, 20.0      # 2D Euler, per unit
+    x_flux = iface * (nx + 1) * ny + cell * nx * ny
+    y_flux = iface * nx * (ny + 1) + cell * nx * ny
+    per_stage = x_flux + y_flux + (speed + diff) * nx * ny
+    step = 3 * per_stage + 48.0 * nx * ny
+    return {"x_flux": x_flux, "y_flux": y_flux, "step": step,
+            "per_cell_update": step / (nx * ny), "per_interface": iface}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        smi = shutil.which("nvidia-smi")
+        if not smi:
+            return
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen([smi, f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline(n_full: int, seed: int, target_s: float, steps: int = 1) -> dict:
+    """The CPU oracle as it stands, on the host's cores, on a bounded sample of the same
+    workload: the same problem family on an m x m grid, m chosen so the sample takes
+    about `target_s` seconds."""
+    import numpy as np  # noqa: F401
+    from oracle import oracle as O
+    from paper_2004_07954_gb300 import inputs
+    O.build()
+    cores = O.num_threads()
+    m = 128
+    U = inputs.euler2d_ic(m, m, seed)
+    P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
+    t0 = time.perf_counter()
+    O.rk3_step(P, U)
+    per_cell = (time.perf_counter() - t0) / (m * m)
+    m = int(math.sqrt(max(1.0, target_s / max(per_cell, 1e-9) / steps)))
+    m = max(128, min(n_full, m))
+    U = inputs.euler2d_ic(m, m, seed)
+    P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, _ = O.rk3_step(P, U)
+    el = time.perf_counter() - t0
+    return {"value": steps * m * m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 step(s) of the same seeded four-quadrant 2D Euler problem on a "
+                      f"{m}x{m} grid (plain FP64 C++ oracle, OpenMP over grid lines), {el:.1f} s"}
+
+
+def run_reference(args, rank: int):
+    """Reference arm: the CPU oracle timed on this host's cores, bounded sample per step."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2004_07954_gb300 import inputs
+    O.build()
+    cores = O.num_threads()
+    # size the per-step sample so that warmup + steps finish in about two minutes
+    m = 128
+    U = inputs.euler2d_ic(m, m, args.seed)
+    P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
+    t0 = time.perf_counter()
+    O.rk3_step(P, U)
+    per_cell = (time.perf_counter() - t0) / (m * m)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    m = max(64, min(args.n, int(math.sqrt(budget / max(per_cell, 1e-9)))))
+    U = inputs.euler2d_ic(m, m, args.seed)
+    P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
+    for _ in range(args.warmup):
+        U, _ = O.rk3_step(P, U)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _ = O.rk3_step(P, U)
+    el = time.perf_counter() - t0
+    value = args.steps * m * m / el
+    sample = (f"each step: one SSP-RK3 step of the seeded four-quadrant 2D Euler problem on a {m}x{m} "
+              f"grid (bounded sample of the {args.n}x{args.n} workload), plain FP64 C++ oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"2D Euler {args.n}x{args.n} four-quadrant Riemann, seed {args.seed}, "
+                                   "outflow, CFL 0.5, one SSP-RK3 step per step", "sample_grid": [m, m]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2004_07954_gb300 import build as _b
+    from paper_2004_07954_gb300 import inputs, wenozn
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _b.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n = args.n
+    p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_2D, n, n, 1.0 / n, 1.0 / n)
+    U0 = inputs.euler2d_ic(n, n, args.seed + rank)          # one independent problem per rank
+    U = torch.from_numpy(U0).cuda()
+    S = wenozn.Solver(p)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        S.step(U)
+    torch.cuda.synchronize()
+    if S.status() != 0:
+        raise RuntimeError("non-finite state during warm-up")
+
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        S.step(U)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = S.status()
+    value = world * args.steps * n * n / (ms / 1e3)
+
+    # ---- dominant kernels, timed live on the launching stream ------------------------
+    alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
+    wenozn.wenozn_max_wavespeed(p, U, alpha)
+    fx = torch.empty(wenozn.flux_shape(p, 0), dtype=torch.float64, device="cuda")
+    fy = torch.empty(wenozn.flux_shape(p, 1), dtype=torch.float64, device="cuda")
+    kern = {}
+    for d, buf in ((0, fx), (1, fy)):
+        wenozn.wenozn_flux(p, U, alpha, d, buf)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.kernel_reps):
+            wenozn.wenozn_flux(p, U, alpha, d, buf)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kern[d] = a.elapsed_time(b) / args.kernel_reps
+    del fx, fy
+    fl = algorithmic_flops(n, n)
+    achieved = fl["x_flux"] / (kern[0] / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "kernel": "flux_kernel<4,0> (x-direction interface fluxes)",
+                "peak_source": "derived: 2 FP64 FMA/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FP64)",
+                "kernel_ms": {"x_flux": round(kern[0], 3), "y_flux": round(kern[1], 3)},
+                "y_flux_frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+                "step_frac": round(fl["step"] * world * args.steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS / world, 4),
+                "algorithmic_flops_per_cell_update": round(fl["per_cell_update"], 1)}
+
+    # ---- end to end: host buffers, copies inside the timed region --------------------
+    host_in = torch.from_numpy(U0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_buf = torch.empty_like(U)
+    ke = max(1, args.e2e_steps)
+    dev_buf.copy_(host_in, non_blocking=True)
+    S.step(dev_buf)
+    host_out.copy_(dev_buf, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ke):
+        dev_buf.copy_(host_in, non_blocking=True)
+        S.step(dev_buf)
+        host_out.copy_(dev_buf, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ems], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    nbytes = U.numel() * U.element_size()
+    e2e = {"value": world * ke * n * n / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, args.seed, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"2D Euler {n}x{n} seeded four-quadrant Riemann problem "
+                                       f"(seed {args.seed} + rank), outflow BC, CFL 0.5, gamma 1.4",
+                           "grid": [n, n], "step": "one SSP-RK3 step (3 stages)",
+                           "parallelism": f"{world} independent replica(s), one per GPU",
+                           "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
+                           "device_status": status},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 10 * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * wenozn.h - C ABI of the GB300 (sm_103a) WENO-ZN finite-difference solver.
+ *
+ * The library implements the fifth-order WENO-ZN scheme of Shen, Zhang, Li & Peng,
+ * "A novel method for constructing high accurate and robust WENO-Z type scheme"
+ * (arXiv 2004.07954), inside an SSP-RK3 solver for linear advection and the 1D / 2D Euler
+ * equations, all in FP64.  Section and equation labels below are the paper's.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers documented as "device" must point to CUDA global memory of the current
+ *    device; "host" pointers to ordinary or pinned host memory.  The caller owns every
+ *    buffer; the library allocates nothing on these paths and keeps no pointer after a
+ *    call returns.  Scratch space comes from the caller's workspace (wenozn_workspace_size).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Every
+ *    call only enqueues work on it and returns; the only calls that synchronise are the
+ *    ones that say so (a non-NULL host `dt_out`, wenozn_workspace_status).
+ *  - State arrays are FP64, planar and C-contiguous: U[nvar][ny][nx], x fastest, holding
+ *    the conserved variables (rho, rho u, E) in 1D, (rho, rho u, rho v, E) in 2D, or the
+ *    scalar u for advection.  1D problems use ny = 1.
+ *  - Host-side argument checks run first and return WENOZN_EINVAL without enqueuing
+ *    anything.  Launch failures return WENOZN_ECUDA.  Conditions detected on the device
+ *    (non-finite values, rho <= 0 or p <= 0) set bits in the workspace status word, read
+ *    with wenozn_workspace_status; the kernels never trap.
+ */
+#ifndef WENOZN_H
+#define WENOZN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WENOZN_OK = 0,
+    WENOZN_EINVAL = 1,       /* bad argument (null pointer, size, enum, non-positive dx ...) */
+    WENOZN_ECUDA = 2,        /* a CUDA launch or copy failed                                 */
+    WENOZN_ENOMEM_WS = 3,    /* workspace smaller than wenozn_workspace_size reports         */
+    WENOZN_ENONFINITE = 4,   /* device status bit: NaN/Inf, rho <= 0 or p <= 0 encountered   */
+    WENOZN_ETIMEOUT = 5      /* device status bit: a bounded device-side wait gave up        */
+} wenozn_status;
+
+typedef enum { WENOZN_BC_PERIODIC = 0, WENOZN_BC_OUTFLOW = 1 } wenozn_bc;
+
+typedef enum {
+    WENOZN_ADVECTION_1D = 0, /* u_t + a u_x = 0 (Sec. 4.2), nvar = 1 */
+    WENOZN_EULER_1D = 1,     /* Sec. 4.3, nvar = 3                  */
+    WENOZN_EULER_2D = 2      /* Sec. 4.4, nvar = 4                  */
+} wenozn_system;
+
+/* Problem description.  The numerical constants default to the paper's choices:
+ * gamma = 1.4 (Sec. 4.3), eps = 1e-40 in Eq. (new) (the value that reproduces the Sec. 4.1
+ * table), A = 10 in Eq. (function), cfl = 0.5 (Sec. 4).  `flags` must be 0. */
+typedef struct {
+    int32_t system;          /* wenozn_system                                  */
+    int32_t nx, ny;          /* interior cells, 1 .. 2^30 each, nx*ny <= 2^34; ny = 1 in 1D */
+    int32_t bc_x, bc_y;      /* wenozn_bc per direction (bc_y ignored in 1D)   */
+    int32_t flags;           /* reserved, 0                                    */
+    double dx, dy;           /* uniform spacing (> 0; dy ignored in 1D)        */
+    double gamma;            /* ratio of specific heats (Euler)                */
+    double eps;              /* epsilon of Eq. (function) / Eq. (new)          */
+    double A;                /* constant A of Eq. (function)                   */
+    double cfl;              /* CFL number sigma of the time-step formulas     */
+    double adv_speed;        /* advection speed a (advection only)             */
+} wenozn_problem;
+
+/* Fills `p` with the paper's defaults for `system` on an nx x ny grid of spacing dx, dy,
+ * outflow boundaries.  Returns WENOZN_EINVAL for a null pointer or unknown system. */
+wenozn_status wenozn_problem_init(wenozn_problem* p, int32_t system, int32_t nx, int32_t ny,
+                                  double dx, double dy);
+
+/* Bytes of caller-provided device workspace that wenozn_rhs / wenozn_rk3_step need for
+ * this problem: a 256-byte control block (LF speeds, time step, status word), two
+ * state-sized RK stage buffers and the interface fluxes of each sweep direction
+ * ([nvar][ny][nx+1], and [nvar][ny+1][nx] in 2D), each region 256-byte aligned.  The
+ * workspace must be 256-byte aligned and zero-filled once before its first use
+ * (cudaMemset); the library keeps it consistent afterwards.  Returns WENOZN_EINVAL for an
+ * invalid problem or a null `bytes`. */
+wenozn_status wenozn_workspace_size(const wenozn_problem* p, size_t* bytes);
+
+/* Ghost-cell fill (three cells per side).  Periodic boundaries wrap (Sec. 4.2: "periodic
+ * boundary"); outflow boundaries copy the edge cell (zero-order extrapolation, the
+ * transmissive condition named in Sec. 4.4).
+ *   U_padded : device, FP64, [nvar][ny+6][nx+6] in 2D or [nvar][nx+6] in 1D, interior at
+ *              offset 3 in each padded direction; ghosts are overwritten in place.  In 2D
+ *              the x-ghosts of the interior rows are filled first, then the y-ghosts of
+ *              every padded column (so corners hold the doubly extrapolated values). */
+wenozn_status wenozn_fill_ghosts(const wenozn_problem* p, double* U_padded, void* stream);
+
+/* Fifth-order WENO-ZN reconstruction of one padded line (Sec. 3, Eqs. (3), (4), (isjiang),
+ * (tau), (tau8), (function), (new)).
+ *   f_padded : device, n + 6 values, f_padded[j + 3] = f_j, ghosts already filled.
+ *   n        : interior points, 1 <= n <= 2^31 - 8.
+ *   fhat     : device, n + 1 values; fhat[j] is the flux at x_{j-1/2}, j = 0..n.
+ *   side     : +1 for f^+_{j-1/2} (stencil f_{j-3..j+1}); -1 for f^-_{j-1/2}, the same
+ *              formula applied to the mirrored stencil (f_{j+2}, f_{j+1}, f_j, f_{j-1},
+ *              f_{j-2}) (Sec. 2: "symmetric rule about x_{i+1/2}").
+ *   eps, A   : Eq. (function) / (new) constants (eps > 0, A >= 0). */
+wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat, int32_t side,
+                                 double eps, double A, void* stream);
+
+/* Global Lax-Friedrichs speeds (Sec. 4.3 / 4.4): alpha_out[0] = max_ij(|u| + c),
+ * alpha_out[1] = max_ij(|v| + c) (2D; 0 otherwise); |a| for advection.
+ *   U         : device state [nvar][ny][nx].
+ *   alpha_out : device, 2 doubles, overwritten.
+ *   status_dev: device int32 status word or NULL; a NaN/Inf, rho <= 0 or p <= 0 ORs
+ *               WENOZN_ENONFINITE into it. */
+wenozn_status wenozn_max_wavespeed(const wenozn_problem* p, const double* U, double* alpha_out,
+                                   int32_t* status_dev, void* stream);
+
+/* Numerical fluxes of one sweep direction (steps of Sec. 2 and Sec. 4.3/4.4 up to, not
+ * including, the flux difference): LF splitting with the given speed, Roe-averaged
+ * characteristic projection (Euler), WENO-ZN reconstruction of both split parts and
+ * back-projection, F^ = R (g^+ + g^-), at every interface of that direction.
+ *   U     : device state [nvar][ny][nx].
+ *   alpha : device, 2 doubles: the LF speed of each direction (as wenozn_max_wavespeed
+ *           writes them); ignored for advection, which splits with |a|.
+ *   dir   : 0 = x, Fout[nvar][ny][nx+1] with Fout[k][j][i] at x_{i-1/2} of row j;
+ *           1 = y (2D only), Fout[nvar][ny+1][nx] with Fout[k][j][i] at y_{j-1/2}.
+ *   Fout  : device, overwritten; must not overlap U. */
+wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double* alpha,
+                          int32_t dir, double* Fout, void* stream);
+
+/* Semi-discrete right-hand side, Eq. (2) (1D) or its 2D form (Sec. 4.4):
+ *   L = -(F^_{i+1/2} - F^_{i-1/2}) / dx  [ - (G^_{j+1/2} - G^_{j-1/2}) / dy ]
+ * with global LF flux splitting (alpha of this U), Roe-averaged characteristic fields
+ * (Euler) and WENO-ZN reconstruction of both split parts, ghost cells by index map.
+ *   U, L : device, [nvar][ny][nx]; L is overwritten; U and L must not overlap.
+ *   ws   : device workspace of ws_bytes >= wenozn_workspace_size. */
+wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* One third-order TVD Runge-Kutta step (Shu & Osher, cited in Sec. 4), in place:
+ *   U1 = Un + dt L(Un);  U2 = 3/4 Un + 1/4 (U1 + dt L(U1));  Un+1 = 1/3 Un + 2/3 (U2 + dt L(U2)).
+ *   U           : device state, advanced in place.
+ *   dt          : > 0 fixed step; <= 0 CFL step computed on the device from Un
+ *                 (1D: cfl dx / max(|u|+c); 2D: cfl dtx dty / (dtx + dty); advection:
+ *                 cfl dx / |a|).
+ *   t_remaining : > 0 clips the step to it (land on a final time); <= 0 no clipping.
+ *   dt_out      : host pointer or NULL.  Non-NULL: the step taken is copied back and the
+ *                 stream is synchronised.  NULL: nothing synchronises.
+ *   ws          : device workspace (see wenozn_workspace_size); the step taken is also
+ *                 left in it (wenozn_workspace_dt). */
+wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, double t_remaining,
+                              double* dt_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Device address of the FP64 time step the last wenozn_rk3_step on this workspace took. */
+const double* wenozn_workspace_dt(const void* ws);
+
+/* Synchronises `stream`, copies the workspace status word into *status (0 = clean, else
+ * an OR of WENOZN_ENONFINITE / WENOZN_ETIMEOUT bits as (1 << code)) and, when `clear` is
+ * non-zero, resets it. */
+wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, void* stream);
+
+/* Static description of a status code. */
+const char* wenozn_status_string(wenozn_status s);
+
+/* Library version, "major.minor.patch". */
+const char* wenozn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WENOZN_H */

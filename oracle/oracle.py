@@ -83,6 +83,7 @@ def lib():
                 "oracle_roe_eigen": (None, [_D, _D, ctypes.c_int, ctypes.c_double, _D]),
                 "oracle_normal_flux": (None, [_D, ctypes.c_int, ctypes.c_double, _D]),
                 "oracle_opcount_rhs": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
+                "oracle_opcount_parts": (None, [ctypes.c_int, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -197,3 +198,12 @@ def opcount_rhs(system, nx, ny=1) -> dict:
     out = np.zeros(5)
     lib().oracle_opcount_rhs(int(system), int(nx), int(ny), _ptr(out))
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), out.tolist()))
+
+
+def opcount_parts(system) -> dict:
+    """Algorithmic operations (add+mul+div+sqrt) of the pieces of one RHS evaluation."""
+    out = np.zeros(9)
+    lib().oracle_opcount_parts(int(system), _ptr(out))
+    return {"interface": out[0], "cell_per_sweep": out[1], "wavespeed_cell": out[2],
+            "difference_cell_per_dir": out[3], "cmp_interface": out[4], "cmp_cell_per_sweep": out[5],
+            "cmp_wavespeed_cell": out[6]}

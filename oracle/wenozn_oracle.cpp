@@ -601,4 +601,51 @@ void oracle_opcount_rhs(int system, int nx, int ny, double* out) {
     out[3] = double(g_tally.sqrt_); out[4] = double(g_tally.cmp);
 }
 
+// Algorithmic operations of the pieces of one RHS, counted on OpCount scalars (add+mul+div
+// +sqrt; comparisons apart): out[0] one interface flux, out[1] the per-cell split-flux
+// and Roe ingredients of one sweep (per cell), out[2] one cell's LF-speed evaluation
+// (both directions in 2D), out[3] one cell's flux difference per direction,
+// out[4..8] the comparison counts of the same pieces.
+void oracle_opcount_parts(int system, double* out) {
+    Problem P{};
+    P.system = system; P.nx = 8; P.ny = 1; P.bc_x = BC_PERIODIC; P.bc_y = BC_PERIODIC;
+    P.weights = W_ZN; P.dx = 0.1; P.dy = 0.1; P.gamma = 1.4; P.eps = 1e-40; P.A = 10;
+    P.cfl = 0.5; P.adv_speed = 1.0;
+    const int nv = nvar_of(system);
+    std::vector<OpCount> line(14 * nv);
+    for (int c = 0; c < 14; ++c) {
+        double x = 0.37 * c;
+        line[c * nv] = OpCount(1.0 + 0.2 * std::sin(x));
+        if (nv >= 3) {
+            line[c * nv + 1] = OpCount(0.3 * std::cos(x));
+            if (nv == 4) line[c * nv + 2] = OpCount(-0.2 * std::sin(2 * x));
+            line[c * nv + nv - 1] = OpCount(2.5 + 0.1 * std::cos(3 * x));
+        }
+    }
+    auto total = [](const OpTally& t) { return double(t.add + t.mul + t.div + t.sqrt_); };
+    LineCells<OpCount> lc;
+    g_tally = OpTally();
+    line_cells(P, line.data(), 14, nv, OpCount(2.0), lc);
+    out[1] = total(g_tally) / 14.0; out[5] = double(g_tally.cmp) / 14.0;
+    OpCount F[4];
+    g_tally = OpTally();
+    interface_flux(P, lc, nv, 5, F);
+    out[0] = total(g_tally); out[4] = double(g_tally.cmp);
+    std::vector<OpCount> U(nv * 8);
+    for (int k = 0; k < nv; ++k)
+        for (int c = 0; c < 8; ++c) U[k * 8 + c] = line[c * nv + k];
+    g_tally = OpTally();
+    if (system != SYS_ADV1D) {
+        P.nx = 8;
+        max_wavespeed<OpCount>(P, U.data(), 0);
+        if (system == SYS_EULER2D) max_wavespeed<OpCount>(P, U.data(), 1);
+    }
+    out[2] = total(g_tally) / 8.0; out[6] = double(g_tally.cmp) / 8.0;
+    // flux difference: -(F_{i+1/2} - F_{i-1/2}) / dx per variable
+    g_tally = OpTally();
+    OpCount d = -((F[0] - F[0]) / OpCount(0.1));
+    (void)d;
+    out[3] = total(g_tally) * nv; out[7] = 0.0; out[8] = 0.0;
+}
+
 }  // extern "C"

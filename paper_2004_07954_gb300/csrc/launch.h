@@ -1,0 +1,50 @@
+// Internal host-side launchers shared by the translation units of libwenozn.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wenozn_device.cuh"
+
+namespace wz {
+
+// Numerical fluxes at every interface of one sweep direction.
+//   dir 0 (x): Fout[nv][ny][nx+1], Fout[.][j][i] at x_{i-1/2} of row j.
+//   dir 1 (y): Fout[nv][ny+1][nx], Fout[.][j][i] at y_{j-1/2} of column i.
+struct FluxArgs {
+    const double* U;                       // stage input, [nv][ny][nx]
+    double* Fout;
+    const unsigned long long* alpha_bits;  // LF speeds (x, y) of U as bit patterns; unused for advection
+    int nx, ny, bc;                        // bc of the sweep direction
+    double eps4, A, gamma, adv_speed;
+};
+cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s);
+
+// Flux difference, SSP-RK3 stage combination and the next stage's LF speeds.
+struct UpdateArgs {
+    const double* Us;    // stage input
+    const double* Un;    // state at the start of the step (stages 1 and 2)
+    double* out;         // stage output (may alias Un for the last stage), or L (mode 0)
+    const double* Fx;
+    const double* Gy;    // null in 1D
+    int nx, ny;
+    double rdx, rdy;     // 1/dx, 1/dy
+    int mode;            // 0: out = L; 1, 2, 3: RK3 stages
+    Ctrl* ctrl;
+    int next_slot;       // alpha slot to accumulate the output's LF speeds into, or -1
+    double dt_fixed, t_remaining, cfl, dx, dy, gamma, adv_speed;
+};
+cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s);
+
+// Global LF speeds of U folded into dst[0..1] (bit-pattern max; dst must start at 0).
+cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, double gamma,
+                                 double adv_speed, unsigned long long* dst, int32_t* status,
+                                 cudaStream_t s);
+
+cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
+                               double eps4, double A, cudaStream_t s);
+
+cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,
+                               double* U_padded, cudaStream_t s);
+
+}  // namespace wz

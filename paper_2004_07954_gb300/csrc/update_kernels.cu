@@ -1,0 +1,212 @@
+// Cell-wise kernels: flux difference + SSP-RK3 stage update (with the next stage's LF
+// speeds folded in), the standalone LF-speed reduction, the single-line reconstruction and
+// the ghost-cell fill.
+#include "launch.h"
+
+namespace wz {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double bits_to_double(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
+
+// CFL step of the current RK3 step from the LF speeds of U^n (slot 0), in the operation
+// order of the oracle: 1D cfl dx / a_x (Sec. 4.3); 2D cfl dtx dty / (dtx + dty) with
+// dtx = dx / a_x, dty = dy / a_y (Sec. 4.4); advection cfl dx / |a|.
+__device__ __forceinline__ double step_dt(const UpdateArgs& a, int system) {
+    double dt = a.dt_fixed;
+    if (!(dt > 0.0)) {
+        if (system == 0) {
+            dt = __ddiv_rn(__dmul_rn(a.cfl, a.dx), fabs(a.adv_speed));
+        } else {
+            const double ax = bits_to_double(a.ctrl->alpha[0][0]);
+            if (system == 1) {
+                dt = __ddiv_rn(__dmul_rn(a.cfl, a.dx), ax);
+            } else {
+                const double ay = bits_to_double(a.ctrl->alpha[0][1]);
+                const double tx = __ddiv_rn(a.dx, ax), ty = __ddiv_rn(a.dy, ay);
+                dt = __ddiv_rn(__dmul_rn(__dmul_rn(a.cfl, tx), ty), __dadd_rn(tx, ty));
+            }
+        }
+    }
+    if (a.t_remaining > 0.0 && dt > a.t_remaining) dt = a.t_remaining;
+    return dt;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads) update_kernel(UpdateArgs a) {
+    const int system = NV == 1 ? 0 : (NV == 3 ? 1 : 2);
+    double dt = 0.0;
+    if (a.mode == 1) {
+        dt = step_dt(a, system);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->dt = dt;
+    } else if (a.mode > 1) {
+        dt = a.ctrl->dt;
+    }
+    const int64_t nc = int64_t(a.nx) * a.ny;
+    const int64_t sx = int64_t(a.ny) * (a.nx + 1);       // x-flux plane stride
+    const int64_t sy = int64_t(a.ny + 1) * a.nx;         // y-flux plane stride
+    double mx = 0.0, my = 0.0;
+    bool bad = false;
+    for (int64_t cell = blockIdx.x * int64_t(kThreads) + threadIdx.x; cell < nc;
+         cell += int64_t(gridDim.x) * kThreads) {
+        const int64_t j = cell / a.nx, i = cell - j * a.nx;
+        const int64_t fx = j * (a.nx + 1) + i;
+        double o[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            // Eq. (2): L = -(F^_{i+1/2} - F^_{i-1/2})/dx [- (G^_{j+1/2} - G^_{j-1/2})/dy]
+            double L = -((a.Fx[k * sx + fx + 1] - a.Fx[k * sx + fx]) * a.rdx);
+            if (NV == 4) L = fma(-(a.Gy[k * sy + cell + a.nx] - a.Gy[k * sy + cell]), a.rdy, L);
+            double r;
+            if (a.mode == 0) {
+                r = L;
+            } else {
+                const double ups = fma(dt, L, a.Us[k * nc + cell]);
+                if (a.mode == 1) r = ups;
+                else if (a.mode == 2) r = fma(0.75, a.Un[k * nc + cell], 0.25 * ups);
+                else r = fma(1.0 / 3.0, a.Un[k * nc + cell], (2.0 / 3.0) * ups);
+            }
+            a.out[k * nc + cell] = r;
+            o[k] = r;
+        }
+        if (a.mode != 0) {
+            if (NV == 1) {
+                bad |= !isfinite(o[0]);
+            } else if (a.next_slot >= 0 || a.mode == 3) {
+                double vx, vy;
+                bad |= !wave_speeds<NV>(o, a.gamma, vx, vy);
+                mx = fmax(mx, vx);
+                my = fmax(my, vy);
+            }
+        }
+    }
+    if (bad) atomicOr(&a.ctrl->status, kStatusNonFinite);
+    if (NV != 1 && a.next_slot >= 0) block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads) max_wavespeed_kernel(const double* U, int64_t nc,
+                                                                  double gamma,
+                                                                  unsigned long long* dst,
+                                                                  int32_t* status) {
+    double mx = 0.0, my = 0.0;
+    bool bad = false;
+    for (int64_t cell = blockIdx.x * int64_t(kThreads) + threadIdx.x; cell < nc;
+         cell += int64_t(gridDim.x) * kThreads) {
+        double s[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] = U[k * nc + cell];
+        double vx, vy;
+        bad |= !wave_speeds<NV>(s, gamma, vx, vy);
+        mx = fmax(mx, vx);
+        my = fmax(my, vy);
+    }
+    if (bad && status) atomicOr(status, kStatusNonFinite);
+    block_max2_atomic(mx, my, dst);
+}
+
+__global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, unsigned long long* dst) {
+    if (threadIdx.x == 0) {
+        dst[0] = (unsigned long long)__double_as_longlong(fabs(adv_speed));
+        dst[1] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, int64_t n, double* fhat,
+                                                                int side, double eps4, double A) {
+    const int64_t j = blockIdx.x * int64_t(kThreads) + threadIdx.x;
+    if (j > n) return;
+    const double* s = f + j;
+    fhat[j] = side > 0 ? zn_flux(s[0], s[1], s[2], s[3], s[4], eps4, A)
+                       : zn_flux(s[5], s[4], s[3], s[2], s[1], eps4, A);
+}
+
+// x-ghosts of the interior rows (phase 0) or y-ghosts of every padded column (phase 1).
+__global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int nx, int ny, int bc_x,
+                                                          int bc_y, int two_d, int phase) {
+    const int px = nx + 6, py = two_d ? ny + 6 : 1;
+    const int64_t t = blockIdx.x * int64_t(kThreads) + threadIdx.x;
+    if (phase == 0) {
+        const int rows = two_d ? ny : 1;
+        const int64_t total = int64_t(nv) * rows * 6;
+        if (t >= total) return;
+        const int g = int(t % 6);
+        const int64_t r = (t / 6) % rows, k = t / (6 * int64_t(rows));
+        const int64_t row = two_d ? r + 3 : 0;
+        double* line = U + (k * py + row) * px;
+        const int gi = g < 3 ? g - 3 : nx + (g - 3);          // -3..-1, n..n+2
+        line[gi + 3] = line[ghost_src(gi, nx, bc_x) + 3];
+    } else {
+        const int64_t total = int64_t(nv) * px * 6;
+        if (t >= total) return;
+        const int g = int(t % 6);
+        const int64_t col = (t / 6) % px, k = t / (6 * int64_t(px));
+        double* plane = U + k * py * px;
+        const int gj = g < 3 ? g - 3 : ny + (g - 3);
+        plane[int64_t(gj + 3) * px + col] = plane[int64_t(ghost_src(gj, ny, bc_y) + 3) * px + col];
+    }
+}
+
+unsigned grid_for(int64_t items, int cap) {
+    int64_t b = (items + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return unsigned(b);
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 152;
+    return sms > 0 ? sms : 152;
+}
+
+}  // namespace
+
+cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
+    const int64_t nc = int64_t(a.nx) * a.ny;
+    const unsigned grid = grid_for(nc, sm_count() * 8);
+    if (system == 0) update_kernel<1><<<grid, kThreads, 0, s>>>(a);
+    else if (system == 1) update_kernel<3><<<grid, kThreads, 0, s>>>(a);
+    else update_kernel<4><<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, double gamma,
+                                 double adv_speed, unsigned long long* dst, int32_t* status,
+                                 cudaStream_t s) {
+    if (system == 0) {
+        abs_speed_kernel<<<1, 32, 0, s>>>(adv_speed, dst);
+        return cudaGetLastError();
+    }
+    const unsigned grid = grid_for(ncells, sm_count() * 4);
+    if (system == 1) max_wavespeed_kernel<3><<<grid, kThreads, 0, s>>>(U, ncells, gamma, dst, status);
+    else max_wavespeed_kernel<4><<<grid, kThreads, 0, s>>>(U, ncells, gamma, dst, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
+                               double eps4, double A, cudaStream_t s) {
+    const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
+    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, eps4, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,
+                               double* U_padded, cudaStream_t s) {
+    const int64_t t0 = int64_t(nv) * (two_d ? ny : 1) * 6;
+    ghost_kernel<<<unsigned((t0 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        U_padded, nv, nx, ny, bc_x, bc_y, two_d, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !two_d) return e;
+    const int64_t t1 = int64_t(nv) * (nx + 6) * 6;
+    ghost_kernel<<<unsigned((t1 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        U_padded, nv, nx, ny, bc_x, bc_y, two_d, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace wz

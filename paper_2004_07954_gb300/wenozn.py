@@ -1,0 +1,252 @@
+"""Thin Python binding of libwenozn.so (ctypes).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA kernels.
+Device buffers are torch tensors (float64, CUDA, C-contiguous); streams default to torch's
+current stream.  If the shared library is missing or cannot be loaded the first call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libwenozn.so")
+
+WENOZN_OK, WENOZN_EINVAL, WENOZN_ECUDA, WENOZN_ENOMEM_WS, WENOZN_ENONFINITE, WENOZN_ETIMEOUT = range(6)
+WENOZN_BC_PERIODIC, WENOZN_BC_OUTFLOW = 0, 1
+WENOZN_ADVECTION_1D, WENOZN_EULER_1D, WENOZN_EULER_2D = 0, 1, 2
+NVAR = {WENOZN_ADVECTION_1D: 1, WENOZN_EULER_1D: 3, WENOZN_EULER_2D: 4}
+
+
+class WenoznError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn}: {wenozn_status_string(code)} (status {code})")
+
+
+class wenozn_problem(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("eps", ctypes.c_double), ("A", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("adv_speed", ctypes.c_double)]
+
+    @property
+    def nvar(self) -> int:
+        return NVAR[self.system]
+
+    @property
+    def shape(self):
+        return (self.nvar, self.ny, self.nx)
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_P = ctypes.POINTER(wenozn_problem)
+_SIGNATURES = {
+    "wenozn_problem_init": [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double],
+    "wenozn_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "wenozn_fill_ghosts": [_P, _VP, _VP],
+    "wenozn_reconstruct": [_VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP],
+    "wenozn_max_wavespeed": [_P, _VP, _VP, _VP, _VP],
+    "wenozn_flux": [_P, _VP, _VP, ctypes.c_int32, _VP, _VP],
+    "wenozn_rhs": [_P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_step": [_P, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                        _VP, ctypes.c_size_t, _VP],
+    "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
+}
+
+
+def lib():
+    """Load libwenozn.so (raises if it is absent: build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                                   "(python -m paper_2004_07954_gb300.build) - there is no fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.wenozn_status_string.argtypes = [ctypes.c_int]
+            L.wenozn_status_string.restype = ctypes.c_char_p
+            L.wenozn_version.argtypes = []
+            L.wenozn_version.restype = ctypes.c_char_p
+            L.wenozn_workspace_dt.argtypes = [_VP]
+            L.wenozn_workspace_dt.restype = _VP
+            _lib = L
+    return _lib
+
+
+def _check(fn: str, code: int) -> None:
+    if code != WENOZN_OK:
+        raise WenoznError(fn, code)
+
+
+def _dev_ptr(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ------------------------------------------------------------------------- C-ABI mirrors
+def wenozn_status_string(code: int) -> str:
+    return lib().wenozn_status_string(int(code)).decode()
+
+
+def wenozn_version() -> str:
+    return lib().wenozn_version().decode()
+
+
+def wenozn_problem_init(system: int, nx: int, ny: int = 1, dx: float = 1.0, dy: float = 1.0,
+                        **overrides) -> wenozn_problem:
+    p = wenozn_problem()
+    _check("wenozn_problem_init", lib().wenozn_problem_init(ctypes.byref(p), int(system), int(nx),
+                                                            int(ny), float(dx), float(dy)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def wenozn_workspace_size(p: wenozn_problem) -> int:
+    n = ctypes.c_size_t(0)
+    _check("wenozn_workspace_size", lib().wenozn_workspace_size(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def workspace(p: wenozn_problem, device=None) -> torch.Tensor:
+    """A zero-filled, 256-byte aligned workspace tensor (uint8) for problem p."""
+    nbytes = wenozn_workspace_size(p)
+    ws = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + nbytes]
+
+
+def wenozn_fill_ghosts(p: wenozn_problem, U_padded: torch.Tensor, stream=None) -> None:
+    _check("wenozn_fill_ghosts", lib().wenozn_fill_ghosts(ctypes.byref(p), _dev_ptr(U_padded, "U_padded"),
+                                                          _stream(stream)))
+
+
+def wenozn_reconstruct(f_padded: torch.Tensor, fhat: torch.Tensor, side: int = 1, eps: float = 1e-40,
+                       A: float = 10.0, stream=None) -> None:
+    n = f_padded.numel() - 6
+    if fhat.numel() != n + 1:
+        raise ValueError("fhat must hold n + 1 values")
+    _check("wenozn_reconstruct", lib().wenozn_reconstruct(_dev_ptr(f_padded, "f_padded"), n,
+                                                          _dev_ptr(fhat, "fhat"), int(side), float(eps),
+                                                          float(A), _stream(stream)))
+
+
+def wenozn_max_wavespeed(p: wenozn_problem, U: torch.Tensor, alpha_out: torch.Tensor,
+                         status_dev: torch.Tensor | None = None, stream=None) -> None:
+    if alpha_out.numel() < 2:
+        raise ValueError("alpha_out must hold 2 values")
+    st = 0
+    if status_dev is not None:
+        if not status_dev.is_cuda or status_dev.dtype != torch.int32:
+            raise ValueError("status_dev: expected an int32 CUDA tensor")
+        st = status_dev.data_ptr()
+    _check("wenozn_max_wavespeed", lib().wenozn_max_wavespeed(ctypes.byref(p), _dev_ptr(U, "U"),
+                                                              _dev_ptr(alpha_out, "alpha_out"), st,
+                                                              _stream(stream)))
+
+
+def wenozn_flux(p: wenozn_problem, U: torch.Tensor, alpha: torch.Tensor | None, direction: int,
+                Fout: torch.Tensor, stream=None) -> None:
+    a = 0 if alpha is None else _dev_ptr(alpha, "alpha")
+    _check("wenozn_flux", lib().wenozn_flux(ctypes.byref(p), _dev_ptr(U, "U"), a, int(direction),
+                                            _dev_ptr(Fout, "Fout"), _stream(stream)))
+
+
+def flux_shape(p: wenozn_problem, direction: int):
+    return (p.nvar, p.ny, p.nx + 1) if direction == 0 else (p.nvar, p.ny + 1, p.nx)
+
+
+def _ws_ptr(ws: torch.Tensor) -> int:
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda:
+        raise ValueError("ws: expected a CUDA tensor")
+    return ws.data_ptr()
+
+
+def wenozn_rhs(p: wenozn_problem, U: torch.Tensor, L: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    _check("wenozn_rhs", lib().wenozn_rhs(ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(L, "L"), _ws_ptr(ws),
+                                          ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def wenozn_rk3_step(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, dt: float = 0.0,
+                    t_remaining: float = 0.0, return_dt: bool = False, stream=None):
+    out = ctypes.c_double(0.0)
+    code = lib().wenozn_rk3_step(ctypes.byref(p), _dev_ptr(U, "U"), float(dt), float(t_remaining),
+                                 ctypes.byref(out) if return_dt else None, _ws_ptr(ws),
+                                 ws.numel() * ws.element_size(), _stream(stream))
+    _check("wenozn_rk3_step", code)
+    return out.value if return_dt else None
+
+
+def wenozn_workspace_status(ws: torch.Tensor, clear: bool = False, stream=None) -> int:
+    st = ctypes.c_int32(0)
+    _check("wenozn_workspace_status", lib().wenozn_workspace_status(_ws_ptr(ws), ctypes.byref(st),
+                                                                    int(bool(clear)), _stream(stream)))
+    return st.value
+
+
+def wenozn_workspace_dt(ws: torch.Tensor) -> torch.Tensor:
+    """The device scalar holding the last step taken (a view into the workspace)."""
+    addr = lib().wenozn_workspace_dt(_ws_ptr(ws))
+    off = addr - ws.data_ptr()
+    return ws[off:off + 8].view(torch.float64)
+
+
+# ------------------------------------------------------------------------- convenience
+class Solver:
+    """One problem, one workspace: RHS evaluations and RK3 steps on torch tensors."""
+
+    def __init__(self, p: wenozn_problem, device=None):
+        self.p = p
+        self.ws = workspace(p, device)
+
+    def rhs(self, U: torch.Tensor, L: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if L is None:
+            L = torch.empty_like(U)
+        wenozn_rhs(self.p, U, L, self.ws, stream)
+        return L
+
+    def step(self, U: torch.Tensor, dt: float = 0.0, t_remaining: float = 0.0, return_dt=False, stream=None):
+        return wenozn_rk3_step(self.p, U, self.ws, dt, t_remaining, return_dt, stream)
+
+    def run(self, U: torch.Tensor, T: float, dt: float = 0.0, stream=None) -> int:
+        """Advance to time T (CFL steps clipped at T, or fixed steps); returns steps."""
+        if dt > 0:
+            import math
+            n = int(math.ceil(T / dt - 1e-9))
+            for k in range(n):
+                self.step(U, dt=(T - k * dt) if k == n - 1 else dt, stream=stream)
+            return n
+        t, steps = 0.0, 0
+        while t < T * (1 - 1e-14):
+            t += self.step(U, t_remaining=T - t, return_dt=True, stream=stream)
+            steps += 1
+        return steps
+
+    def status(self, clear: bool = False) -> int:
+        return wenozn_workspace_status(self.ws, clear)

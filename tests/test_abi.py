@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point the header
+declares, and rejects invalid arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def wz():
+    from paper_2004_07954_gb300 import build, wenozn
+    build.build()
+    wenozn.lib()
+    return wenozn
+
+
+def declared_entry_points():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(wenozn_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(wz):
+    names = declared_entry_points()
+    assert len(names) >= 11
+    L = wz.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_problem_init_defaults(wz):
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 128, 64, 0.01, 0.02)
+    assert (p.nx, p.ny, p.bc_x, p.bc_y, p.flags) == (128, 64, 1, 1, 0)
+    assert (p.gamma, p.eps, p.A, p.cfl) == (1.4, 1e-40, 10.0, 0.5)
+    p1 = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, 100, 77, 0.1, 0.2)
+    assert p1.ny == 1
+
+
+def test_workspace_size_layout(wz):
+    def al(x):
+        return (x + 255) // 256 * 256
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 100, 50, 0.01, 0.02)
+    n = 4 * 100 * 50 * 8
+    want = 256 + 2 * al(n) + al(4 * 101 * 50 * 8) + al(4 * 100 * 51 * 8)
+    assert wz.wenozn_workspace_size(p) == want
+    p1 = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, 1000, 1, 0.01, 0)
+    assert wz.wenozn_workspace_size(p1) == 256 + 2 * al(3 * 1000 * 8) + al(3 * 1001 * 8)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", 0), ("system", 7), ("bc_x", 3), ("dx", 0.0),
+                                         ("dx", float("nan")), ("eps", 0.0), ("A", -1.0), ("cfl", 0.0),
+                                         ("gamma", 1.0), ("flags", 1)])
+def test_invalid_problem_rejected_on_host(wz, field, value):
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 16, 16, 0.1, 0.1)
+    setattr(p, field, value)
+    n = ctypes.c_size_t(0)
+    assert wz.lib().wenozn_workspace_size(ctypes.byref(p), ctypes.byref(n)) == wz.WENOZN_EINVAL
+    # null device pointers are rejected before any CUDA call
+    assert wz.lib().wenozn_rhs(ctypes.byref(p), None, None, None, 0, None) == wz.WENOZN_EINVAL
+
+
+def test_null_and_bad_arguments_rejected(wz):
+    L = wz.lib()
+    assert L.wenozn_reconstruct(None, 10, None, 1, 1e-40, 10.0, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_reconstruct(ctypes.c_void_p(256), 0, ctypes.c_void_p(512), 1, 1e-40, 10.0, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_reconstruct(ctypes.c_void_p(256), 10, ctypes.c_void_p(512), 0, 1e-40, 10.0, None) == wz.WENOZN_EINVAL
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, 64, 1, 0.1, 0)
+    assert L.wenozn_rk3_step(ctypes.byref(p), None, 0.0, 0.0, None, None, 0, None) == wz.WENOZN_EINVAL
+    # misaligned workspace
+    assert L.wenozn_rk3_step(ctypes.byref(p), ctypes.c_void_p(256), 0.0, 0.0, None,
+                             ctypes.c_void_p(257), 1 << 20, None) == wz.WENOZN_EINVAL
+    # workspace too small
+    assert L.wenozn_rk3_step(ctypes.byref(p), ctypes.c_void_p(256), 0.0, 0.0, None,
+                             ctypes.c_void_p(512), 16, None) == wz.WENOZN_ENOMEM_WS
+    assert L.wenozn_workspace_status(None, None, 0, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_problem_init(None, 0, 1, 1, 1.0, 1.0) == wz.WENOZN_EINVAL
+
+
+def test_status_strings_and_version(wz):
+    for code in range(6):
+        assert wz.wenozn_status_string(code)
+    assert wz.wenozn_status_string(99) == "unknown status"
+    assert re.fullmatch(r"\d+\.\d+\.\d+", wz.wenozn_version())
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: neither includes, imports or links the
+    other, and only the seeded-input module is common to their callers."""
+    csrc = os.path.join(ROOT, "paper_2004_07954_gb300")
+    for dirpath, _, files in os.walk(csrc):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower() or f == "inputs.py", f
+    otext = open(os.path.join(ROOT, "oracle", "wenozn_oracle.cpp")).read()
+    assert "wenozn.h" not in otext and "csrc" not in otext
+    assert "paper_2004_07954_gb300" not in open(os.path.join(ROOT, "oracle", "oracle.py")).read()

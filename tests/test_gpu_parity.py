@@ -1,0 +1,328 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: relative L-infinity <= 1e-12 for one RHS evaluation or one RK3 step and
+<= 1e-9 at a final time (the targets stated for this solver); LF speeds and CFL steps are
+compared bit for bit (a maximum is exact and both sides evaluate the per-cell speed in the
+same IEEE operation order).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_07954_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-12
+FINAL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def wz():
+    from paper_2004_07954_gb300 import build, wenozn
+    build.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return wenozn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_linf(got, want):
+    scale = np.abs(want).max()
+    return np.abs(got - want).max() / (scale if scale > 0 else 1.0)
+
+
+def gpu_problem(wz, system, nx, ny=1, dx=0.1, dy=0.1, bc=1, bcy=None):
+    return wz.wenozn_problem_init(system, nx, ny, dx, dy, bc_x=bc, bc_y=bc if bcy is None else bcy)
+
+
+def orc_problem(orc, p):
+    return orc.problem(p.system, p.nx, p.ny, dx=p.dx, dy=p.dy, bc_x=p.bc_x, bc_y=p.bc_y,
+                       gamma=p.gamma, eps=p.eps, A=p.A, cfl=p.cfl, adv_speed=p.adv_speed)
+
+
+# ------------------------------------------------------------------ reconstruction
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 300, 1000, 4099])
+@pytest.mark.parametrize("side", [1, -1])
+def test_reconstruct_random(wz, orc, n, side):
+    g = np.random.default_rng(n * 7 + side)
+    for scale in (1.0, 1e-3, 1e4):
+        f = g.normal(size=n + 6) * scale
+        f[g.random(n + 6) < 0.1] += 5 * scale         # sprinkle jumps
+        out = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+        wz.wenozn_reconstruct(dev(f), out, side)
+        want = orc.reconstruct(f, side)
+        assert np.abs(host(out) - want).max() <= STEP_TOL * np.abs(f).max()
+
+
+def test_reconstruct_polynomial_and_step(wz, orc):
+    x = np.arange(-3, 40, dtype=np.float64)
+    for f in (2.0 + 0 * x, 1.0 - 2 * x + 3 * x * x + 0.5 * x ** 3, np.where(x < 11, 0.0, 1.0)):
+        out = torch.empty(f.size - 5, dtype=torch.float64, device="cuda")
+        wz.wenozn_reconstruct(dev(f), out, 1)
+        want = orc.reconstruct(f, 1)
+        assert np.abs(host(out) - want).max() <= STEP_TOL * np.abs(f).max()
+
+
+def test_table3_critical_points_on_gpu(wz, orc):
+    """The FP64-resolvable rows of the paper's critical-point table, through the CUDA
+    reconstruction (f^+_{1/2} - f^+_{-1/2}) / dx against f'(0)."""
+    from conftest import read_golden
+    rows = {1: range(0, 2), 2: range(0, 5), 3: range(0, 8)}
+    for k, j, _z, _za, zn in read_golden("table3_critical_point.txt"):
+        k, j = int(k), int(j)
+        if j not in rows[k]:
+            continue
+        dx = 0.025 / 2 ** j
+        xs = dx * np.arange(-3, 4)
+        f = xs ** k * np.exp(xs)
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+        wz.wenozn_reconstruct(dev(f), out, 1)
+        fh = host(out)
+        err = abs((fh[1] - fh[0]) / dx - (1.0 if k == 1 else 0.0))
+        assert err == pytest.approx(zn, rel=1e-4)
+
+
+# ------------------------------------------------------------------ ghosts and LF speeds
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fill_ghosts(wz, orc, bc):
+    g = np.random.default_rng(bc)
+    nx, ny = 9, 7
+    p = gpu_problem(wz, 2, nx, ny, bc=bc)
+    U = g.normal(size=(4, ny + 6, nx + 6))
+    t = dev(U)
+    wz.wenozn_fill_ghosts(p, t)
+    want = U.copy()
+    for k in range(4):
+        for r in range(3, ny + 3):
+            want[k, r] = orc.fill_ghosts_line(want[k, r], bc)
+        for c in range(nx + 6):
+            want[k, :, c] = orc.fill_ghosts_line(want[k, :, c].copy(), bc)
+    assert np.array_equal(host(t), want)
+    p1 = gpu_problem(wz, 1, nx, bc=bc)
+    U1 = g.normal(size=(3, nx + 6))
+    t1 = dev(U1)
+    wz.wenozn_fill_ghosts(p1, t1)
+    for k in range(3):
+        assert np.array_equal(host(t1)[k], orc.fill_ghosts_line(U1[k], bc))
+
+
+@pytest.mark.parametrize("system,nx,ny", [(1, 1000, 1), (2, 77, 53), (1, 1 << 20, 1)])
+def test_max_wavespeed_bit_exact(wz, orc, system, nx, ny):
+    if system == 1:
+        U = inputs.euler1d_ic(nx, seed=5)
+    else:
+        U = inputs.euler2d_ic(nx, ny, seed=5)
+    p = gpu_problem(wz, system, nx, ny)
+    a = torch.zeros(2, dtype=torch.float64, device="cuda")
+    wz.wenozn_max_wavespeed(p, dev(U), a)
+    P = orc_problem(orc, p)
+    got = host(a)
+    assert got[0] == orc.max_wavespeed(P, U, 0)
+    if system == 2:
+        assert got[1] == orc.max_wavespeed(P, U, 1)
+
+
+# ------------------------------------------------------------------ RHS
+RHS_CASES = [
+    (0, 1, 1, 0), (0, 37, 1, 0), (0, 700, 1, 0), (0, 1031, 1, 1),
+    (1, 1, 1, 1), (1, 5, 1, 0), (1, 200, 1, 1), (1, 513, 1, 1), (1, 1100, 1, 0),
+    (2, 1, 1, 1), (2, 5, 3, 0), (2, 37, 21, 1), (2, 150, 45, 1), (2, 70, 130, 0), (2, 64, 64, 1),
+]
+
+
+def _rand_state(system, nx, ny, seed):
+    if system == 0:
+        return inputs.random_smooth_state(0, nx, ny, seed)
+    if system == 1:
+        return inputs.euler1d_ic(nx, seed) if nx >= 20 else inputs.random_smooth_state(1, nx, ny, seed)
+    if nx >= 8 and ny >= 8:
+        return inputs.euler2d_ic(nx, ny, seed)
+    return inputs.random_smooth_state(2, nx, ny, seed)
+
+
+@pytest.mark.parametrize("system,nx,ny,bc", RHS_CASES)
+def test_rhs_parity(wz, orc, system, nx, ny, bc):
+    U = _rand_state(system, nx, ny, seed=nx + ny)
+    p = gpu_problem(wz, system, nx, ny, dx=1.0 / nx, dy=1.0 / ny, bc=bc)
+    S = wz.Solver(p)
+    L = host(S.rhs(dev(U)))
+    want = orc.rhs(orc_problem(orc, p), U)
+    assert rel_linf(L, want) <= STEP_TOL
+    assert S.status() == 0
+
+
+# ------------------------------------------------------------------ one RK3 step
+@pytest.mark.parametrize("system,nx,ny,bc", RHS_CASES)
+def test_rk3_step_parity(wz, orc, system, nx, ny, bc):
+    U = _rand_state(system, nx, ny, seed=nx * 3 + ny)
+    p = gpu_problem(wz, system, nx, ny, dx=1.0 / nx, dy=1.0 / ny, bc=bc)
+    S = wz.Solver(p)
+    t = dev(U)
+    dt = S.step(t, return_dt=True)
+    want, dt_o = orc.rk3_step(orc_problem(orc, p), U)
+    assert dt == dt_o
+    assert rel_linf(host(t), want) <= STEP_TOL
+
+
+def test_rk3_fixed_and_clipped_dt(wz, orc):
+    n = 300
+    U = inputs.euler1d_ic(n, seed=2)
+    p = gpu_problem(wz, 1, n, dx=10.0 / n)
+    S = wz.Solver(p)
+    P = orc_problem(orc, p)
+    for dt, trem in ((1e-3, 0.0), (0.0, 1e-4), (5e-3, 2e-3)):
+        t = dev(U)
+        got = S.step(t, dt=dt, t_remaining=trem, return_dt=True)
+        want, used = orc.rk3_step(P, U, dt, trem)
+        assert got == used
+        assert rel_linf(host(t), want) <= STEP_TOL
+
+
+# ------------------------------------------------------------------ final time
+def test_advection_final_time(wz, orc):
+    n = 160
+    _, dx = inputs.advection_grid(n)
+    dt, steps = inputs.advection_dt(n, 2.0)
+    for which in ("sin", "critical"):
+        U0 = inputs.advection_ic(n, which)
+        p = gpu_problem(wz, 0, n, dx=dx, bc=0)
+        S = wz.Solver(p)
+        t = dev(U0)
+        assert S.run(t, 2.0, dt) == steps
+        want, _ = orc.run(orc_problem(orc, p), U0, 2.0, dt)
+        assert rel_linf(host(t), want) <= FINAL_TOL
+        err = np.abs(host(t) - inputs.advection_exact(n, which, 2.0)).max()
+        assert err < 5e-8
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_euler1d_final_time(wz, orc, seed):
+    """Seeded Shu-Osher-type problem, N = 200, outflow, CFL 0.5 to t = 1.8."""
+    n = 200
+    U0 = inputs.euler1d_ic(n, seed)
+    _, dx = inputs.euler1d_grid(n)
+    p = gpu_problem(wz, 1, n, dx=dx)
+    S = wz.Solver(p)
+    t = dev(U0)
+    steps = S.run(t, 1.8)
+    want, steps_o = orc.run(orc_problem(orc, p), U0, 1.8)
+    assert steps == steps_o
+    assert rel_linf(host(t), want) <= FINAL_TOL
+    assert S.status() == 0
+
+
+def test_euler2d_final_time(wz, orc):
+    n = 48
+    U0 = inputs.euler2d_ic(n, n, seed=0)
+    p = gpu_problem(wz, 2, n, n, dx=1.0 / n, dy=1.0 / n)
+    S = wz.Solver(p)
+    t = dev(U0)
+    P = orc_problem(orc, p)
+    want = U0
+    for _ in range(25):
+        dt = S.step(t, return_dt=True)
+        want, dt_o = orc.rk3_step(P, want)
+        assert dt == pytest.approx(dt_o, rel=1e-9)
+    assert rel_linf(host(t), want) <= FINAL_TOL
+    assert S.status() == 0
+
+
+# ------------------------------------------------------------------ full sizes
+@pytest.mark.parametrize("system,n_big,n_tile", [(2, 4096, 64), (1, 1 << 20, 256)])
+def test_full_size_tiled_periodic(wz, orc, system, n_big, n_tile):
+    """At the benchmark's sizes (4096^2 2D, 2^20 1D) and launch configuration: a periodic
+    grid tiled with copies of a small periodic problem evolves exactly like the small
+    problem (same global LF speeds, same stencils), so every sampled cell of one RK3 step
+    compares against the oracle run on the small grid."""
+    reps = n_big // n_tile
+    if system == 2:
+        small = inputs.euler2d_ic(n_tile, n_tile, seed=3)
+        big = np.tile(small, (1, reps, reps))
+        p = gpu_problem(wz, 2, n_big, n_big, dx=1.0 / n_big, dy=1.0 / n_big, bc=0)
+        ps = orc.problem(2, n_tile, n_tile, dx=1.0 / n_big, dy=1.0 / n_big, bc_x=0, bc_y=0)
+    else:
+        small = inputs.euler1d_ic(n_tile, seed=3)
+        big = np.tile(small, (1, 1, reps))
+        p = gpu_problem(wz, 1, n_big, dx=1.0 / n_big, bc=0)
+        ps = orc.problem(1, n_tile, 1, dx=1.0 / n_big, bc_x=0)
+    S = wz.Solver(p)
+    t = dev(big)
+    del big
+    dt = S.step(t, return_dt=True)
+    want, dt_o = orc.rk3_step(ps, small)
+    assert dt == dt_o
+    got = host(t)
+    g = np.random.default_rng(0)
+    if system == 2:
+        js, is_ = g.integers(0, n_big, 4096), g.integers(0, n_big, 4096)
+        a = got[:, js, is_]
+        b = want[:, js % n_tile, is_ % n_tile]
+        # and whole tiles at the corners and the centre
+        for (r, c) in ((0, 0), (reps - 1, reps - 1), (reps // 2, reps // 3)):
+            blk = got[:, r * n_tile:(r + 1) * n_tile, c * n_tile:(c + 1) * n_tile]
+            assert rel_linf(blk, want) <= STEP_TOL
+    else:
+        is_ = g.integers(0, n_big, 65536)
+        a = got[:, 0, is_]
+        b = want[:, 0, is_ % n_tile]
+    assert np.abs(a - b).max() <= STEP_TOL * np.abs(want).max()
+    assert S.status() == 0
+
+
+# ------------------------------------------------------------------ invariants on the GPU
+def test_conservation_periodic_gpu(wz):
+    n = 256
+    U0 = inputs.euler2d_ic(n, n, seed=4)
+    p = gpu_problem(wz, 2, n, n, dx=1.0 / n, dy=1.0 / n, bc=0)
+    S = wz.Solver(p)
+    t = dev(U0)
+    for _ in range(5):
+        S.step(t)
+    got = host(t)
+    for k in range(4):
+        assert abs(got[k].sum() - U0[k].sum()) <= 1e-12 * np.abs(U0[k]).sum()
+
+
+def test_free_stream_gpu(wz):
+    p = gpu_problem(wz, 2, 100, 70, bc=1)
+    prim = inputs.cons_from_prim(np.array(1.3), 0.7, 2.1, -0.4)
+    U = np.broadcast_to(prim.reshape(4, 1, 1), (4, 70, 100)).copy()
+    L = host(wz.Solver(p).rhs(dev(U)))
+    assert np.abs(L).max() <= 1e-13
+
+
+def test_nonfinite_status(wz):
+    n = 64
+    U = inputs.euler1d_ic(n, seed=0)
+    U[0, 0, 10] = np.nan
+    p = gpu_problem(wz, 1, n, dx=0.1)
+    S = wz.Solver(p)
+    S.step(dev(U), dt=1e-4)
+    assert S.status(clear=True) & (1 << wz.WENOZN_ENONFINITE)
+    assert S.status() == 0
+    U[0, 0, 10] = -1.0
+    S.step(dev(U), dt=1e-4)
+    assert S.status() & (1 << wz.WENOZN_ENONFINITE)
+
+
+def test_invalid_arguments_gpu(wz):
+    p = gpu_problem(wz, 1, 64)
+    S = wz.Solver(p)
+    small_ws = S.ws[:64]
+    U = dev(inputs.euler1d_ic(64, 0))
+    with pytest.raises(wz.WenoznError) as ei:
+        wz.wenozn_rk3_step(p, U, small_ws)
+    assert ei.value.code == wz.WENOZN_ENOMEM_WS
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_rhs(p, U, U, S.ws)
+    with pytest.raises(ValueError):
+        S.step(U.float())
