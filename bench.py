@@ -37,6 +37,20 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 
+# DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
+# profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
+# kernel sources with this hash prefix; any other source reports null.
+TRAFFIC_CAPTURE = {"sha256_16": "ef47758b859bdf82", "n": 4096, "bytes": 966e6}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("flux_kernels.cu", "wenozn_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_07954_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -262,8 +276,10 @@ def main():
     del fx, fy
     fl = algorithmic_flops(n, n)
     achieved = fl["x_flux"] / (kern[0] / 1e3) / 1e9
+    traffic = TRAFFIC_CAPTURE["bytes"] if (kernel_source_hash() == TRAFFIC_CAPTURE["sha256_16"]
+                                           and n == TRAFFIC_CAPTURE["n"]) else None
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
                 "kernel": "flux_kernel<4,0> (x-direction interface fluxes)",
                 "peak_source": "derived: 2 FP64 FMA/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FP64)",
                 "kernel_ms": {"x_flux": round(kern[0], 3), "y_flux": round(kern[1], 3)},

@@ -201,10 +201,10 @@ def test_advection_final_time(wz, orc):
         want, _ = orc.run(orc_problem(orc, p), U0, 2.0, dt)
         assert rel_linf(host(t), want) <= FINAL_TOL
         err = np.abs(host(t) - inputs.advection_exact(n, which, 2.0)).max()
-        assert err < 5e-8
+        assert err < {"sin": 2e-8, "critical": 5e-7}[which]   # oracle: 9.8e-9, 2.05e-7
 
 
-@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("seed", [0, 2, 3])
 def test_euler1d_final_time(wz, orc, seed):
     """Seeded Shu-Osher-type problem, N = 200, outflow, CFL 0.5 to t = 1.8."""
     n = 200
@@ -217,6 +217,37 @@ def test_euler1d_final_time(wz, orc, seed):
     want, steps_o = orc.run(orc_problem(orc, p), U0, 1.8)
     assert steps == steps_o
     assert rel_linf(host(t), want) <= FINAL_TOL
+    assert S.status() == 0
+
+
+def test_euler1d_final_time_ill_conditioned(wz, orc):
+    """Seed 1 at t = 1.8 is ill-conditioned in FP64: next to the right outflow boundary the
+    fluid is at rest (u at rounding-noise level) and, with eps = 1e-40, the weights of the
+    acoustic characteristic fields there are set by that noise.  A 1-ulp perturbation of
+    the initial data moves the oracle's own result by 1e-8 - 3e-8 relative in cells 185..199,
+    while the rest of the grid agrees to 1e-13.  So: the 1e-9 bar on cells 0..184, and on
+    the boundary cells a distance within 4x the oracle's own 1-ulp response."""
+    n, seed, T = 200, 1, 1.8
+    U0 = inputs.euler1d_ic(n, seed)
+    _, dx = inputs.euler1d_grid(n)
+    p = gpu_problem(wz, 1, n, dx=dx)
+    P = orc_problem(orc, p)
+    S = wz.Solver(p)
+    t = dev(U0)
+    S.run(t, T)
+    got = host(t)
+    want, _ = orc.run(P, U0, T)
+    scale = np.abs(want).max()
+    sens = 0.0
+    for draw in range(3):
+        sign = np.random.default_rng(draw).choice([-1.0, 1.0], size=U0.shape)
+        pert, _ = orc.run(P, U0 * (1 + 2.0 ** -52 * sign), T)
+        sens = max(sens, np.abs(pert - want).max() / scale)
+        assert np.abs(pert - want)[:, :, :185].max() / scale <= FINAL_TOL
+    assert sens > FINAL_TOL                     # the case really is ill-conditioned
+    diff = np.abs(got - want) / scale
+    assert diff[:, :, :185].max() <= FINAL_TOL
+    assert diff.max() <= 4 * sens
     assert S.status() == 0
 
 
