@@ -132,6 +132,21 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
 wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, void* ws,
                          size_t ws_bytes, void* stream);
 
+/* wenozn_rhs without a workspace, for callers that cannot allocate device memory (code
+ * running where cudaMalloc is unavailable or not allowed, e.g. inside a plug-in or callback
+ * that must not allocate, or under a fully reserved memory pool).  The paper has no
+ * counterpart: this is a property of the library, not of the scheme.
+ *   U, L : device, [nvar][ny][nx]; L is overwritten; same result as wenozn_rhs.
+ * Scratch comes from one 8 MiB array in the library's device memory, held on every GPU that
+ * loads the library until the process exits.  Problems that need more (2D Euler beyond about
+ * 131,000 cells, 1D Euler beyond about 349,000, advection beyond about 1,048,000) return
+ * WENOZN_ENOMEM_WS.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture on that device.  All
+ * calls share the array and each clears what must start at zero; calls whose GPU work
+ * overlaps (unordered streams) race and give wrong results.  Device-detected conditions
+ * (non-finite values, rho <= 0, p <= 0) are not reported.  Allocates nothing. */
+wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const double* U, double* L, void* stream);
+
 /* One third-order TVD Runge-Kutta step (Shu & Osher, cited in Sec. 4), in place:
  *   U1 = Un + dt L(Un);  U2 = 3/4 Un + 1/4 (U1 + dt L(U1));  Un+1 = 1/3 Un + 2/3 (U2 + dt L(U2)).
  *   U           : device state, advanced in place.

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "wenozn_max_wavespeed": [_P, _VP, _VP, _VP, _VP],
     "wenozn_flux": [_P, _VP, _VP, ctypes.c_int32, _VP, _VP],
     "wenozn_rhs": [_P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rhs_noalloc": [_P, _VP, _VP, _VP],
     "wenozn_rk3_step": [_P, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                         _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
@@ -191,6 +192,13 @@ def _ws_ptr(ws: torch.Tensor) -> int:
 def wenozn_rhs(p: wenozn_problem, U: torch.Tensor, L: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
     _check("wenozn_rhs", lib().wenozn_rhs(ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(L, "L"), _ws_ptr(ws),
                                           ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def wenozn_rhs_noalloc(p: wenozn_problem, U: torch.Tensor, L: torch.Tensor, stream=None) -> None:
+    """wenozn_rhs with the library's fixed 8 MiB device scratch instead of a workspace, for
+    callers that cannot allocate (see the header for limits and sharing rules)."""
+    _check("wenozn_rhs_noalloc", lib().wenozn_rhs_noalloc(ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(L, "L"),
+                                                          _stream(stream)))
 
 
 def wenozn_rk3_step(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, dt: float = 0.0,
