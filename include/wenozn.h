@@ -169,6 +169,13 @@ const double* wenozn_workspace_dt(const void* ws);
  * non-zero, resets it. */
 wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, void* stream);
 
+/* Diagnostic: evaluates, for n positive normal doubles d, the reciprocal the reconstruction
+ * uses for f^ = num/den (Newton-Raphson refinement of the hardware approximation) into
+ * `fast` and CUDA's IEEE 1/d into `ieee`, so that tests can bound the former's error.
+ *   d, fast, ieee : device, n doubles (1 <= n <= 2^31). */
+wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, double* ieee,
+                                      void* stream);
+
 /* Static description of a status code. */
 const char* wenozn_status_string(wenozn_status s);
 

@@ -65,7 +65,8 @@ cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const unsign
     fa.nx = p.nx;
     fa.ny = p.ny;
     fa.eps4 = 4.0 * p.eps;
-    fa.A = p.A;
+    fa.A4 = 0.25 * p.A;
+    fa.fast_rcp = zn_fast_rcp(p.eps, p.A);
     fa.gamma = p.gamma;
     fa.adv_speed = p.adv_speed;
     fa.Fout = fx;
@@ -143,7 +144,7 @@ wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat
     if (!f_padded || !fhat || n < 1 || n > (int64_t(1) << 31) - 8) return WENOZN_EINVAL;
     if (side != 1 && side != -1) return WENOZN_EINVAL;
     if (!finite_pos(eps) || !std::isfinite(A) || A < 0.0) return WENOZN_EINVAL;
-    return cuda_status(launch_reconstruct(f_padded, n, fhat, side, 4.0 * eps, A,
+    return cuda_status(launch_reconstruct(f_padded, n, fhat, side, eps, A,
                                           static_cast<cudaStream_t>(stream)));
 }
 
@@ -173,7 +174,8 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     fa.nx = p->nx;
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
-    fa.A = p->A;
+    fa.A4 = 0.25 * p->A;
+    fa.fast_rcp = zn_fast_rcp(p->eps, p->A);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;
     fa.Fout = Fout;
@@ -266,6 +268,12 @@ wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, 
     if (e != cudaSuccess) return WENOZN_ECUDA;
     *status = host;
     return WENOZN_OK;
+}
+
+wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, double* ieee,
+                                      void* stream) {
+    if (!d || !fast || !ieee || n < 1 || n > (int64_t(1) << 31)) return WENOZN_EINVAL;
+    return cuda_status(launch_rcp_check(d, n, fast, ieee, static_cast<cudaStream_t>(stream)));
 }
 
 const char* wenozn_status_string(wenozn_status s) {

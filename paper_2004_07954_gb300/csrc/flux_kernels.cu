@@ -20,8 +20,8 @@ constexpr int kThreads = 256;
 template <int NV, int DIR> struct Tile;
 template <> struct Tile<1, 0> { static constexpr int TI = 512, TA = 1; };
 template <> struct Tile<3, 0> { static constexpr int TI = 512, TA = 1; };
-template <> struct Tile<4, 0> { static constexpr int TI = 64, TA = 8; };
-template <> struct Tile<4, 1> { static constexpr int TI = 16, TA = 32; };
+template <> struct Tile<4, 0> { static constexpr int TI = 128, TA = 4; };
+template <> struct Tile<4, 1> { static constexpr int TI = 32, TA = 16; };
 
 template <int NV> struct SmemLayout {
     // number of doubles per cell in shared memory
@@ -29,7 +29,7 @@ template <int NV> struct SmemLayout {
 };
 
 template <int NV, int DIR>
-__global__ void __launch_bounds__(kThreads) flux_kernel(FluxArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) flux_kernel(FluxArgs a) {
     constexpr int TI = Tile<NV, DIR>::TI, TA = Tile<NV, DIR>::TA;
     constexpr int CL = TI + 5;            // cells per line in the tile
     constexpr int NC = CL * TA;           // cells per tile
@@ -84,17 +84,18 @@ __global__ void __launch_bounds__(kThreads) flux_kernel(FluxArgs a) {
         const double kin = NV == 4 ? 0.5 * fma(mn, un, mt * ut) : 0.5 * (mn * un);
         const double p = gm1 * (E - kin);
         const double Ep = E + p;
-        double F[NV], Uc[NV];
+        // half the physical flux, F/2 = (m_n, m_n u_n + p, m_t u_n, u_n (E + p)) / 2
+        const double hun = 0.5 * un;
+        double hF[NV], Uc[NV];
         Uc[0] = rho; Uc[1] = mn; Uc[NV - 1] = E;
-        F[0] = mn;
-        F[1] = fma(mn, un, p);
-        if (NV == 4) { Uc[2] = mt; F[2] = mt * un; }
-        F[NV - 1] = un * Ep;
+        hF[0] = 0.5 * mn;
+        hF[1] = fma(mn, hun, 0.5 * p);
+        if (NV == 4) { Uc[2] = mt; hF[2] = mt * hun; }
+        hF[NV - 1] = hun * Ep;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const double hf = 0.5 * F[k];
-            sHp[k * NC + si] = fma(half_a, Uc[k], hf);
-            sHm[k * NC + si] = fma(-half_a, Uc[k], hf);
+            sHp[k * NC + si] = fma(half_a, Uc[k], hF[k]);
+            sHm[k * NC + si] = fma(-half_a, Uc[k], hF[k]);
         }
         sSr[si] = rho * rs;                                // sqrt(rho)
         sUn[si] = un;
@@ -115,12 +116,12 @@ __global__ void __launch_bounds__(kThreads) flux_kernel(FluxArgs a) {
             Fh[0] = zn_split_flux(sHp[sidx(l, jl)], sHp[sidx(l, jl + 1)], sHp[sidx(l, jl + 2)],
                                   sHp[sidx(l, jl + 3)], sHp[sidx(l, jl + 4)],
                                   sHm[sidx(l, jl + 1)], sHm[sidx(l, jl + 2)], sHm[sidx(l, jl + 3)],
-                                  sHm[sidx(l, jl + 4)], sHm[sidx(l, jl + 5)], a.eps4, a.A);
+                                  sHm[sidx(l, jl + 4)], sHm[sidx(l, jl + 5)], a.eps4, a.A4, a.fast_rcp != 0);
         } else {
             // Roe average between cells j-1 and j (local jl+2, jl+3)
             const int cl = sidx(l, jl + 2), cr = sidx(l, jl + 3);
             const double srl = sSr[cl], srr = sSr[cr];
-            const double rsum = 1.0 / (srl + srr);
+            const double rsum = rcp_nr(srl + srr);
             const double wl = srl * rsum, wr = srr * rsum;
             const double u = fma(wl, sUn[cl], wr * sUn[cr]);
             const double v = NV == 4 ? fma(wl, sUt[cl], wr * sUt[cr]) : 0.0;
@@ -131,48 +132,37 @@ __global__ void __launch_bounds__(kThreads) flux_kernel(FluxArgs a) {
             const double c = c2 * rc;
             const double b1 = gm1 * (rc * rc);             // (gamma - 1) / c^2
             const double b2 = 0.5 * q2 * b1;
-            const double urc = u * rc, b1u = b1 * u, hb1 = 0.5 * b1;
-            // left eigenvectors (rows) in the direction frame
-            double Lm[NV][NV];
-            Lm[0][0] = 0.5 * (b2 + urc);
-            Lm[0][1] = -0.5 * (b1u + rc);
-            Lm[NV - 1][0] = 0.5 * (b2 - urc);
-            Lm[NV - 1][1] = -0.5 * (b1u - rc);
-            Lm[0][NV - 1] = hb1;
-            Lm[NV - 1][NV - 1] = hb1;
-            Lm[1][0] = 1.0 - b2;
-            Lm[1][1] = b1u;
-            Lm[1][NV - 1] = -b1;
-            if (NV == 4) {
-                Lm[0][2] = -hb1 * v;
-                Lm[3][2] = -hb1 * v;
-                Lm[1][2] = b1 * v;
-                Lm[2][0] = -v; Lm[2][1] = 0.0; Lm[2][2] = 1.0; Lm[2][3] = 0.0;
+            const double hrc = 0.5 * rc;
+            // Projection onto the left eigenvectors of the Roe state (rows, direction frame)
+            //   l_{u-c} = ( (b2 + u/c)/2, -(b1 u + 1/c)/2, -b1 v/2, b1/2 )
+            //   l_u     = ( 1 - b2, b1 u, b1 v, -b1 )
+            //   l_shear = ( -v, 0, 1, 0 )                          (2D only)
+            //   l_{u+c} = ( (b2 - u/c)/2, -(b1 u - 1/c)/2, -b1 v/2, b1/2 )
+            // evaluated through their shared parts: with W = u h_1 + v h_2 - h_E,
+            // Z = b2 h_0 - b1 W and B = (u h_0 - h_1)/(2c),
+            //   l_u.h = h_0 - Z,  l_{u-+c}.h = Z/2 +- B,  l_shear.h = h_2 - v h_0.
+            auto project = [&](const double* hs, int i, double* g) {
+                const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
+                const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+                const double Z = fma(b2, h0, -(b1 * W));
+                const double B = hrc * fma(u, h0, -h1);
+                g[0] = fma(0.5, Z, B);
+                g[1] = h0 - Z;
+                if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+                g[NV - 1] = fma(0.5, Z, -B);
+            };
+            double gp[5][NV], gm[5][NV];
+#pragma unroll
+            for (int st = 0; st < 5; ++st) {
+                project(sHp, sidx(l, jl + st), gp[st]);
+                project(sHm, sidx(l, jl + 1 + st), gm[st]);
             }
             double gh[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                double gp[5], gm[5];
-#pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const int ip = sidx(l, jl + s), im = sidx(l, jl + 1 + s);
-                    if (NV == 4 && k == 2) {                 // shear wave: m_t - v rho
-                        gp[s] = fma(-v, sHp[ip], sHp[2 * NC + ip]);
-                        gm[s] = fma(-v, sHm[im], sHm[2 * NC + im]);
-                    } else {
-                        double accp = Lm[k][0] * sHp[ip], accm = Lm[k][0] * sHm[im];
-#pragma unroll
-                        for (int m = 1; m < NV; ++m) {
-                            accp = fma(Lm[k][m], sHp[m * NC + ip], accp);
-                            accm = fma(Lm[k][m], sHm[m * NC + im], accm);
-                        }
-                        gp[s] = accp;
-                        gm[s] = accm;
-                    }
-                }
-                gh[k] = zn_split_flux(gp[0], gp[1], gp[2], gp[3], gp[4],
-                                      gm[0], gm[1], gm[2], gm[3], gm[4], a.eps4, a.A);
-            }
+            for (int k = 0; k < NV; ++k)
+                gh[k] = zn_split_flux(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k],
+                                      gm[0][k], gm[1][k], gm[2][k], gm[3][k], gm[4][k], a.eps4, a.A4,
+                                      a.fast_rcp != 0);
             // back-projection F^ = R g^ with the right eigenvectors (columns)
             const double uc = u * c;
             if (NV == 3) {

@@ -16,8 +16,11 @@ struct FluxArgs {
     double* Fout;
     const unsigned long long* alpha_bits;  // LF speeds (x, y) of U as bit patterns; unused for advection
     int nx, ny, bc;                        // bc of the sweep direction
-    double eps4, A, gamma, adv_speed;
+    int fast_rcp;                          // 1: Newton reciprocal for f^ = num/den (see zn_flux)
+    double eps4, A4, gamma, adv_speed;     // eps4 = 4 eps, A4 = A / 4
 };
+// Whether the WENO-ZN denominator is guaranteed positive and normal (Newton reciprocal).
+inline int zn_fast_rcp(double eps, double A) { return A > 0.0 && eps >= 1e-60 ? 1 : 0; }
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s);
 
 // Flux difference, SSP-RK3 stage combination and the next stage's LF speeds.
@@ -42,7 +45,9 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
                                  cudaStream_t s);
 
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
-                               double eps4, double A, cudaStream_t s);
+                               double eps, double A, cudaStream_t s);
+
+cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,
                                double* U_padded, cudaStream_t s);

@@ -93,7 +93,8 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
     fa.nx = p->nx;
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
-    fa.A = p->A;
+    fa.A4 = 0.25 * p->A;
+    fa.fast_rcp = zn_fast_rcp(p->eps, p->A);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;
     if (e == cudaSuccess) {

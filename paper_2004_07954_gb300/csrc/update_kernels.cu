@@ -117,12 +117,21 @@ __global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, u
 }
 
 __global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, int64_t n, double* fhat,
-                                                                int side, double eps4, double A) {
+                                                                int side, double eps4, double A4,
+                                                                int fast_rcp) {
     const int64_t j = blockIdx.x * int64_t(kThreads) + threadIdx.x;
     if (j > n) return;
     const double* s = f + j;
-    fhat[j] = side > 0 ? zn_flux(s[0], s[1], s[2], s[3], s[4], eps4, A)
-                       : zn_flux(s[5], s[4], s[3], s[2], s[1], eps4, A);
+    fhat[j] = side > 0 ? zn_flux(s[0], s[1], s[2], s[3], s[4], eps4, A4, fast_rcp != 0)
+                       : zn_flux(s[5], s[4], s[3], s[2], s[1], eps4, A4, fast_rcp != 0);
+}
+
+__global__ void __launch_bounds__(kThreads) rcp_check_kernel(const double* d, int64_t n, double* fast,
+                                                              double* ieee) {
+    const int64_t i = blockIdx.x * int64_t(kThreads) + threadIdx.x;
+    if (i >= n) return;
+    fast[i] = rcp_nr(d[i]);
+    ieee[i] = 1.0 / d[i];
 }
 
 // x-ghosts of the interior rows (phase 0) or y-ghosts of every padded column (phase 1).
@@ -190,9 +199,15 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
 }
 
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
-                               double eps4, double A, cudaStream_t s) {
+                               double eps, double A, cudaStream_t s) {
     const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
-    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, eps4, A);
+    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, 0.25 * A,
+                                                 zn_fast_rcp(eps, A));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s) {
+    rcp_check_kernel<<<unsigned((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, n, fast, ieee);
     return cudaGetLastError();
 }
 

@@ -16,27 +16,47 @@ namespace wz {
 //
 //   Eq. (4)        q_0 = (2a - 7b + 11c)/6, q_1 = (-b + 5c + 2d)/6, q_2 = (2c + 5d - e)/6
 //   Eq. (isjiang)  IS_k = 13/12 s_k^2 + 1/4 t_k^2 with s_k the second difference and t_k
-//                  the one-sided first differences of sub-stencil k
+//                  the one-sided first difference of sub-stencil k
 //   Eq. (tau)      tau5 = |IS_0 - IS_2|
 //   Eq. (tau8)     tau8 = (a - 4b + 6c - 4d + e)^2
 //   Eq. (function) C = A ((IS_0 + IS_2 - tau5 + eps)/(tau5 + eps))^2
 //   Eq. (new)      alpha_k = c_k (C + tau8/(IS_k + eps)),  c = (1, 6, 3)/10
 //   Eq. (3)        f^ = sum_k alpha_k q_k / sum_k alpha_k
 //
-// Evaluation: indicators and tau8 are carried scaled by 4 (4 IS_k = 13/3 s_k^2 + t_k^2,
-// 4 tau8 = (2 d4)^2) with eps4 = 4 eps, which leaves C and tau8/(IS_k + eps) unchanged.
-// IS_0 + IS_2 - tau5 = 2 min(IS_0, IS_2).  Multiplying every alpha_k by
-// (tau5 + eps)^2 (IS_0 + eps)(IS_1 + eps)(IS_2 + eps) / c_k gives
-//   a_k = A m^2 b_0 b_1 b_2 + 4 tau8 P^2 prod_{j != k} b_j,  m = 2 min + eps, P = tau5 + eps,
-// all positive (a_k >= A (4 eps)^5 > 0), and the optimal weights are folded into the
-// integer coefficients of the sub-stencil fluxes.  Range: finite for |f| below ~1e20.
+// Evaluation (exact algebra; only the rounding differs from the plain order):
+//  * with s_0 = a - 2b + c, s_1 = b - 2c + d, s_2 = c - 2d + e and t_0 = a - 4b + 3c,
+//    t_1 = b - d, t_2 = 3c - 4d + e, the sub-stencil fluxes are
+//    q_k = c + s_k/12 + t_k/4 (k = 0) and c + s_k/12 - t_k/4 (k = 1, 2);
+//  * indicators are carried scaled by 4 together with eps: b_k = 4 (IS_k + eps)
+//    = 13/3 s_k^2 + t_k^2 + 4 eps, so C and tau8/(IS_k + eps) = 4 tau8 / b_k are unchanged;
+//  * IS_0 + IS_2 - tau5 = 2 min(IS_0, IS_2), i.e. 4 (IS_0 + IS_2 - tau5 + eps) = 2 min(b) - 4 eps
+//    = m and 4 (tau5 + eps) = max(b) - min(b) + 4 eps = P; min/max of the non-negative b
+//    run on the integer pipe;
+//  * every alpha_k is multiplied by P^2 b_0 b_1 b_2 / (4 c_k) and the common factor divided
+//    out: a_k = (A/4) m^2 b_0 b_1 b_2 + (d4 P)^2 prod_{j != k} b_j with d4 the fourth
+//    difference, all positive (a_k >= (A/4) (4 eps)^5 > 0); the optimal weights (1, 6, 3)/10
+//    then enter through 6 q_1 and 3 q_2 and the denominator a_0 + 6 a_1 + 3 a_2, leaving one
+//    division per reconstruction.  The fourth difference is d4 = t_0 + t_2.
+// Range: finite for |f| below ~1e20.
 // ------------------------------------------------------------------------------------
 struct ZnParts {
     double num, den;     // f^ = num / den
 };
 
+// Reciprocal of a positive, normal double: start from the hardware approximation
+// r0 (rcp.approx.ftz.f64, about 23 correct bits), form e = 1 - d r0 and take one step of
+// the cubically convergent series 1/d = r0 (1 + e + e^2 + ...) truncated after e^2
+// (Householder's third-order iteration): the relative error becomes about e^3 ~ 2^-69, so
+// the result is within about one ulp of 1/d.  Used where d is known to be positive and normal.
+__device__ __forceinline__ double rcp_nr(double d) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
 __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double d, double e,
-                                            double eps4, double A) {
+                                            double eps4, double A4) {
     const double s0 = fma(-2.0, b, a) + c;
     const double s1 = fma(-2.0, c, b) + d;
     const double s2 = fma(-2.0, d, c) + e;
@@ -44,35 +64,43 @@ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double
     const double t1 = b - d;
     const double t2 = fma(3.0, c, fma(-4.0, d, e));
     const double k13_3 = 13.0 / 3.0;
-    const double is0 = fma(k13_3 * s0, s0, t0 * t0);
-    const double is1 = fma(k13_3 * s1, s1, t1 * t1);
-    const double is2 = fma(k13_3 * s2, s2, t2 * t2);
-    const double d4 = fma(-2.0, s1, s0) + s2;               // fourth difference
+    const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));   // 4 (IS_0 + eps)
+    const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
+    const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
+    const double d4 = t0 + t2;                                  // a - 4b + 6c - 4d + e
     // non-negative doubles order like their bit patterns: min/max on the integer pipe
-    const long long i0 = __double_as_longlong(is0), i2 = __double_as_longlong(is2);
+    const long long i0 = __double_as_longlong(b0), i2 = __double_as_longlong(b2);
     const double mn = __longlong_as_double(i0 < i2 ? i0 : i2);
     const double mx = __longlong_as_double(i0 < i2 ? i2 : i0);
-    const double P = (mx - mn) + eps4;                       // tau5 + eps
-    const double m = fma(2.0, mn, eps4);                     // IS_0 + IS_2 - tau5 + eps
-    const double b0 = is0 + eps4, b1 = is1 + eps4, b2 = is2 + eps4;
+    const double P = (mx - mn) + eps4;                          // 4 (tau5 + eps)
+    const double m = fma(2.0, mn, -eps4);                       // 4 (IS_0 + IS_2 - tau5 + eps)
     const double b01 = b0 * b1, b12 = b1 * b2, b02 = b0 * b2;
-    const double X = (A * m) * m * (b01 * b2);
+    const double X = (A4 * m) * m * (b01 * b2);
     const double z = d4 * P;
-    const double Y = 4.0 * (z * z);
-    const double a0 = fma(Y, b12, X), a1 = fma(Y, b02, X), a2 = fma(Y, b01, X);
-    const double q0 = fma(11.0, c, fma(-7.0, b, 2.0 * a));   //  6 q_0
-    const double q1 = fma(12.0, d, fma(30.0, c, -6.0 * b));  // 36 q_1
-    const double q2 = fma(15.0, d, fma(6.0, c, -3.0 * e));   // 18 q_2
+    const double Y = z * z;
+    const double a0 = fma(Y, b12, X);
+    const double a1 = fma(Y, b02, X);
+    const double a2 = fma(Y, b01, X);
+    // q_k scaled by the optimal-weight ratios (1, 6, 3): 6 q_1 = 6c + s_1/2 - 3 t_1/2,
+    // 3 q_2 = 3c + s_2/4 - 3 t_2/4
+    const double k1_12 = 1.0 / 12.0;
+    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
+    const double q0 = fma(k1_12, s0, fma(0.25, t0, c));
+    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
+    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
     ZnParts r;
     r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
-    r.den = fma(6.0, a0, fma(36.0, a1, 18.0 * a2));
+    r.den = fma(6.0, a1, fma(3.0, a2, a0));
     return r;
 }
 
+// f^ = num / den.  With A > 0 and eps >= 1e-60, den >= 10 (A/4) (4 eps)^5 is a positive
+// normal number, so the Newton reciprocal applies (fast_rcp = true, chosen by the host);
+// otherwise the IEEE division is used.
 __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
-                                          double eps4, double A) {
-    const ZnParts r = zn_parts(a, b, c, d, e, eps4, A);
-    return r.num / r.den;
+                                          double eps4, double A4, bool fast_rcp) {
+    const ZnParts r = zn_parts(a, b, c, d, e, eps4, A4);
+    return fast_rcp ? r.num * rcp_nr(r.den) : r.num / r.den;
 }
 
 // f^+ + f^- at one interface: plus side from (p0..p4) = h+_{i-2..i+2}, minus side from the
@@ -80,8 +108,8 @@ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d
 // "symmetric rule about x_{i+1/2}").
 __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2, double p3, double p4,
                                                 double m0, double m1, double m2, double m3, double m4,
-                                                double eps4, double A) {
-    return zn_flux(p0, p1, p2, p3, p4, eps4, A) + zn_flux(m4, m3, m2, m1, m0, eps4, A);
+                                                double eps4, double A4, bool fast_rcp) {
+    return zn_flux(p0, p1, p2, p3, p4, eps4, A4, fast_rcp) + zn_flux(m4, m3, m2, m1, m0, eps4, A4, fast_rcp);
 }
 
 // ------------------------------------------------------------------------------------

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "wenozn_rk3_step": [_P, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                         _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
+    "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
 }
 
 
@@ -216,6 +217,15 @@ def wenozn_workspace_status(ws: torch.Tensor, clear: bool = False, stream=None) 
     _check("wenozn_workspace_status", lib().wenozn_workspace_status(_ws_ptr(ws), ctypes.byref(st),
                                                                     int(bool(clear)), _stream(stream)))
     return st.value
+
+
+def wenozn_check_reciprocal(d: torch.Tensor, stream=None):
+    """(fast, ieee): the reconstruction's Newton reciprocal and CUDA's IEEE 1/d."""
+    fast, ieee = torch.empty_like(d), torch.empty_like(d)
+    _check("wenozn_check_reciprocal", lib().wenozn_check_reciprocal(_dev_ptr(d, "d"), d.numel(),
+                                                                    _dev_ptr(fast, "fast"), _dev_ptr(ieee, "ieee"),
+                                                                    _stream(stream)))
+    return fast, ieee
 
 
 def wenozn_workspace_dt(ws: torch.Tensor) -> torch.Tensor:

@@ -91,6 +91,19 @@ def test_table3_critical_points_on_gpu(wz, orc):
         assert err == pytest.approx(zn, rel=1e-4)
 
 
+def test_newton_reciprocal_within_one_ulp(wz):
+    """The reciprocal behind f^ = num/den (Newton-Raphson on the hardware approximation)
+    stays within one ulp of CUDA's IEEE 1/d over the whole normal range it is used on."""
+    g = np.random.default_rng(7)
+    d = np.ldexp(g.uniform(1.0, 2.0, 200000), g.integers(-1000, 1000, 200000))
+    d = np.concatenate([d, [1.0, 2.0, 3.0, 1e-300, 1e300, 0.1, 7.0, np.nextafter(2.0, 0)]])
+    fast, ieee = wz.wenozn_check_reciprocal(dev(d))
+    f, i = host(fast), host(ieee)
+    assert np.array_equal(i, 1.0 / d)                     # CUDA's division is IEEE
+    ulp = np.spacing(np.abs(i))
+    assert np.all(np.abs(f - i) <= ulp)
+
+
 # ------------------------------------------------------------------ ghosts and LF speeds
 @pytest.mark.parametrize("bc", [0, 1])
 def test_fill_ghosts(wz, orc, bc):
