@@ -46,7 +46,7 @@ TRAFFIC_CAPTURE = {"sha256_16": "ef47758b859bdf82", "n": 4096, "bytes": 966e6}
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("flux_kernels.cu", "wenozn_device.cuh"):
+    for f in ("flux_kernels.cu", "wenozn_device.cuh", "euler_device.cuh"):
         with open(os.path.join(ROOT, "paper_2004_07954_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -169,6 +169,66 @@ const double* wenozn_workspace_dt(const void* ws);
  * non-zero, resets it. */
 wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched 1D Euler: B independent problems of uneven size (the 1D Euler set-up of Sec. 4.3,
+ * each with its own grid), advanced together by one persistent kernel launch per RK stage.
+ *
+ * Layout: U[3][total] concatenated per variable; instance b occupies columns
+ * offsets[b] .. offsets[b+1]-1 (offsets[0] = 0, every instance >= 1 cell).  Each instance
+ * has its own spacing dx[b], its own global LF speed (max |u|+c over its cells, per RK
+ * stage), its own CFL step dt_b = cfl dx_b / alpha_b from its U^n, and its own time t_b;
+ * with t_final > 0 no instance steps past t_final (finished instances are left unchanged).
+ * `offsets` is the same host array of B+1 int64 on every call; the library keeps no copy
+ * on the host.  The step launches no memset and does not synchronise, so a sequence of
+ * steps can be captured in a CUDA graph (after wenozn_batch_init).
+ * --------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t nbatch;   /* instances B, 1 .. 2^24                                            */
+    int32_t bc;       /* wenozn_bc of every instance                                       */
+    int32_t shape;    /* kernel tile shape, 0 .. wenozn_batch_num_shapes()-1; -1 = default */
+    int32_t flags;    /* reserved, 0                                                       */
+    double gamma;     /* 1.4 (Sec. 4.3)                                                     */
+    double eps;       /* Eq. (new), 1e-40                                                   */
+    double A;         /* Eq. (function), 10                                                 */
+    double cfl;       /* 0.5                                                                */
+    double t_final;   /* > 0: stop every instance there; <= 0: no limit                     */
+} wenozn_batch_params;
+
+/* Number of compiled tile shapes, and the (interfaces per tile, threads per block) of one. */
+int32_t wenozn_batch_num_shapes(void);
+wenozn_status wenozn_batch_shape(int32_t shape, int32_t* tile, int32_t* threads);
+
+/* Device workspace bytes for the batch (control block, per-instance arrays, tile prefix
+ * counts of every shape, two RK stage buffers of 3 x total doubles), 256-byte aligned. */
+wenozn_status wenozn_batch_workspace_size(const wenozn_batch_params* bp, const int64_t* offsets,
+                                          size_t* bytes);
+
+/* Copies offsets and dx (host arrays, B+1 and B entries) into the workspace, builds the
+ * tile lists, computes every instance's LF speed of U (device, [3][total]) and sets t = 0.
+ * Synchronises `stream`; the host arrays may be released afterwards.  Call it before any
+ * stream capture that contains wenozn_batch_rk3_step. */
+wenozn_status wenozn_batch_init(const wenozn_batch_params* bp, const int64_t* offsets, const double* dx,
+                                const double* U, void* ws, size_t ws_bytes, void* stream);
+
+/* One SSP-RK3 step of every instance (Sec. 4: third-order TVD Runge-Kutta), in place:
+ * three launches of the batched stage kernel, each fusing LF splitting, characteristic
+ * WENO-ZN fluxes, the flux difference of Eq. (2), the stage update and the next stage's
+ * per-instance LF speeds. */
+wenozn_status wenozn_batch_rk3_step(const wenozn_batch_params* bp, const int64_t* offsets, double* U,
+                                    void* ws, size_t ws_bytes, void* stream);
+
+/* Autotuner: times `steps` RK3 steps (after one warm-up step) of every compiled shape on
+ * this batch and stores the fastest in bp->shape; ms_per_step (host, num_shapes floats) or
+ * NULL receives the timings.  U is advanced by the trial steps: tune on a copy.
+ * Synchronises `stream`. */
+wenozn_status wenozn_batch_tune(wenozn_batch_params* bp, const int64_t* offsets, double* U, void* ws,
+                                size_t ws_bytes, int32_t steps, float* ms_per_step, void* stream);
+
+/* Device addresses of the per-instance time t[B], step dt[B] (of the last RK3 step) and the
+ * batch's status word inside the workspace (any output pointer may be NULL). */
+wenozn_status wenozn_batch_state(void* ws, int32_t nbatch, const int64_t* offsets, double** t,
+                                 double** dt, int32_t** status);
+
 /* Diagnostic: evaluates, for n positive normal doubles d, the reciprocal the reconstruction
  * uses for f^ = num/den (Newton-Raphson refinement of the hardware approximation) into
  * `fast` and CUDA's IEEE 1/d into `ieee`, so that tests can bound the former's error.

@@ -1,0 +1,151 @@
+// Per-cell and per-interface building blocks shared by the single-problem flux kernels and
+// the batched kernel: LF flux splitting of one cell (Sec. 2, Sec. 4.3) and the numerical
+// flux of one interface (Roe average, characteristic projection, WENO-ZN of both split
+// parts, back-projection).  Everything lives in shared memory planes of a tile.
+#pragma once
+
+#include "wenozn_device.cuh"
+
+namespace wz {
+
+// Shared-memory planes of one tile of NC cells: split fluxes h+ and h- (NV planes each),
+// and for the Euler systems sqrt(rho), u_n, H (and u_t in 2D).
+template <int NV>
+struct CellPlanes {
+    static constexpr int kPerCell = NV == 1 ? 2 : 2 * NV + (NV == 4 ? 4 : 3);
+    double* hp;
+    double* hm;
+    double* sr;
+    double* un;
+    double* H;
+    double* ut;
+    int NC;
+    __device__ __forceinline__ CellPlanes(double* base, int nc) : NC(nc) {
+        hp = base;
+        hm = hp + NV * nc;
+        sr = hm + NV * nc;
+        un = sr + nc;
+        H = un + nc;
+        ut = H + nc;
+    }
+};
+
+// One cell: Uc = (rho, m_n[, m_t], E) in the sweep direction's frame (or the scalar u with
+// the advection speed `a`), alpha the LF speed.  Writes h+- = (F +- alpha U)/2 and the Roe
+// ingredients at shared index si.
+template <int NV>
+__device__ __forceinline__ void split_cell(const double* Uc, double alpha, double a_adv, double gm1,
+                                           const CellPlanes<NV>& s, int si) {
+    const double half_a = 0.5 * alpha;
+    if (NV == 1) {
+        const double u = Uc[0];
+        const double f = a_adv * u;
+        s.hp[si] = 0.5 * fma(alpha, u, f);
+        s.hm[si] = 0.5 * fma(-alpha, u, f);
+        return;
+    }
+    const double rho = Uc[0], mn = Uc[1], E = Uc[NV - 1];
+    const double mt = NV == 4 ? Uc[2] : 0.0;
+    const double rs = rsqrt(rho);
+    const double rr = rs * rs;                         // 1 / rho
+    const double un = mn * rr;
+    const double ut = mt * rr;
+    const double kin = NV == 4 ? 0.5 * fma(mn, un, mt * ut) : 0.5 * (mn * un);
+    const double p = gm1 * (E - kin);
+    const double Ep = E + p;
+    // half the physical flux, F/2 = (m_n, m_n u_n + p, m_t u_n, u_n (E + p)) / 2
+    const double hun = 0.5 * un;
+    double hF[NV];
+    hF[0] = 0.5 * mn;
+    hF[1] = fma(mn, hun, 0.5 * p);
+    if (NV == 4) hF[2] = mt * hun;
+    hF[NV - 1] = hun * Ep;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        s.hp[k * s.NC + si] = fma(half_a, Uc[k], hF[k]);
+        s.hm[k * s.NC + si] = fma(-half_a, Uc[k], hF[k]);
+    }
+    s.sr[si] = rho * rs;                               // sqrt(rho)
+    s.un[si] = un;
+    s.H[si] = Ep * rr;
+    if (NV == 4) s.ut[si] = ut;
+}
+
+// Numerical flux F^ at the interface between the stencil's cells 2 and 3, the stencil being
+// the six cells base + k*stride, k = 0..5 (cells i-2 .. i+3 around x_{i+1/2}).
+// Fh is in the sweep direction's frame.
+template <int NV>
+__device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base, int stride,
+                                               double gm1, double eps4, double A4, bool fast_rcp,
+                                               double* Fh) {
+    const int NC = s.NC;
+    if (NV == 1) {
+        Fh[0] = zn_split_flux(s.hp[base], s.hp[base + stride], s.hp[base + 2 * stride],
+                              s.hp[base + 3 * stride], s.hp[base + 4 * stride],
+                              s.hm[base + stride], s.hm[base + 2 * stride], s.hm[base + 3 * stride],
+                              s.hm[base + 4 * stride], s.hm[base + 5 * stride], eps4, A4, fast_rcp);
+        return;
+    }
+    // Roe average between the stencil's cells 2 and 3
+    const int cl = base + 2 * stride, cr = base + 3 * stride;
+    const double srl = s.sr[cl], srr = s.sr[cr];
+    const double rsum = rcp_nr(srl + srr);
+    const double wl = srl * rsum, wr = srr * rsum;
+    const double u = fma(wl, s.un[cl], wr * s.un[cr]);
+    const double v = NV == 4 ? fma(wl, s.ut[cl], wr * s.ut[cr]) : 0.0;
+    const double H = fma(wl, s.H[cl], wr * s.H[cr]);
+    const double q2 = NV == 4 ? fma(u, u, v * v) : u * u;
+    const double c2 = gm1 * fma(-0.5, q2, H);
+    const double rc = rsqrt(c2);
+    const double c = c2 * rc;
+    const double b1 = gm1 * (rc * rc);                 // (gamma - 1) / c^2
+    const double b2 = 0.5 * q2 * b1;
+    const double hrc = 0.5 * rc;
+    // Projection onto the left eigenvectors of the Roe state (rows, direction frame)
+    //   l_{u-c} = ( (b2 + u/c)/2, -(b1 u + 1/c)/2, -b1 v/2, b1/2 )
+    //   l_u     = ( 1 - b2, b1 u, b1 v, -b1 )
+    //   l_shear = ( -v, 0, 1, 0 )                          (2D only)
+    //   l_{u+c} = ( (b2 - u/c)/2, -(b1 u - 1/c)/2, -b1 v/2, b1/2 )
+    // evaluated through their shared parts: with W = u h_1 + v h_2 - h_E,
+    // Z = b2 h_0 - b1 W and B = (u h_0 - h_1)/(2c),
+    //   l_u.h = h_0 - Z,  l_{u-+c}.h = Z/2 +- B,  l_shear.h = h_2 - v h_0.
+    auto project = [&](const double* hs, int i, double* g) {
+        const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
+        const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+        const double Z = fma(b2, h0, -(b1 * W));
+        const double B = hrc * fma(u, h0, -h1);
+        g[0] = fma(0.5, Z, B);
+        g[1] = h0 - Z;
+        if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+        g[NV - 1] = fma(0.5, Z, -B);
+    };
+    double gp[5][NV], gm[5][NV];
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        project(s.hp, base + st * stride, gp[st]);
+        project(s.hm, base + (st + 1) * stride, gm[st]);
+    }
+    double gh[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        gh[k] = zn_split_flux(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k],
+                              gm[0][k], gm[1][k], gm[2][k], gm[3][k], gm[4][k], eps4, A4, fast_rcp);
+    // back-projection F^ = R g^ with the right eigenvectors (columns)
+    //   r_{u-c} = (1, u-c, [v,] H-uc), r_u = (1, u, [v,] q^2/2), r_shear = (0, 0, 1, v),
+    //   r_{u+c} = (1, u+c, [v,] H+uc)
+    const double uc = u * c;
+    if (NV == 3) {
+        const double d20 = gh[2] - gh[0];
+        Fh[0] = gh[0] + gh[1] + gh[2];
+        Fh[1] = fma(u, Fh[0], c * d20);
+        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, 0.5 * q2 * gh[1]));
+    } else {
+        const double d30 = gh[3] - gh[0];
+        Fh[0] = gh[0] + gh[1] + gh[3];
+        Fh[1] = fma(u, Fh[0], c * d30);
+        Fh[2] = fma(v, Fh[0], gh[2]);
+        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(0.5 * q2, gh[1], v * gh[2])));
+    }
+}
+
+}  // namespace wz

@@ -47,6 +47,33 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
                                double eps, double A, cudaStream_t s);
 
+// Batched 1D Euler (see batch_kernels.cu).
+struct BatchArgs {
+    const double* Us;          // stage input, [3][total]
+    const double* Un;          // state at the start of the step
+    double* out;               // stage output (aliases Un in the last stage)
+    int64_t total;             // plane stride: total cells of the batch
+    int B;                     // instances
+    const int64_t* off;        // [B+1] first cell of each instance
+    const int32_t* tile_off;   // [B+1] prefix count of tiles (tiles of TI-1 cells)
+    const double* dx;          // [B]
+    unsigned long long* alpha; // [3][B] LF speeds per stage slot, bit patterns
+    double* dt;                // [B] step of the current RK3 step
+    double* t;                 // [B] time reached
+    int32_t* status;
+    int stage;                 // 0, 1, 2
+    int bc;                    // ghost map of every instance
+    int fast_rcp;
+    double gamma, eps4, A4, cfl;
+    double t_final;            // > 0: no instance steps past it
+};
+struct BatchShape { int tile, threads; };
+constexpr int kNumBatchShapes = 5;
+extern const BatchShape kBatchShapes[kNumBatchShapes];
+cudaError_t batch_configure();
+cudaError_t launch_batch_init(const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_batch_stage(int shape, const BatchArgs& a, int sms, cudaStream_t s);
+
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,

@@ -152,9 +152,11 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Block-wide maximum of two non-negative values, folded into `dst` (bit-pattern atomicMax:
-// order-independent and exact).  Must be called by every thread of the block.
-__device__ __forceinline__ void block_max2_atomic(double vx, double vy, unsigned long long* dst) {
+// Block-wide maximum of two non-negative values, folded into dst[0] and dst[1] (bit-pattern
+// atomicMax: order-independent and exact); with only_first, just vx into dst[0].  Must be
+// called by every thread of the block.
+__device__ __forceinline__ void block_max2_atomic(double vx, double vy, unsigned long long* dst,
+                                                  bool only_first = false) {
     __shared__ double red[2][32];
     vx = warp_max(vx);
     vy = warp_max(vy);
@@ -168,7 +170,7 @@ __device__ __forceinline__ void block_max2_atomic(double vx, double vy, unsigned
         vy = warp_max(vy);
         if (lane == 0) {
             atomicMax(&dst[0], (unsigned long long)__double_as_longlong(vx));
-            atomicMax(&dst[1], (unsigned long long)__double_as_longlong(vy));
+            if (!only_first) atomicMax(&dst[1], (unsigned long long)__double_as_longlong(vy));
         }
     }
 }

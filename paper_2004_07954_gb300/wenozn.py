@@ -44,6 +44,12 @@ class wenozn_problem(ctypes.Structure):
         return (self.nvar, self.ny, self.nx)
 
 
+class wenozn_batch_params(ctypes.Structure):
+    _fields_ = [("nbatch", ctypes.c_int32), ("bc", ctypes.c_int32), ("shape", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
+                ("A", ctypes.c_double), ("cfl", ctypes.c_double), ("t_final", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -62,6 +68,14 @@ _SIGNATURES = {
                         _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
+    "wenozn_batch_shape": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "wenozn_batch_workspace_size": [ctypes.POINTER(wenozn_batch_params), _VP, ctypes.POINTER(ctypes.c_size_t)],
+    "wenozn_batch_init": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_batch_rk3_step": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_batch_tune": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int32,
+                          ctypes.POINTER(ctypes.c_float), _VP],
+    "wenozn_batch_state": [_VP, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                           ctypes.POINTER(ctypes.c_void_p)],
 }
 
 
@@ -82,6 +96,8 @@ def lib():
             L.wenozn_status_string.restype = ctypes.c_char_p
             L.wenozn_version.argtypes = []
             L.wenozn_version.restype = ctypes.c_char_p
+            L.wenozn_batch_num_shapes.argtypes = []
+            L.wenozn_batch_num_shapes.restype = ctypes.c_int32
             L.wenozn_workspace_dt.argtypes = [_VP]
             L.wenozn_workspace_dt.restype = _VP
             _lib = L
@@ -268,3 +284,89 @@ class Solver:
 
     def status(self, clear: bool = False) -> int:
         return wenozn_workspace_status(self.ws, clear)
+
+
+# ------------------------------------------------------------------------- batched 1D Euler
+def wenozn_batch_num_shapes() -> int:
+    return lib().wenozn_batch_num_shapes()
+
+
+def wenozn_batch_shape(shape: int):
+    t, th = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check("wenozn_batch_shape", lib().wenozn_batch_shape(int(shape), ctypes.byref(t), ctypes.byref(th)))
+    return t.value, th.value
+
+
+class Batch:
+    """B independent 1D Euler problems in one concatenated state U[3][total] (float64, CUDA),
+    instance b at columns offsets[b]:offsets[b+1] with spacing dx[b]."""
+
+    def __init__(self, offsets, dx, U: torch.Tensor, *, bc=WENOZN_BC_OUTFLOW, shape=-1, t_final=0.0,
+                 gamma=1.4, eps=1e-40, A=10.0, cfl=0.5, device=None):
+        import numpy as np
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.dx = np.ascontiguousarray(dx, dtype=np.float64)
+        B = self.offsets.size - 1
+        if self.dx.size != B:
+            raise ValueError("dx must hold one spacing per instance")
+        self.bp = wenozn_batch_params(B, bc, shape, 0, gamma, eps, A, cfl, t_final)
+        n = ctypes.c_size_t(0)
+        _check("wenozn_batch_workspace_size", lib().wenozn_batch_workspace_size(
+            ctypes.byref(self.bp), self.offsets.ctypes.data, ctypes.byref(n)))
+        ws = torch.zeros(n.value + 256, dtype=torch.uint8, device=device or U.device)
+        off = (-ws.data_ptr()) % 256
+        self.ws = ws[off:off + n.value]
+        self.init(U)
+
+    @property
+    def nbatch(self) -> int:
+        return self.bp.nbatch
+
+    def init(self, U: torch.Tensor, stream=None) -> None:
+        _check("wenozn_batch_init", lib().wenozn_batch_init(
+            ctypes.byref(self.bp), self.offsets.ctypes.data, self.dx.ctypes.data, _dev_ptr(U, "U"),
+            self.ws.data_ptr(), self.ws.numel(), _stream(stream)))
+
+    def step(self, U: torch.Tensor, stream=None) -> None:
+        _check("wenozn_batch_rk3_step", lib().wenozn_batch_rk3_step(
+            ctypes.byref(self.bp), self.offsets.ctypes.data, _dev_ptr(U, "U"), self.ws.data_ptr(),
+            self.ws.numel(), _stream(stream)))
+
+    def tune(self, U_scratch: torch.Tensor, steps: int = 2, stream=None):
+        """Times every compiled tile shape on U_scratch (advanced by the trials) and keeps the
+        fastest; returns the per-shape milliseconds per step."""
+        ms = (ctypes.c_float * wenozn_batch_num_shapes())()
+        _check("wenozn_batch_tune", lib().wenozn_batch_tune(
+            ctypes.byref(self.bp), self.offsets.ctypes.data, _dev_ptr(U_scratch, "U"), self.ws.data_ptr(),
+            self.ws.numel(), int(steps), ms, _stream(stream)))
+        return list(ms)
+
+    def _state_ptrs(self):
+        t, dt, st = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check("wenozn_batch_state", lib().wenozn_batch_state(self.ws.data_ptr(), self.nbatch,
+                                                              self.offsets.ctypes.data, ctypes.byref(t),
+                                                              ctypes.byref(dt), ctypes.byref(st)))
+        return t.value, dt.value, st.value
+
+    def _view(self, addr: int, count: int, dtype) -> torch.Tensor:
+        off = addr - self.ws.data_ptr()
+        return self.ws[off:off + count * torch.empty((), dtype=dtype).element_size()].view(dtype)
+
+    def times(self) -> torch.Tensor:
+        return self._view(self._state_ptrs()[0], self.nbatch, torch.float64)
+
+    def steps_taken(self) -> torch.Tensor:
+        return self._view(self._state_ptrs()[1], self.nbatch, torch.float64)
+
+    def status(self) -> int:
+        torch.cuda.synchronize()
+        return int(self._view(self._state_ptrs()[2], 1, torch.int32).item())
+
+    def capture(self, U: torch.Tensor, steps: int) -> "torch.cuda.CUDAGraph":
+        """A CUDA graph of `steps` RK3 steps of the batch on U (replay with .replay())."""
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            for _ in range(steps):
+                self.step(U)
+        return g
