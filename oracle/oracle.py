@@ -84,6 +84,8 @@ def lib():
                 "oracle_normal_flux": (None, [_D, ctypes.c_int, ctypes.c_double, _D]),
                 "oracle_opcount_rhs": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
                 "oracle_opcount_parts": (None, [ctypes.c_int, _D]),
+                "oracle_rhs_jvp": (None, [_P, _D, _D, _D, _D]),
+                "oracle_rollout_jvp": (None, [_P, _D, _D, ctypes.c_double, ctypes.c_int64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -207,3 +209,18 @@ def opcount_parts(system) -> dict:
     return {"interface": out[0], "cell_per_sweep": out[1], "wavespeed_cell": out[2],
             "difference_cell_per_dir": out[3], "cmp_interface": out[4], "cmp_cell_per_sweep": out[5],
             "cmp_wavespeed_cell": out[6]}
+
+
+def rhs_jvp(P: Problem, U, dU):
+    """(L, J dU) with J the Jacobian of the discrete RHS (forward mode)."""
+    u, du = _f64(U), _f64(dU)
+    L, dL = np.zeros_like(u), np.zeros_like(u)
+    lib().oracle_rhs_jvp(ctypes.byref(P), _ptr(u), _ptr(du), _ptr(L), _ptr(dL))
+    return L, dL
+
+
+def rollout_jvp(P: Problem, U, dU, dt, steps):
+    """`steps` fixed-dt SSP-RK3 steps of U and of the tangent dU; returns (U_T, dU_T)."""
+    u, du = _f64(U).copy(), _f64(dU).copy()
+    lib().oracle_rollout_jvp(ctypes.byref(P), _ptr(u), _ptr(du), float(dt), int(steps))
+    return u, du

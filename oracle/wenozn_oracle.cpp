@@ -74,6 +74,34 @@ template <class T> inline double tod(T x) { return double(x); }
 inline double tod(OpCount x) { return x.v; }
 
 // ---------------------------------------------------------------------------------------
+// Forward-mode dual number (value, derivative along one direction): running the solver on
+// it gives the exact Jacobian-vector product of the discrete scheme.  Conventions at the
+// scheme's non-smooth points: d|x|/dx = 0 at x = 0; a maximum passes the derivative of the
+// selected argument (the first one on ties, i.e. the lowest cell index for the LF speed).
+// ---------------------------------------------------------------------------------------
+struct Dual {
+    double v, d;
+    Dual() : v(0), d(0) {}
+    explicit Dual(double x) : v(x), d(0) {}
+    Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual tsqrt(Dual x) { const double r = std::sqrt(x.v); return Dual(r, x.d / (2.0 * r)); }
+inline double tod(Dual x) { return x.v; }
+template <> inline Dual tabs<Dual>(Dual x) {
+    if (x.v < 0) return -x;
+    if (x.v > 0) return x;
+    return Dual(0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------------------
 // Sec. 2.1 / Sec. 3: one fifth-order reconstruction f^+_{i+1/2} from (f_{i-2},...,f_{i+2}).
 // ---------------------------------------------------------------------------------------
 enum WeightKind { W_ZN = 0, W_Z = 1, W_LINEAR = 2 };
@@ -100,14 +128,18 @@ WenoParts<T> weno5(const T f[5], T eps, T A, int kind) {
         r.IS[1] = cst<T>(13, 12) * a * a + cst<T>(1, 4) * b * b;
     }
     {
-        T a = f0 - T(2) * fp1 + fp2, b = T(3) * f0 - T(4) * fp1 + fp2;
+        // the mirror image of IS_0's one-sided difference, (f_{i+2} - 4 f_{i+1}) + 3 f_i: like
+        // IS_0's it is exactly zero on constant data
+        T a = f0 - T(2) * fp1 + fp2, b = fp2 - T(4) * fp1 + T(3) * f0;
         r.IS[2] = cst<T>(13, 12) * a * a + cst<T>(1, 4) * b * b;
     }
     // Eq. (tau) = Eq. (tao5): tau5 = |IS_0 - IS_2|.
     r.tau5 = tabs(r.IS[0] - r.IS[2]);
     // Eq. (tau8): square of the five-point fourth difference.
     {
-        T d4 = fm2 - T(4) * fm1 + T(6) * f0 - T(4) * fp1 + fp2;
+        // summed symmetrically, (f_{i-2} + f_{i+2}) - 4 (f_{i-1} + f_{i+1}) + 6 f_i, which is
+        // exactly zero on constant data
+        T d4 = (fm2 + fp2) - T(4) * (fm1 + fp1) + T(6) * f0;
         r.tau8 = d4 * d4;
     }
     // Eq. (function): C = A ((IS_0 + IS_2 - tau + eps) / (tau + eps))^2.
@@ -421,6 +453,20 @@ void ssp_rk3(int64_t n, double* U, double dt, RhsFn L) {
     for (int64_t c = 0; c < n; ++c) U[c] = U0[c] / 3.0 + 2.0 / 3.0 * (U2[c] + dt * K[c]);
 }
 
+// The same SSP-RK3 on any scalar type with a fixed step (used by the JVP instantiation).
+template <class T>
+void ssp_rk3_fixed(const Problem& P, std::vector<T>& U, double dt_d) {
+    const size_t n = U.size();
+    const T dt(dt_d);
+    std::vector<T> U0(U), U1(n), U2(n), K(n);
+    rhs<T>(P, U0.data(), K.data());
+    for (size_t c = 0; c < n; ++c) U1[c] = U0[c] + dt * K[c];
+    rhs<T>(P, U1.data(), K.data());
+    for (size_t c = 0; c < n; ++c) U2[c] = T(0.75) * U0[c] + T(0.25) * (U1[c] + dt * K[c]);
+    rhs<T>(P, U2.data(), K.data());
+    for (size_t c = 0; c < n; ++c) U[c] = U0[c] / T(3.0) + T(2.0) / T(3.0) * (U2[c] + dt * K[c]);
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -646,6 +692,25 @@ void oracle_opcount_parts(int system, double* out) {
     OpCount d = -((F[0] - F[0]) / OpCount(0.1));
     (void)d;
     out[3] = total(g_tally) * nv; out[7] = 0.0; out[8] = 0.0;
+}
+
+// Jacobian-vector products of the discrete scheme (forward mode, Dual scalars).
+// rhs: L = rhs(U), dL = J(U) dU (the LF speed differentiated through its argmax cell).
+void oracle_rhs_jvp(const Problem* P, const double* U, const double* dU, double* L, double* dL) {
+    const int64_t n = int64_t(nvar_of(P->system)) * P->nx * P->ny;
+    std::vector<Dual> u(n), l(n);
+    for (int64_t c = 0; c < n; ++c) u[c] = Dual(U[c], dU[c]);
+    rhs<Dual>(*P, u.data(), l.data());
+    for (int64_t c = 0; c < n; ++c) { L[c] = l[c].v; dL[c] = l[c].d; }
+}
+
+// `steps` SSP-RK3 steps with the fixed step dt, in place for U and the tangent dU.
+void oracle_rollout_jvp(const Problem* P, double* U, double* dU, double dt, int64_t steps) {
+    const int64_t n = int64_t(nvar_of(P->system)) * P->nx * P->ny;
+    std::vector<Dual> u(n);
+    for (int64_t c = 0; c < n; ++c) u[c] = Dual(U[c], dU[c]);
+    for (int64_t k = 0; k < steps; ++k) ssp_rk3_fixed<Dual>(*P, u, dt);
+    for (int64_t c = 0; c < n; ++c) { U[c] = u[c].v; dU[c] = u[c].d; }
 }
 
 }  // extern "C"
