@@ -170,6 +170,32 @@ const double* wenozn_workspace_dt(const void* ws);
 wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Discrete adjoint of the 1D systems (advection and 1D Euler; 2D returns WENOZN_EINVAL).
+ * Vector-Jacobian products of the scheme as implemented, with these conventions at its
+ * non-smooth points: the global LF speed alpha = max_i(|u_i| + c_i) is differentiated
+ * through its argmax cell (the lowest index on ties), d|x|/dx = 0 at x = 0 (in |u| and in
+ * tau5 = |IS_0 - IS_2| of Eq. (tau)), and the time step of an RK3 step is a fixed input.
+ * --------------------------------------------------------------------------------------- */
+
+/* Workspace bytes of wenozn_rhs_vjp / wenozn_rk3_step_vjp: the forward workspace of
+ * wenozn_workspace_size followed by per-interface cotangent contributions ([n+1][6][nvar]),
+ * per-block partial sums, an index and two state-sized cotangent vectors.  A workspace of
+ * this size also serves wenozn_rhs and wenozn_rk3_step. */
+wenozn_status wenozn_vjp_workspace_size(const wenozn_problem* p, size_t* bytes);
+
+/* out = J(U)^T lam with J the Jacobian of the RHS of Eq. (2) (LF splitting, Roe-averaged
+ * characteristic fields, WENO-ZN), including the dependence through alpha.
+ *   U, lam, out : device, [nvar][nx]; out must not overlap U or lam.  Deterministic. */
+wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const double* lam, double* out,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Reverse of one SSP-RK3 step with the fixed step dt > 0 (the forward step being
+ * wenozn_rk3_step(p, U, dt, 0, ...)): on entry lam is the cotangent of U^{n+1}, on exit the
+ * cotangent of U^n = U.  The stage inputs U^(1), U^(2) are recomputed from U inside. */
+wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, double dt, double* lam, void* ws,
+                                  size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Batched 1D Euler: B independent problems of uneven size (the 1D Euler set-up of Sec. 4.3,
  * each with its own grid), advanced together by one persistent kernel launch per RK stage.
  *

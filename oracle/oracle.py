@@ -85,6 +85,8 @@ def lib():
                 "oracle_opcount_rhs": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
                 "oracle_opcount_parts": (None, [ctypes.c_int, _D]),
                 "oracle_rhs_jvp": (None, [_P, _D, _D, _D, _D]),
+                "oracle_rhs_jvp_quad": (None, [_P, _D, _D, _D, _D]),
+                "oracle_rollout_jvp_quad": (None, [_P, _D, _D, ctypes.c_double, ctypes.c_int64]),
                 "oracle_rollout_jvp": (None, [_P, _D, _D, ctypes.c_double, ctypes.c_int64]),
             }
             for name, (res, args) in sig.items():
@@ -219,8 +221,23 @@ def rhs_jvp(P: Problem, U, dU):
     return L, dL
 
 
+def rhs_jvp_quad(P: Problem, U, dU):
+    """rhs_jvp evaluated in binary128 (inputs and outputs rounded to double)."""
+    u, du = _f64(U), _f64(dU)
+    L, dL = np.zeros_like(u), np.zeros_like(u)
+    lib().oracle_rhs_jvp_quad(ctypes.byref(P), _ptr(u), _ptr(du), _ptr(L), _ptr(dL))
+    return L, dL
+
+
 def rollout_jvp(P: Problem, U, dU, dt, steps):
     """`steps` fixed-dt SSP-RK3 steps of U and of the tangent dU; returns (U_T, dU_T)."""
     u, du = _f64(U).copy(), _f64(dU).copy()
     lib().oracle_rollout_jvp(ctypes.byref(P), _ptr(u), _ptr(du), float(dt), int(steps))
+    return u, du
+
+
+def rollout_jvp_quad(P: Problem, U, dU, dt, steps):
+    """rollout_jvp evaluated in binary128 (inputs and outputs rounded to double)."""
+    u, du = _f64(U).copy(), _f64(dU).copy()
+    lib().oracle_rollout_jvp_quad(ctypes.byref(P), _ptr(u), _ptr(du), float(dt), int(steps))
     return u, du

@@ -79,27 +79,49 @@ inline double tod(OpCount x) { return x.v; }
 // scheme's non-smooth points: d|x|/dx = 0 at x = 0; a maximum passes the derivative of the
 // selected argument (the first one on ties, i.e. the lowest cell index for the LF speed).
 // ---------------------------------------------------------------------------------------
-struct Dual {
-    double v, d;
-    Dual() : v(0), d(0) {}
-    explicit Dual(double x) : v(x), d(0) {}
-    Dual(double x, double dx) : v(x), d(dx) {}
-};
-inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
-inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
-inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
-inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
-inline Dual tsqrt(Dual x) { const double r = std::sqrt(x.v); return Dual(r, x.d / (2.0 * r)); }
-inline double tod(Dual x) { return x.v; }
-template <> inline Dual tabs<Dual>(Dual x) {
-    if (x.v < 0) return -x;
-    if (x.v > 0) return x;
-    return Dual(0.0, 0.0);
+template <class S> inline S sqrt_of(S x);
+template <> inline double sqrt_of<double>(double x) { return std::sqrt(x); }
+// binary128 square root: two Newton steps from the double one (quadratic convergence)
+template <> inline Quad sqrt_of<Quad>(Quad x) {
+    if (!(x > 0)) return Quad(0);
+    Quad r = Quad(std::sqrt(double(x)));
+    r = (r + x / r) / Quad(2);
+    r = (r + x / r) / Quad(2);
+    return r;
 }
+
+template <class S> struct DualT {
+    S v, d;
+    DualT() : v(0), d(0) {}
+    explicit DualT(S x) : v(x), d(0) {}
+    DualT(S x, S dx) : v(x), d(dx) {}
+};
+template <class S> inline DualT<S> operator+(DualT<S> a, DualT<S> b) { return DualT<S>(a.v + b.v, a.d + b.d); }
+template <class S> inline DualT<S> operator-(DualT<S> a, DualT<S> b) { return DualT<S>(a.v - b.v, a.d - b.d); }
+template <class S> inline DualT<S> operator*(DualT<S> a, DualT<S> b) {
+    return DualT<S>(a.v * b.v, a.d * b.v + a.v * b.d);
+}
+template <class S> inline DualT<S> operator/(DualT<S> a, DualT<S> b) {
+    return DualT<S>(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+template <class S> inline DualT<S> operator-(DualT<S> a) { return DualT<S>(-a.v, -a.d); }
+template <class S> inline bool operator<(DualT<S> a, DualT<S> b) { return a.v < b.v; }
+template <class S> inline bool operator>(DualT<S> a, DualT<S> b) { return a.v > b.v; }
+template <class S> inline DualT<S>& operator+=(DualT<S>& a, DualT<S> b) { a = a + b; return a; }
+template <class S> inline DualT<S> tsqrt(DualT<S> x) {
+    const S r = sqrt_of<S>(x.v);
+    return DualT<S>(r, x.d / (S(2) * r));
+}
+template <class S> inline double tod(DualT<S> x) { return double(x.v); }
+template <class S> inline DualT<S> tabs_dual(DualT<S> x) {
+    if (x.v < S(0)) return -x;
+    if (x.v > S(0)) return x;
+    return DualT<S>(S(0), S(0));
+}
+typedef DualT<double> Dual;
+typedef DualT<Quad> DualQ;
+template <> inline Dual tabs<Dual>(Dual x) { return tabs_dual(x); }
+template <> inline DualQ tabs<DualQ>(DualQ x) { return tabs_dual(x); }
 
 // ---------------------------------------------------------------------------------------
 // Sec. 2.1 / Sec. 3: one fifth-order reconstruction f^+_{i+1/2} from (f_{i-2},...,f_{i+2}).
@@ -457,7 +479,7 @@ void ssp_rk3(int64_t n, double* U, double dt, RhsFn L) {
 template <class T>
 void ssp_rk3_fixed(const Problem& P, std::vector<T>& U, double dt_d) {
     const size_t n = U.size();
-    const T dt(dt_d);
+    const T dt{dt_d};
     std::vector<T> U0(U), U1(n), U2(n), K(n);
     rhs<T>(P, U0.data(), K.data());
     for (size_t c = 0; c < n; ++c) U1[c] = U0[c] + dt * K[c];
@@ -704,6 +726,16 @@ void oracle_rhs_jvp(const Problem* P, const double* U, const double* dU, double*
     for (int64_t c = 0; c < n; ++c) { L[c] = l[c].v; dL[c] = l[c].d; }
 }
 
+// The same product evaluated in binary128 (reference derivative where the double one is
+// ill-conditioned, e.g. at IS_0 ~ IS_2 where the derivative of C divides by (tau5 + eps)^2).
+void oracle_rhs_jvp_quad(const Problem* P, const double* U, const double* dU, double* L, double* dL) {
+    const int64_t n = int64_t(nvar_of(P->system)) * P->nx * P->ny;
+    std::vector<DualQ> u(n), l(n);
+    for (int64_t c = 0; c < n; ++c) u[c] = DualQ(Quad(U[c]), Quad(dU[c]));
+    rhs<DualQ>(*P, u.data(), l.data());
+    for (int64_t c = 0; c < n; ++c) { L[c] = double(l[c].v); dL[c] = double(l[c].d); }
+}
+
 // `steps` SSP-RK3 steps with the fixed step dt, in place for U and the tangent dU.
 void oracle_rollout_jvp(const Problem* P, double* U, double* dU, double dt, int64_t steps) {
     const int64_t n = int64_t(nvar_of(P->system)) * P->nx * P->ny;
@@ -711,6 +743,15 @@ void oracle_rollout_jvp(const Problem* P, double* U, double* dU, double dt, int6
     for (int64_t c = 0; c < n; ++c) u[c] = Dual(U[c], dU[c]);
     for (int64_t k = 0; k < steps; ++k) ssp_rk3_fixed<Dual>(*P, u, dt);
     for (int64_t c = 0; c < n; ++c) { U[c] = u[c].v; dU[c] = u[c].d; }
+}
+
+// The same rollout derivative in binary128.
+void oracle_rollout_jvp_quad(const Problem* P, double* U, double* dU, double dt, int64_t steps) {
+    const int64_t n = int64_t(nvar_of(P->system)) * P->nx * P->ny;
+    std::vector<DualQ> u(n);
+    for (int64_t c = 0; c < n; ++c) u[c] = DualQ(Quad(U[c]), Quad(dU[c]));
+    for (int64_t k = 0; k < steps; ++k) ssp_rk3_fixed<DualQ>(*P, u, dt);
+    for (int64_t c = 0; c < n; ++c) { U[c] = double(u[c].v); dU[c] = double(u[c].d); }
 }
 
 }  // extern "C"

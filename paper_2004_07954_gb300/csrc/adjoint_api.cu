@@ -1,0 +1,124 @@
+// C ABI of the discrete adjoint (declarations and contracts in include/wenozn.h).
+#include "host_common.h"
+
+using namespace wz;
+
+namespace {
+
+VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
+    VjpArgs v;
+    std::memset(&v, 0, sizeof v);
+    v.C = reinterpret_cast<double*>(ws_base(ws) + L.C);
+    v.partial = reinterpret_cast<double*>(ws_base(ws) + L.partial);
+    v.argmax = reinterpret_cast<int*>(ws_base(ws) + L.argmax);
+    v.n = p.nx;
+    v.bc = p.bc_x;
+    v.nblocks = vjp_interface_blocks(p.nx);
+    v.rdx = 1.0 / p.dx;
+    v.gamma = p.gamma;
+    v.eps4 = 4.0 * p.eps;
+    v.A4 = 0.25 * p.A;
+    v.adv_speed = p.adv_speed;
+    return v;
+}
+
+wenozn_status check_vjp(const wenozn_problem* p, void* ws, size_t ws_bytes, Layout* L) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (p->system == WENOZN_EULER_2D) return WENOZN_EINVAL;     // the adjoint covers the 1D systems
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    *L = layout_of(*p);
+    if (ws_bytes < L->total_vjp) return WENOZN_ENOMEM_WS;
+    return WENOZN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wenozn_status wenozn_vjp_workspace_size(const wenozn_problem* p, size_t* bytes) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!bytes || p->system == WENOZN_EULER_2D) return WENOZN_EINVAL;
+    *bytes = layout_of(*p).total_vjp;
+    return WENOZN_OK;
+}
+
+wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const double* lam, double* out,
+                             void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    wenozn_status st = check_vjp(p, ws, ws_bytes, &L);
+    if (st != WENOZN_OK) return st;
+    if (!U || !lam || !out || out == U || out == lam) return WENOZN_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + L.ctrl);
+    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
+    if (e == cudaSuccess) {
+        VjpArgs v = vjp_args(*p, L, ws);
+        v.U = U;
+        v.lam = lam;
+        v.alpha_bits = ctrl->alpha[0];
+        v.out = out;
+        v.d = 1.0;
+        e = launch_vjp(p->system, v, s);
+    }
+    return cuda_status(e);
+}
+
+wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, double dt, double* lam, void* ws,
+                                  size_t ws_bytes, void* stream) {
+    Layout L;
+    wenozn_status st = check_vjp(p, ws, ws_bytes, &L);
+    if (st != WENOZN_OK) return st;
+    if (!U || !lam || U == lam || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + L.ctrl);
+    double* u1 = reinterpret_cast<double*>(ws_base(ws) + L.u1);
+    double* u2 = reinterpret_cast<double*>(ws_base(ws) + L.u2);
+    double* fx = reinterpret_cast<double*>(ws_base(ws) + L.fx);
+    double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
+    double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
+    const bool euler = p->system != WENOZN_ADVECTION_1D;
+
+    // recompute the stage inputs U1, U2 of the forward step (same kernels, fixed dt)
+    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
+    const double* stage_in[2] = {U, u1};
+    double* stage_out[2] = {u1, u2};
+    for (int stage = 0; stage < 2 && e == cudaSuccess; ++stage) {
+        e = launch_fluxes(*p, stage_in[stage], ctrl->alpha[stage], fx, nullptr, s);
+        if (e != cudaSuccess) break;
+        UpdateArgs u = update_args(*p, ctrl, fx, nullptr);
+        u.mode = stage + 1;
+        u.Us = stage_in[stage];
+        u.Un = U;
+        u.out = stage_out[stage];
+        u.next_slot = euler ? stage + 1 : -1;
+        u.dt_fixed = dt;
+        e = launch_update(p->system, u, s);
+    }
+    // reverse of U3 = U0/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)),
+    // U1 = U0 + dt L(U0)
+    VjpArgs v = vjp_args(*p, L, ws);
+    if (e == cudaSuccess) {                 // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
+        v.U = u2; v.lam = lam; v.alpha_bits = ctrl->alpha[2]; v.out = ub2;
+        v.X1 = lam; v.c1 = 2.0 / 3.0; v.d = (2.0 / 3.0) * dt;
+        e = launch_vjp(p->system, v, s);
+    }
+    if (e == cudaSuccess) {                 // Ub1 = 1/4 Ub2 + 1/4 dt J(U1)^T Ub2
+        v.U = u1; v.lam = ub2; v.alpha_bits = ctrl->alpha[1]; v.out = ub1;
+        v.X1 = ub2; v.c1 = 0.25; v.d = 0.25 * dt;
+        e = launch_vjp(p->system, v, s);
+    }
+    if (e == cudaSuccess) {                 // lam <- lam/3 + 3/4 Ub2 + Ub1 + dt J(U0)^T Ub1
+        v.U = U; v.lam = ub1; v.alpha_bits = ctrl->alpha[0]; v.out = lam;
+        v.X1 = lam; v.c1 = 1.0 / 3.0; v.X2 = ub2; v.c2 = 0.75; v.X3 = ub1; v.c3 = 1.0; v.d = dt;
+        e = launch_vjp(p->system, v, s);
+    }
+    return cuda_status(e);
+}
+
+}  // extern "C"

@@ -3,103 +3,10 @@
 #include <cmath>
 #include <cstring>
 
-#include "../../include/wenozn.h"
-#include "launch.h"
+#include "host_common.h"
 
 using namespace wz;
 
-namespace {
-
-constexpr size_t kAlign = 256;
-
-size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-int nvar_of(int system) { return system == WENOZN_ADVECTION_1D ? 1 : (system == WENOZN_EULER_1D ? 3 : 4); }
-
-struct Layout {
-    size_t ctrl, u1, u2, fx, gy, total;
-};
-
-Layout layout_of(const wenozn_problem& p) {
-    const size_t nv = size_t(nvar_of(p.system));
-    const size_t nx = size_t(p.nx), ny = size_t(p.ny);
-    Layout L;
-    L.ctrl = 0;
-    L.u1 = align_up(sizeof(Ctrl));
-    L.u2 = L.u1 + align_up(nv * nx * ny * sizeof(double));
-    L.fx = L.u2 + align_up(nv * nx * ny * sizeof(double));
-    L.gy = L.fx + align_up(nv * (nx + 1) * ny * sizeof(double));
-    L.total = L.gy + (p.system == WENOZN_EULER_2D ? align_up(nv * nx * (ny + 1) * sizeof(double)) : 0);
-    return L;
-}
-
-bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
-
-wenozn_status check_problem(const wenozn_problem* p) {
-    if (!p) return WENOZN_EINVAL;
-    if (p->system < 0 || p->system > 2 || p->flags != 0) return WENOZN_EINVAL;
-    const bool two_d = p->system == WENOZN_EULER_2D;
-    if (p->nx < 1 || p->nx > (1 << 30)) return WENOZN_EINVAL;
-    if (two_d ? (p->ny < 1 || p->ny > (1 << 30)) : p->ny != 1) return WENOZN_EINVAL;
-    if (int64_t(p->nx) * p->ny > (int64_t(1) << 34)) return WENOZN_EINVAL;
-    if ((p->bc_x != WENOZN_BC_PERIODIC && p->bc_x != WENOZN_BC_OUTFLOW)) return WENOZN_EINVAL;
-    if (two_d && p->bc_y != WENOZN_BC_PERIODIC && p->bc_y != WENOZN_BC_OUTFLOW) return WENOZN_EINVAL;
-    if (!finite_pos(p->dx) || (two_d && !finite_pos(p->dy))) return WENOZN_EINVAL;
-    if (!finite_pos(p->eps) || !std::isfinite(p->A) || p->A < 0.0 || !finite_pos(p->cfl)) return WENOZN_EINVAL;
-    if (p->system == WENOZN_ADVECTION_1D) {
-        if (!std::isfinite(p->adv_speed) || p->adv_speed == 0.0) return WENOZN_EINVAL;
-    } else if (!std::isfinite(p->gamma) || p->gamma <= 1.0) {
-        return WENOZN_EINVAL;
-    }
-    return WENOZN_OK;
-}
-
-wenozn_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WENOZN_OK : WENOZN_ECUDA; }
-
-// Launches the x (and y) flux kernels for stage input U with LF speeds in `alpha_bits`.
-cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const unsigned long long* alpha_bits,
-                          double* fx, double* gy, cudaStream_t s) {
-    FluxArgs fa;
-    fa.U = U;
-    fa.alpha_bits = alpha_bits;
-    fa.nx = p.nx;
-    fa.ny = p.ny;
-    fa.eps4 = 4.0 * p.eps;
-    fa.A4 = 0.25 * p.A;
-    fa.fast_rcp = zn_fast_rcp(p.eps, p.A);
-    fa.gamma = p.gamma;
-    fa.adv_speed = p.adv_speed;
-    fa.Fout = fx;
-    fa.bc = p.bc_x;
-    cudaError_t e = launch_flux(p.system, 0, fa, s);
-    if (e != cudaSuccess || p.system != WENOZN_EULER_2D) return e;
-    fa.Fout = gy;
-    fa.bc = p.bc_y;
-    return launch_flux(p.system, 1, fa, s);
-}
-
-UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double* fx, const double* gy) {
-    UpdateArgs u;
-    std::memset(&u, 0, sizeof u);
-    u.Fx = fx;
-    u.Gy = gy;
-    u.nx = p.nx;
-    u.ny = p.ny;
-    u.rdx = 1.0 / p.dx;
-    u.rdy = p.system == WENOZN_EULER_2D ? 1.0 / p.dy : 0.0;
-    u.ctrl = ctrl;
-    u.next_slot = -1;
-    u.cfl = p.cfl;
-    u.dx = p.dx;
-    u.dy = p.dy;
-    u.gamma = p.gamma;
-    u.adv_speed = p.adv_speed;
-    return u;
-}
-
-char* ws_base(void* ws) { return static_cast<char*>(ws); }
-
-}  // namespace
 
 extern "C" {
 

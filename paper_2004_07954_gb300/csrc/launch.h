@@ -74,6 +74,25 @@ cudaError_t batch_configure();
 cudaError_t launch_batch_init(const BatchArgs& a, cudaStream_t s);
 cudaError_t launch_batch_stage(int shape, const BatchArgs& a, int sms, cudaStream_t s);
 
+// Adjoint of the 1D right-hand side (see adjoint_kernels.cu).
+struct VjpArgs {
+    const double* U;                       // stage input, [nv][n]
+    const double* lam;                     // cotangent of L(U), [nv][n]
+    double* C;                             // [n+1][6][nv] per-interface contributions
+    double* partial;                       // [nblocks] partial sums of the LF-speed cotangent
+    int* argmax;                           // lowest index of the LF-speed maximum
+    const unsigned long long* alpha_bits;  // LF speed of U (bit pattern)
+    double* out;                           // c1 X1 + c2 X2 + c3 X3 + d J^T lam
+    const double* X1;
+    const double* X2;
+    const double* X3;
+    double c1, c2, c3, d;
+    int n, bc, nblocks;
+    double rdx, gamma, eps4, A4, adv_speed;
+};
+int vjp_interface_blocks(int n);
+cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
+
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,

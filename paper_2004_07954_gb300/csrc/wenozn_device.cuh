@@ -24,8 +24,11 @@ namespace wz {
 //   Eq. (3)        f^ = sum_k alpha_k q_k / sum_k alpha_k
 //
 // Evaluation (exact algebra; only the rounding differs from the plain order):
-//  * with s_0 = a - 2b + c, s_1 = b - 2c + d, s_2 = c - 2d + e and t_0 = a - 4b + 3c,
-//    t_1 = b - d, t_2 = 3c - 4d + e, the sub-stencil fluxes are
+//  * with the first differences D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e, the second
+//    differences s_0 = D1 - D2, s_1 = D2 - D3, s_2 = D3 - D4 and the one-sided ones
+//    t_0 = D1 - 3 D2 = a - 4b + 3c, t_1 = D2 + D3 = b - d, t_2 = 3 D3 - D4 = 3c - 4d + e (equal
+//    inputs give exact zeros, so constant data keep exactly the linear weights), the
+//    sub-stencil fluxes are
 //    q_k = c + s_k/12 + t_k/4 (k = 0) and c + s_k/12 - t_k/4 (k = 1, 2);
 //  * indicators are carried scaled by 4 together with eps: b_k = 4 (IS_k + eps)
 //    = 13/3 s_k^2 + t_k^2 + 4 eps, so C and tau8/(IS_k + eps) = 4 tau8 / b_k are unchanged;
@@ -48,30 +51,37 @@ struct ZnParts {
 // the cubically convergent series 1/d = r0 (1 + e + e^2 + ...) truncated after e^2
 // (Householder's third-order iteration): the relative error becomes about e^3 ~ 2^-69, so
 // the result is within about one ulp of 1/d.  Used where d is known to be positive and normal.
-__device__ __forceinline__ double rcp_nr(double d) {
+__host__ __device__ __forceinline__ double rcp_nr(double d) {
+#ifdef __CUDA_ARCH__
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
     const double e = fma(-d, r, 1.0);
     return fma(r, fma(e, e, e), r);
+#else
+    return 1.0 / d;
+#endif
 }
 
-__device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double d, double e,
-                                            double eps4, double A4) {
-    const double s0 = fma(-2.0, b, a) + c;
-    const double s1 = fma(-2.0, c, b) + d;
-    const double s2 = fma(-2.0, d, c) + e;
-    const double t0 = fma(3.0, c, fma(-4.0, b, a));
-    const double t1 = b - d;
-    const double t2 = fma(3.0, c, fma(-4.0, d, e));
+__host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double d, double e,
+                                                     double eps4, double A4) {
+    // first differences, then the second (s_k) and one-sided (t_k) differences from them:
+    // equal inputs give exact zeros
+    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+    const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
+    const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
     const double k13_3 = 13.0 / 3.0;
     const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));   // 4 (IS_0 + eps)
     const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
     const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
     const double d4 = t0 + t2;                                  // a - 4b + 6c - 4d + e
     // non-negative doubles order like their bit patterns: min/max on the integer pipe
+#ifdef __CUDA_ARCH__
     const long long i0 = __double_as_longlong(b0), i2 = __double_as_longlong(b2);
     const double mn = __longlong_as_double(i0 < i2 ? i0 : i2);
     const double mx = __longlong_as_double(i0 < i2 ? i2 : i0);
+#else
+    const double mn = b0 < b2 ? b0 : b2, mx = b0 < b2 ? b2 : b0;
+#endif
     const double P = (mx - mn) + eps4;                          // 4 (tau5 + eps)
     const double m = fma(2.0, mn, -eps4);                       // 4 (IS_0 + IS_2 - tau5 + eps)
     const double b01 = b0 * b1, b12 = b1 * b2, b02 = b0 * b2;
@@ -97,8 +107,8 @@ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double
 // f^ = num / den.  With A > 0 and eps >= 1e-60, den >= 10 (A/4) (4 eps)^5 is a positive
 // normal number, so the Newton reciprocal applies (fast_rcp = true, chosen by the host);
 // otherwise the IEEE division is used.
-__device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
-                                          double eps4, double A4, bool fast_rcp) {
+__host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
+                                                   double eps4, double A4, bool fast_rcp) {
     const ZnParts r = zn_parts(a, b, c, d, e, eps4, A4);
     return fast_rcp ? r.num * rcp_nr(r.den) : r.num / r.den;
 }
@@ -176,7 +186,7 @@ __device__ __forceinline__ void block_max2_atomic(double vx, double vy, unsigned
 }
 
 // Ghost-cell index map: periodic wrap or zero-order extrapolation (outflow).
-__device__ __forceinline__ int ghost_src(int g, int n, int bc) {
+__host__ __device__ __forceinline__ int ghost_src(int g, int n, int bc) {
     if (bc == 0) {
         g %= n;
         return g < 0 ? g + n : g;

@@ -17,7 +17,9 @@ Families (each a seeded generalisation of a paper set-up):
   * 2D Euler on [0, 1]^2, four-quadrant Riemann data split at (0.5, 0.5) (Sec. 4.4.1),
     per quadrant rho in [0.1, 1.5], u, v in [-1.2, 1.2], p in [0.03, 1.5];
   * smooth entropy waves (density sine carried by a constant velocity at constant pressure)
-    whose exact solution is the translated profile.
+    whose exact solution is the translated profile;
+  * the adjoint workload: a seeded smooth multi-wave state on the periodic domain [-5, 5]
+    in which density, velocity and pressure all vary (no flat or resting region).
 """
 from __future__ import annotations
 
@@ -158,6 +160,27 @@ def entropy_wave_2d(nx: int, ny: int, t: float = 0.0, u: float = 1.0, v: float =
     X, Y = np.meshgrid(x, y)
     rho = 1.0 + amp * np.sin(np.pi * ((X - u * t) + (Y - v * t)))
     return np.ascontiguousarray(cons_from_prim(rho, u, 1.0, v)), dx, dy
+
+
+def adjoint_params(seed: int) -> dict:
+    g = _rng(seed)
+    # whole waves on the period 10; the first one spans it once, so the state has no
+    # shorter period (no exactly repeated maximum of |u| + c)
+    m = np.concatenate([[1], g.integers(1, 4, size=3)])
+    return {"A": g.uniform(0.1, 0.2), "B": g.uniform(0.05, 0.2), "C": g.uniform(0.05, 0.2),
+            "u0": g.uniform(-0.5, 0.5), "k": 2.0 * np.pi * m / 10.0, "phi": g.uniform(0.0, 2.0 * np.pi, size=4)}
+
+
+def adjoint_ic(n: int, seed: int) -> np.ndarray:
+    """Smooth periodic 1D Euler state on [-5, 5] (cell centres): rho = 1 + A sin(k1 x + p1)
+    + A/2 sin(k2 x + p2), u = u0 + B sin(k3 x + p3), p = 1 + C sin(k4 x + p4)."""
+    q = adjoint_params(seed)
+    x, _ = euler1d_grid(n)
+    k, ph = q["k"], q["phi"]
+    rho = 1.0 + q["A"] * np.sin(k[0] * x + ph[0]) + 0.5 * q["A"] * np.sin(k[1] * x + ph[1])
+    u = q["u0"] + q["B"] * np.sin(k[2] * x + ph[2])
+    p = 1.0 + q["C"] * np.sin(k[3] * x + ph[3])
+    return cons_from_prim(rho, u, p).reshape(3, 1, n).copy()
 
 
 def random_smooth_state(system: int, nx: int, ny: int, seed: int) -> np.ndarray:

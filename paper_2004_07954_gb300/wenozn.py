@@ -68,6 +68,9 @@ _SIGNATURES = {
                         _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
+    "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_batch_shape": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "wenozn_batch_workspace_size": [ctypes.POINTER(wenozn_batch_params), _VP, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_batch_init": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
@@ -249,6 +252,33 @@ def wenozn_workspace_dt(ws: torch.Tensor) -> torch.Tensor:
     addr = lib().wenozn_workspace_dt(_ws_ptr(ws))
     off = addr - ws.data_ptr()
     return ws[off:off + 8].view(torch.float64)
+
+
+def wenozn_vjp_workspace_size(p: wenozn_problem) -> int:
+    n = ctypes.c_size_t(0)
+    _check("wenozn_vjp_workspace_size", lib().wenozn_vjp_workspace_size(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def vjp_workspace(p: wenozn_problem, device=None) -> torch.Tensor:
+    """Zero-filled, 256-byte aligned workspace for the adjoint (and forward) entry points."""
+    nbytes = wenozn_vjp_workspace_size(p)
+    ws = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + nbytes]
+
+
+def wenozn_rhs_vjp(p: wenozn_problem, U: torch.Tensor, lam: torch.Tensor, out: torch.Tensor, ws: torch.Tensor,
+                   stream=None) -> None:
+    _check("wenozn_rhs_vjp", lib().wenozn_rhs_vjp(ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(lam, "lam"),
+                                                  _dev_ptr(out, "out"), _ws_ptr(ws), ws.numel(), _stream(stream)))
+
+
+def wenozn_rk3_step_vjp(p: wenozn_problem, U: torch.Tensor, dt: float, lam: torch.Tensor, ws: torch.Tensor,
+                        stream=None) -> None:
+    _check("wenozn_rk3_step_vjp", lib().wenozn_rk3_step_vjp(ctypes.byref(p), _dev_ptr(U, "U"), float(dt),
+                                                            _dev_ptr(lam, "lam"), _ws_ptr(ws), ws.numel(),
+                                                            _stream(stream)))
 
 
 # ------------------------------------------------------------------------- convenience

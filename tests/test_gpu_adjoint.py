@@ -1,0 +1,157 @@
+"""Discrete adjoint kernels against the oracle's forward-mode derivatives and against
+central finite differences."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_07954_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wz():
+    from paper_2004_07954_gb300 import build, wenozn
+    build.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return wenozn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _problem(wz, orc, system, n, dx, bc):
+    p = wz.wenozn_problem_init(system, n, 1, dx, 1.0, bc_x=bc)
+    P = orc.problem(system, n, 1, dx=dx, bc_x=bc)
+    return p, P
+
+
+def _state(system, n, seed):
+    return inputs.random_smooth_state(system, n, 1, seed)
+
+
+@pytest.mark.parametrize("system,bc,n", [(1, 1, 12), (1, 0, 12), (0, 0, 12), (1, 1, 3), (1, 0, 2), (0, 0, 5),
+                                         (1, 1, 1)])
+def test_rhs_vjp_elementwise_against_oracle_jacobian(wz, orc, system, bc, n):
+    """Full Jacobian of the oracle RHS from forward-mode columns; J^T lam from the GPU
+    (small grids exercise the ghost-cell preimages of the gather)."""
+    p, P = _problem(wz, orc, system, n, 0.1, bc)
+    U = _state(system, n, seed=3)
+    nv = U.shape[0]
+    J = np.zeros((nv * n, nv * n))
+    for col in range(nv * n):
+        e = np.zeros(nv * n)
+        e[col] = 1.0
+        _, dL = orc.rhs_jvp(P, U, e.reshape(U.shape))
+        J[:, col] = dL.ravel()
+    lam = np.random.default_rng(1).normal(size=U.shape)
+    out = torch.empty_like(dev(U))
+    ws = wz.vjp_workspace(p)
+    wz.wenozn_rhs_vjp(p, dev(U), dev(lam), out, ws)
+    want = (J.T @ lam.ravel()).reshape(U.shape)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("system,n,bc", [(1, 300, 1), (1, 257, 0), (0, 500, 0), (1, 4099, 1)])
+def test_rhs_vjp_dot_product(wz, orc, system, n, bc):
+    p, P = _problem(wz, orc, system, n, 10.0 / n, bc)
+    U = inputs.euler1d_ic(n, seed=4) if system == 1 else _state(0, n, 4)
+    g = np.random.default_rng(2)
+    ws = wz.vjp_workspace(p)
+    for _ in range(3):
+        v, lam = g.normal(size=U.shape), g.normal(size=U.shape)
+        # binary128 reference: the double forward-mode derivative of C divides by
+        # (tau5 + eps)^2 and loses digits where IS_0 ~ IS_2 (e.g. the exact antisymmetry of
+        # the sine profile about x = 0, a cell centre for n = 257 and n = 4099)
+        _, Jv = orc.rhs_jvp_quad(P, U, v)
+        out = torch.empty_like(dev(U))
+        wz.wenozn_rhs_vjp(p, dev(U), dev(lam), out, ws)
+        a, b = float(np.sum(lam * Jv)), float(np.sum(out.cpu().numpy() * v))
+        assert b == pytest.approx(a, rel=1e-10, abs=1e-12 * np.abs(lam).sum() * np.abs(Jv).max())
+
+
+@pytest.mark.parametrize("system,bc", [(1, 0), (1, 1), (0, 0)])
+def test_rk3_step_vjp_dot_product(wz, orc, system, bc):
+    """One RK3 step of the smooth adjoint workload (no rounding-flat fields, whose exact
+    tangent is noise-driven with eps = 1e-40)."""
+    n = 240
+    p, P = _problem(wz, orc, system, n, 10.0 / n, bc)
+    U = inputs.adjoint_ic(n, seed=6) if system == 1 else _state(0, n, 6)
+    dt = 0.4 * p.dx / (orc.max_wavespeed(P, U) if system == 1 else 1.0)
+    g = np.random.default_rng(3)
+    ws = wz.vjp_workspace(p)
+    for _ in range(3):
+        v, lam = g.normal(size=U.shape), g.normal(size=U.shape)
+        _, Jv = orc.rollout_jvp_quad(P, U, v, dt, 1)      # binary128 reference (see above)
+        l = dev(lam)
+        wz.wenozn_rk3_step_vjp(p, dev(U), dt, l, ws)
+        a, b = float(np.sum(lam * Jv)), float(np.sum(l.cpu().numpy() * v))
+        assert b == pytest.approx(a, rel=1e-10)
+
+
+def _loss_grad(wz, p, U0, dt, steps, target, every=1):
+    from paper_2004_07954_gb300.rollout import rollout
+    U = dev(U0).requires_grad_(True)
+    UT = rollout(U, p, dt, steps, checkpoint_every=every)
+    loss = 0.5 * ((UT[0] - target) ** 2).sum()
+    (g,) = torch.autograd.grad(loss, U)
+    return float(loss.item()), g.cpu().numpy()
+
+
+def test_rollout_gradient_against_oracle_jvp(wz, orc):
+    """Adjoint of a 30-step rollout of the smooth adjoint workload against the oracle's
+    forward-mode derivative (the CPU reference gradient along seeded directions)."""
+    n, steps = 200, 30
+    p, P = _problem(wz, orc, 1, n, 10.0 / n, 0)
+    U0 = inputs.adjoint_ic(n, seed=7)
+    dt = 0.5 * p.dx / orc.max_wavespeed(P, U0)
+    target = dev(inputs.adjoint_ic(n, seed=8)[0])
+    loss, grad = _loss_grad(wz, p, U0, dt, steps, target)
+    UT, _ = orc.rollout_jvp(P, U0, np.zeros_like(U0), dt, steps)
+    resid = UT[0] - target.cpu().numpy()
+    g = np.random.default_rng(4)
+    for _ in range(5):
+        v = g.normal(size=U0.shape)
+        _, dUT = orc.rollout_jvp_quad(P, U0, v, dt, steps)
+        want = float(np.sum(resid * dUT[0]))
+        assert float(np.sum(grad * v)) == pytest.approx(want, rel=1e-8)
+
+
+def test_rollout_gradient_against_central_fd(wz, orc):
+    """Central differences (h = 1e-7) of the GPU forward on seeded directions."""
+    from paper_2004_07954_gb300.rollout import rollout
+    n, steps, h = 512, 200, 1e-7
+    p, P = _problem(wz, orc, 1, n, 10.0 / n, 0)
+    U0 = inputs.adjoint_ic(n, seed=9)
+    dt = 0.5 * p.dx / orc.max_wavespeed(P, U0)
+    target = dev(inputs.adjoint_ic(n, seed=10)[0])
+    _, grad = _loss_grad(wz, p, U0, dt, steps, target)
+
+    def loss_at(U):
+        with torch.no_grad():
+            UT = rollout(dev(U), p, dt, steps)
+            return 0.5 * float(((UT[0] - target) ** 2).sum().item())
+    g = np.random.default_rng(11)
+    for _ in range(6):
+        v = g.normal(size=U0.shape) * np.abs(U0)          # relative perturbation direction
+        fd = (loss_at(U0 + h * v) - loss_at(U0 - h * v)) / (2 * h)
+        assert float(np.sum(grad * v)) == pytest.approx(fd, rel=1e-6)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(wz, orc):
+    n, steps = 256, 23
+    p, P = _problem(wz, orc, 1, n, 10.0 / n, 0)
+    U0 = inputs.adjoint_ic(n, seed=12)
+    dt = 0.5 * p.dx / orc.max_wavespeed(P, U0)
+    target = dev(inputs.adjoint_ic(n, seed=13)[0])
+    _, g1 = _loss_grad(wz, p, U0, dt, steps, target, every=1)
+    _, g7 = _loss_grad(wz, p, U0, dt, steps, target, every=7)
+    _, g50 = _loss_grad(wz, p, U0, dt, steps, target, every=50)
+    assert np.array_equal(g1, g7) and np.array_equal(g1, g50)
+
+
+def test_vjp_rejects_2d(wz):
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 8, 8, 0.1, 0.1)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_vjp_workspace_size(p)

@@ -213,3 +213,48 @@ def test_cfl_dt_definitions(orc):
     assert orc.max_wavespeed(P, U, 0) == ax and orc.max_wavespeed(P, U, 1) == ay
     tx, ty = (1 / 8) / ax, (1 / 6) / ay
     assert orc.cfl_dt(P, U) == pytest.approx(0.5 * tx * ty / (tx + ty), rel=1e-15)
+
+
+# ------------------------------------------------------------------ derivatives (adjoint reference)
+@pytest.mark.parametrize("system,bc", [(1, 1), (1, 0), (2, 1), (0, 0)])
+def test_oracle_jvp_matches_central_differences(orc, system, bc):
+    """The forward-mode derivative of the discrete RHS against central differences of the
+    oracle's own RHS on generic data (no flat fields, no ties)."""
+    nx, ny = (30, 1) if system != 2 else (9, 8)
+    U = inputs.random_smooth_state(system, nx, ny, seed=21)
+    P = orc.problem(system, nx, ny, dx=0.1, dy=0.1, bc_x=bc, bc_y=bc)
+    v = np.random.default_rng(4).normal(size=U.shape)
+    _, dL = orc.rhs_jvp(P, U, v)
+    h = 1e-6
+    fd = (orc.rhs(P, U + h * v) - orc.rhs(P, U - h * v)) / (2 * h)
+    assert np.abs(fd - dL).max() <= 1e-6 * np.abs(dL).max()
+    _, dLq = orc.rhs_jvp_quad(P, U, v)
+    assert np.abs(dLq - dL).max() <= 1e-10 * np.abs(dL).max()
+
+
+def test_oracle_rollout_jvp_matches_central_differences(orc):
+    n, steps = 128, 40
+    U0 = inputs.adjoint_ic(n, seed=3)
+    P = orc.problem(orc.EULER1D, n, 1, dx=10.0 / n, bc_x=orc.PERIODIC)
+    dt = 0.5 * P.dx / orc.max_wavespeed(P, U0)
+    v = np.random.default_rng(5).normal(size=U0.shape) * np.abs(U0)
+    _, dU = orc.rollout_jvp(P, U0, v, dt, steps)
+    h = 1e-7
+    up, _ = orc.rollout_jvp(P, U0 + h * v, np.zeros_like(v), dt, steps)
+    um, _ = orc.rollout_jvp(P, U0 - h * v, np.zeros_like(v), dt, steps)
+    fd = (up - um) / (2 * h)
+    assert np.abs(fd - dU).max() <= 1e-6 * np.abs(dU).max()
+
+
+def test_rounding_flat_fields_make_the_exact_tangent_explode(orc):
+    """Documented property of the scheme with eps = 1e-40: in the resting region of the
+    Shu-Osher-type family the velocity is rounding noise after one step, the acoustic
+    characteristic fields are flat to rounding and their weights are set by that noise, so
+    the exact tangent of the discrete map grows by orders of magnitude per step."""
+    n = 256
+    U = inputs.euler1d_ic(n, seed=9)
+    P = orc.problem(orc.EULER1D, n, 1, dx=10.0 / n, bc_x=orc.OUTFLOW)
+    dt = 0.5 * P.dx / orc.max_wavespeed(P, U)
+    v = np.random.default_rng(11).normal(size=U.shape) * np.abs(U)
+    _, dU = orc.rollout_jvp(P, U, v, dt, 20)
+    assert np.abs(dU).max() > 1e15
