@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-fd-dirs", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
 
@@ -201,6 +203,83 @@ def bench_batched(wenozn, inputs, seed: int, K: int, B: int = 2048) -> dict:
                                       "speedup_vs_eager": round(eager_ms / ms_step, 1),
                                       "speedup_vs_graph": round(graph_ms / ms_step, 2)},
             "device_status": status}
+
+
+def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, fd_dirs: int = 20) -> dict:
+    """Discrete adjoint of a fixed-step rollout of the 1D Euler equations: loss
+    1/2 ||rho(T) - rho_target||^2, gradient with respect to the initial conserved state.
+    Times the forward rollout, the adjoint with every state kept and with a checkpoint
+    every 50 steps, and checks the gradient against central differences (h = 1e-7) of the
+    GPU forward along `fd_dirs` seeded directions."""
+    import numpy as np
+    import torch
+    from paper_2004_07954_gb300.rollout import cfl_step, rollout
+    p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_1D, n, 1, 10.0 / n, 1.0, bc_x=wenozn.WENOZN_BC_PERIODIC)
+    ws = wenozn.vjp_workspace(p)
+    U0 = torch.from_numpy(inputs.adjoint_ic(n, seed)).cuda()
+    dt = cfl_step(p, U0)
+    with torch.no_grad():
+        target = rollout(torch.from_numpy(inputs.adjoint_ic(n, seed + 1)).cuda(), p, dt, steps, ws=ws)[0].clone()
+
+    def fwd_only(U):
+        U = U.clone()
+        for _ in range(steps):
+            wenozn.wenozn_rk3_step(p, U, ws, dt=dt)
+        return U
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    fwd_only(U0)
+    _, t_fwd = timed(lambda: fwd_only(U0))
+    res = {}
+    for every in (1, 50):
+        def fwd_bwd():
+            U = U0.clone().requires_grad_(True)
+            UT = rollout(U, p, dt, steps, checkpoint_every=every, ws=ws)
+            loss = 0.5 * ((UT[0] - target) ** 2).sum()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            (g,) = torch.autograd.grad(loss, U)
+            torch.cuda.synchronize()
+            return g, loss, time.perf_counter() - t1
+        fwd_bwd()
+        (g, loss, t_bwd), t_all = timed(fwd_bwd)
+        res[every] = {"forward_with_checkpoints_s": round(t_all - t_bwd, 4), "adjoint_s": round(t_bwd, 4),
+                      "adjoint_over_forward": round(t_bwd / t_fwd, 3)}
+    grad = g.cpu().numpy()
+    u0 = U0.cpu().numpy()
+    gen = np.random.default_rng(seed + 7)
+    h = 1e-7
+    x = (np.arange(n) + 0.5) * (10.0 / n) - 5.0
+    checks = {}
+    with torch.no_grad():
+        for kind in ("smooth", "white"):
+            worst = 0.0
+            for _ in range(fd_dirs):
+                if kind == "smooth":      # a few random Fourier modes per variable, scaled like U0
+                    v = np.zeros_like(u0)
+                    for k in range(3):
+                        for m in range(1, 5):
+                            v[k, 0] += gen.normal() * np.sin(2 * np.pi * m * x / 10 + gen.uniform(0, 2 * np.pi))
+                        v[k, 0] *= np.abs(u0[k, 0]).mean()
+                else:
+                    v = gen.normal(size=u0.shape) * np.abs(u0)
+                vt = torch.from_numpy(v).cuda()
+                lp = 0.5 * float(((fwd_only(U0 + h * vt)[0] - target) ** 2).sum())
+                lm = 0.5 * float(((fwd_only(U0 - h * vt)[0] - target) ** 2).sum())
+                fd = (lp - lm) / (2 * h)
+                gv = float(np.sum(grad * v))
+                worst = max(worst, abs(gv - fd) / abs(fd))
+            checks[kind] = {"directions": fd_dirs, "max_rel_err": worst}
+    return {"workload": f"1D Euler N={n}, seeded smooth periodic multi-wave state, {steps} SSP-RK3 steps of "
+                        f"fixed dt (CFL 0.5 of U0), loss 1/2||rho(T) - rho_target||^2, rho_target from seed+1",
+            "forward_s": round(t_fwd, 4), "store_all": res[1], "checkpoint_every_50": res[50],
+            "loss": float(loss.detach()), "fd_check": {"h": h, **checks}}
 
 
 def cpu_baseline(n_full: int, seed: int, target_s: float, steps: int = 1) -> dict:
@@ -387,6 +466,8 @@ def main():
            "d2h_bytes_per_step": nbytes, "steps": ke}
 
     batched = None if args.no_batched else bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
+    adjoint = None if args.no_adjoint else bench_adjoint(wenozn, inputs, args.seed + rank,
+                                                         fd_dirs=args.adjoint_fd_dirs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -402,7 +483,7 @@ def main():
                            "parallelism": f"{world} independent replica(s), one per GPU",
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "adjoint": adjoint,
                 "gpu_launches": 10 * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -195,6 +195,21 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
 wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, double dt, double* lam, void* ws,
                                   size_t ws_bytes, void* stream);
 
+/* The same reverse step given the forward step's stage inputs, so nothing is recomputed:
+ *   U, U1, U2 : device, the inputs U^n, U^(1), U^(2) of the three RK stages;
+ *   alphas    : device, 3 doubles, the LF speeds of U^n, U^(1), U^(2) (as the forward step
+ *               computed them; see wenozn_workspace_stages);
+ *   lam       : cotangent of U^{n+1} on entry, of U^n on exit (must not overlap the stages). */
+wenozn_status wenozn_rk3_step_vjp_stages(const wenozn_problem* p, const double* U, const double* U1,
+                                         const double* U2, const double* alphas, double dt, double* lam,
+                                         void* ws, size_t ws_bytes, void* stream);
+
+/* Device addresses, inside the workspace, of the stage inputs U^(1), U^(2) of the last
+ * wenozn_rk3_step on it and of its LF speeds (3 doubles with a stride of 2: U^n, U^(1),
+ * U^(2) at alphas[0], alphas[2], alphas[4]).  Valid until the next call on the workspace. */
+wenozn_status wenozn_workspace_stages(void* ws, const wenozn_problem* p, const double** U1, const double** U2,
+                                      const double** alphas);
+
 /* ---------------------------------------------------------------------------------------
  * Batched 1D Euler: B independent problems of uneven size (the 1D Euler set-up of Sec. 4.3,
  * each with its own grid), advanced together by one persistent kernel launch per RK stage.

@@ -10,10 +10,10 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     std::memset(&v, 0, sizeof v);
     v.C = reinterpret_cast<double*>(ws_base(ws) + L.C);
     v.partial = reinterpret_cast<double*>(ws_base(ws) + L.partial);
-    v.argmax = reinterpret_cast<int*>(ws_base(ws) + L.argmax);
+    v.ctl = reinterpret_cast<unsigned*>(ws_base(ws) + L.vjp_ctl);
     v.n = p.nx;
     v.bc = p.bc_x;
-    v.nblocks = vjp_interface_blocks(p.nx);
+    v.fast_rcp = zn_fast_rcp(p.eps, p.A);
     v.rdx = 1.0 / p.dx;
     v.gamma = p.gamma;
     v.eps4 = 4.0 * p.eps;
@@ -30,6 +30,34 @@ wenozn_status check_vjp(const wenozn_problem* p, void* ws, size_t ws_bytes, Layo
     *L = layout_of(*p);
     if (ws_bytes < L->total_vjp) return WENOZN_ENOMEM_WS;
     return WENOZN_OK;
+}
+
+// Reverse of U3 = U0/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)),
+// U1 = U0 + dt L(U0), given the stage inputs and their LF speeds (bit patterns).
+wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws, const double* U0,
+                             const double* U1, const double* U2, const unsigned long long* a0,
+                             const unsigned long long* a1, const unsigned long long* a2, double dt,
+                             double* lam, cudaStream_t s) {
+    double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
+    double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
+    VjpArgs v = vjp_args(p, L, ws);
+    cudaError_t e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return WENOZN_ECUDA;
+    // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
+    v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
+    v.X1 = lam; v.c1 = 2.0 / 3.0; v.d = (2.0 / 3.0) * dt;
+    e = launch_vjp(p.system, v, s);
+    if (e == cudaSuccess) {                 // Ub1 = 1/4 Ub2 + 1/4 dt J(U1)^T Ub2
+        v.U = U1; v.lam = ub2; v.alpha_bits = a1; v.out = ub1;
+        v.X1 = ub2; v.c1 = 0.25; v.d = 0.25 * dt;
+        e = launch_vjp(p.system, v, s);
+    }
+    if (e == cudaSuccess) {                 // lam <- lam/3 + 3/4 Ub2 + Ub1 + dt J(U0)^T Ub1
+        v.U = U0; v.lam = ub1; v.alpha_bits = a0; v.out = lam;
+        v.X1 = lam; v.c1 = 1.0 / 3.0; v.X2 = ub2; v.c2 = 0.75; v.X3 = ub1; v.c3 = 1.0; v.d = dt;
+        e = launch_vjp(p.system, v, s);
+    }
+    return cuda_status(e);
 }
 
 }  // namespace
@@ -55,8 +83,9 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
     cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
+    VjpArgs v = vjp_args(*p, L, ws);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) {
-        VjpArgs v = vjp_args(*p, L, ws);
         v.U = U;
         v.lam = lam;
         v.alpha_bits = ctrl->alpha[0];
@@ -100,25 +129,33 @@ wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, doub
         u.dt_fixed = dt;
         e = launch_update(p->system, u, s);
     }
-    // reverse of U3 = U0/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)),
-    // U1 = U0 + dt L(U0)
-    VjpArgs v = vjp_args(*p, L, ws);
-    if (e == cudaSuccess) {                 // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
-        v.U = u2; v.lam = lam; v.alpha_bits = ctrl->alpha[2]; v.out = ub2;
-        v.X1 = lam; v.c1 = 2.0 / 3.0; v.d = (2.0 / 3.0) * dt;
-        e = launch_vjp(p->system, v, s);
-    }
-    if (e == cudaSuccess) {                 // Ub1 = 1/4 Ub2 + 1/4 dt J(U1)^T Ub2
-        v.U = u1; v.lam = ub2; v.alpha_bits = ctrl->alpha[1]; v.out = ub1;
-        v.X1 = ub2; v.c1 = 0.25; v.d = 0.25 * dt;
-        e = launch_vjp(p->system, v, s);
-    }
-    if (e == cudaSuccess) {                 // lam <- lam/3 + 3/4 Ub2 + Ub1 + dt J(U0)^T Ub1
-        v.U = U; v.lam = ub1; v.alpha_bits = ctrl->alpha[0]; v.out = lam;
-        v.X1 = lam; v.c1 = 1.0 / 3.0; v.X2 = ub2; v.c2 = 0.75; v.X3 = ub1; v.c3 = 1.0; v.d = dt;
-        e = launch_vjp(p->system, v, s);
-    }
-    return cuda_status(e);
+    if (e != cudaSuccess) return WENOZN_ECUDA;
+    const unsigned long long* a = &ctrl->alpha[0][0];
+    return reverse_stages(*p, L, ws, U, u1, u2, a, a + 2, a + 4, dt, lam, s);
+}
+
+wenozn_status wenozn_rk3_step_vjp_stages(const wenozn_problem* p, const double* U, const double* U1,
+                                         const double* U2, const double* alphas, double dt, double* lam,
+                                         void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    wenozn_status st = check_vjp(p, ws, ws_bytes, &L);
+    if (st != WENOZN_OK) return st;
+    if (!U || !U1 || !U2 || !alphas || !lam || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
+    if (lam == U || lam == U1 || lam == U2) return WENOZN_EINVAL;
+    const unsigned long long* a = reinterpret_cast<const unsigned long long*>(alphas);
+    return reverse_stages(*p, L, ws, U, U1, U2, a, a + 1, a + 2, dt, lam, static_cast<cudaStream_t>(stream));
+}
+
+wenozn_status wenozn_workspace_stages(void* ws, const wenozn_problem* p, const double** U1, const double** U2,
+                                      const double** alphas) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!ws) return WENOZN_EINVAL;
+    const Layout L = layout_of(*p);
+    if (U1) *U1 = reinterpret_cast<const double*>(ws_base(ws) + L.u1);
+    if (U2) *U2 = reinterpret_cast<const double*>(ws_base(ws) + L.u2);
+    if (alphas) *alphas = reinterpret_cast<const double*>(&reinterpret_cast<Ctrl*>(ws_base(ws) + L.ctrl)->alpha[0][0]);
+    return WENOZN_OK;
 }
 
 }  // extern "C"

@@ -4,22 +4,23 @@
 // RHS: L_i = -(F^_{i+1/2} - F^_{i-1/2})/dx, F^ at interface j (x_{j-1/2}) depends on the six
 // cells j-3 .. j+2 and on the global LF speed alpha = max_i(|u_i| + c_i).  For a cotangent
 // lambda of L the interface cotangent is Fbar_j = (lambda_j - lambda_{j-1})/dx (lambda outside
-// the grid is 0).  Each interface thread recomputes its forward quantities and sweeps them
-// backwards, writing the cotangent contributions to its six stencil cells into a buffer
-// C[j][s][k]; a gather kernel then sums, for every cell, the contributions of the stencil
-// positions that map to it (ghost cells included) in a fixed order, so the result is
-// deterministic.  alpha is differentiated through its argmax cell (the lowest index on ties);
-// d|x|/dx is taken as 0 at x = 0.
+// the grid is 0).  The interface kernel recomputes the forward quantities of each interface
+// and sweeps them backwards, writing the cotangents of its six stencil cells' split fluxes
+// (and of its Roe-average inputs) to a buffer; a gather kernel then sums, for every cell, the
+// contributions of the stencil positions that map to it (ghost cells included) in a fixed
+// order and applies the cell's own derivatives once, so the result is deterministic.  alpha
+// is differentiated through its argmax cell (the lowest index on ties); d|x|/dx is taken as
+// 0 at x = 0.
 #include "launch.h"
 
 namespace wz {
 
 namespace {
 
-constexpr int kThreads = 128;
-
-// Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), adds dW/df * Wb to fb.
-__host__ __device__ __forceinline__ void zn_vjp(const double* f, double Wb, double eps4, double A4, double* fb) {
+// Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), adds dW/df * Wb to fb
+// and returns W(f).
+__host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double A4, int fast,
+                                                  double* fb) {
     const double a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
     // first differences, then the second (s_k) and one-sided (t_k) differences from them:
     // equal inputs give exact zeros
@@ -46,7 +47,7 @@ __host__ __device__ __forceinline__ void zn_vjp(const double* f, double Wb, doub
     const double q2 = fma(0.25, s2, fma(-0.75, t2, 3.0 * c));
     const double N = fma(a0, q0, fma(a1, q1, a2 * q2));
     const double D = fma(6.0, a1, fma(3.0, a2, a0));
-    const double rD = 1.0 / D;
+    const double rD = fast ? rcp_nr(D) : 1.0 / D;
     const double W = N * rD;
     // reverse
     const double Nb = Wb * rD, Db = -Wb * W * rD;
@@ -78,287 +79,346 @@ __host__ __device__ __forceinline__ void zn_vjp(const double* f, double Wb, doub
     fb[2] += cb + s0b - 2.0 * s1b + s2b + 3.0 * t0b + 3.0 * t2b;
     fb[3] += s1b - 2.0 * s2b - t1b - 4.0 * t2b;
     fb[4] += s2b + t2b;
+    return W;
 }
 
-// Cotangents Ub[6][NV] of the six stencil cells (and alpha) of one interface flux, given
-// the cotangent Fb of F^ at that interface.  NV = 1: advection with speed a (alpha = |a|,
-// constant); NV = 3: 1D Euler.
-template <int NV>
-__host__ __device__ void interface_vjp(const double (*Us)[3], double alpha, double a_adv, double gamma, double eps4,
-                              double A4, const double* Fb, double (*Ub)[3], double& alphab) {
-    const double gm1 = gamma - 1.0;
-    double hp[6][NV], hm[6][NV];
-    double u[6], p[6], Ep[6];
-    for (int s = 0; s < 6; ++s) {
-        if (NV == 1) {
-            const double f = a_adv * Us[s][0];
-            hp[s][0] = 0.5 * (f + alpha * Us[s][0]);
-            hm[s][0] = 0.5 * (f - alpha * Us[s][0]);
-            continue;
-        }
-        const double rho = Us[s][0], mom = Us[s][1], E = Us[s][2];
-        u[s] = mom / rho;
-        p[s] = gm1 * (E - 0.5 * mom * u[s]);
-        Ep[s] = E + p[s];
-        const double F[3] = {mom, fma(mom, u[s], p[s]), u[s] * Ep[s]};
-        for (int k = 0; k < 3; ++k) {
-            hp[s][k] = 0.5 * (F[k] + alpha * Us[s][k]);
-            hm[s][k] = 0.5 * (F[k] - alpha * Us[s][k]);
-        }
-    }
-    for (int s = 0; s < 6; ++s)
-        for (int k = 0; k < 3; ++k) Ub[s][k] = 0.0;
-    alphab = 0.0;
-    double hpb[6][NV], hmb[6][NV];
-    for (int s = 0; s < 6; ++s)
-        for (int k = 0; k < NV; ++k) hpb[s][k] = hmb[s][k] = 0.0;
+// ---------------------------------------------------------------------------------------
+// Interface kernels.  A block takes kTI consecutive interfaces j0 .. j0+kTI-1 and their
+// kCells stencil cells, whose split fluxes h+- (and, for Euler, u, H, sqrt(rho), 1/rho) it
+// computes once into shared memory.  For Euler each interface is then handled by three
+// threads, one per characteristic field k (warp k of the block): the Roe state, row k of the
+// left and column k of the right eigenvectors, the projection of the stencil onto field k,
+// both WENO-ZN reconstructions of that field and their reverse sweeps.  The three fields'
+// cotangents of the split fluxes and of the Roe quantities are summed through shared memory.
+//
+// Output, planar over interfaces (P = n + 1 planes):
+//   C[(s Q + m) P + j]      = (hbar+_{s,m} + hbar-_{s,m}) / 2,
+//   C[(s Q + NV + m) P + j] = (hbar+_{s,m} - hbar-_{s,m}) / 2,
+//   for stencil position s = 0..5 (cell j - 3 + s), Q = 2 NV values per position, and for
+//   Euler C[(36 + 3 t + m) P + j], t = 0, 1: the conserved-variable cotangent of the left
+//   (cell j - 1) and right (cell j) Roe-average inputs.
+// The split flux is h+- = (F(U) +- alpha U)/2, so hbar+ dh+/dU + hbar- dh-/dU is
+// J_F^T (hbar+ + hbar-)/2 + alpha (hbar+ - hbar-)/2: the gather applies J_F^T once per cell to
+// the summed first part.
+// ---------------------------------------------------------------------------------------
+constexpr int kTI = 32;                 // interfaces per block (one warp per field)
+constexpr int kCells = kTI + 5;         // cells j0-3 .. j0+kTI+1
+constexpr int kGather = 256;            // cells per gather block
+constexpr int kRoe = 36;                // first Roe plane (Euler)
 
-    if (NV == 1) {
-        const double fp[5] = {hp[0][0], hp[1][0], hp[2][0], hp[3][0], hp[4][0]};
-        const double fm[5] = {hm[5][0], hm[4][0], hm[3][0], hm[2][0], hm[1][0]};
-        double fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
-        zn_vjp(fp, Fb[0], eps4, A4, fpb);
-        zn_vjp(fm, Fb[0], eps4, A4, fmb);
-        for (int s = 0; s < 5; ++s) {
-            hpb[s][0] += fpb[s];
-            hmb[5 - s][0] += fmb[s];
-        }
-        for (int s = 0; s < 6; ++s)
-            Ub[s][0] = 0.5 * (a_adv + alpha) * hpb[s][0] + 0.5 * (a_adv - alpha) * hmb[s][0];
-        return;
-    }
+struct EulerSmem {
+    double hp[3][kCells], hm[3][kCells];
+    double u[kCells], H[kCells], sq[kCells], r[kCells];
+    double red[3][36][kTI];             // per field: hbar+ (5 x 3), hbar- (5 x 3), 6 Roe scalars
+};
 
-    // ---- forward: Roe state and eigenvectors of cells 2 and 3 ----------------------------
-    const double rhoL = Us[2][0], rhoR = Us[3][0];
-    const double sl = sqrt(rhoL), sr = sqrt(rhoR);
-    const double HL = Ep[2] / rhoL, HR = Ep[3] / rhoR;
-    const double S = sl + sr;
-    const double wl = sl / S, wr = sr / S;
-    const double ut = wl * u[2] + wr * u[3];
-    const double Ht = wl * HL + wr * HR;
-    const double c2 = gm1 * (Ht - 0.5 * ut * ut);
-    const double c = sqrt(c2);
-    const double rc = 1.0 / c;
-    const double b1 = gm1 * rc * rc, b2 = 0.5 * ut * ut * b1;
-    const double Lm[3][3] = {{0.5 * (b2 + ut * rc), -0.5 * (b1 * ut + rc), 0.5 * b1},
-                             {1.0 - b2, b1 * ut, -b1},
-                             {0.5 * (b2 - ut * rc), -0.5 * (b1 * ut - rc), 0.5 * b1}};
-    const double R[3][3] = {{1.0, 1.0, 1.0},
-                            {ut - c, ut, ut + c},
-                            {Ht - ut * c, 0.5 * ut * ut, Ht + ut * c}};
-    double gp[3][5], gm[3][5], gh[3];
-    for (int k = 0; k < 3; ++k) {
-        for (int s = 0; s < 5; ++s) {
-            gp[k][s] = Lm[k][0] * hp[s][0] + Lm[k][1] * hp[s][1] + Lm[k][2] * hp[s][2];
-            gm[k][s] = Lm[k][0] * hm[s + 1][0] + Lm[k][1] * hm[s + 1][1] + Lm[k][2] * hm[s + 1][2];
-        }
-        const double fpk[5] = {gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4]};
-        const double fmk[5] = {gm[k][4], gm[k][3], gm[k][2], gm[k][1], gm[k][0]};
-        gh[k] = zn_flux(fpk[0], fpk[1], fpk[2], fpk[3], fpk[4], eps4, A4, false) +
-                zn_flux(fmk[0], fmk[1], fmk[2], fmk[3], fmk[4], eps4, A4, false);
-    }
-    // ---- reverse --------------------------------------------------------------------------
-    double ghb[3], Rb[3][3], Lb[3][3];
-    for (int k = 0; k < 3; ++k) {
-        ghb[k] = R[0][k] * Fb[0] + R[1][k] * Fb[1] + R[2][k] * Fb[2];
+__global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
+    __shared__ EulerSmem sm;
+    const int n = a.n, j0 = blockIdx.x * kTI, tid = threadIdx.x;
+    const int64_t P = int64_t(n) + 1;
+    const double gm1 = a.gamma - 1.0;
+    const unsigned long long abits = a.alpha_bits[0];
+    const double alpha = __longlong_as_double((long long)abits);
+    for (int c = tid; c < kCells; c += 3 * kTI) {
+        const int g = j0 - 3 + c;
+        const int src = ghost_src(g, n, a.bc);
+        double s[3];
+        for (int m = 0; m < 3; ++m) s[m] = a.U[int64_t(m) * n + src];
+        const double r = 1.0 / s[0];
+        const double u = s[1] * r;
+        const double p = gm1 * (s[2] - 0.5 * s[1] * u);
+        const double Ep = s[2] + p;
+        const double F[3] = {s[1], fma(s[1], u, p), u * Ep};
         for (int m = 0; m < 3; ++m) {
-            Rb[m][k] = Fb[m] * gh[k];
-            Lb[k][m] = 0.0;
+            sm.hp[m][c] = 0.5 * fma(alpha, s[m], F[m]);
+            sm.hm[m][c] = 0.5 * fma(-alpha, s[m], F[m]);
+        }
+        sm.u[c] = u;
+        sm.H[c] = Ep * r;
+        sm.sq[c] = sqrt(s[0]);
+        sm.r[c] = r;
+        if (g == src && c >= 3 && c < 3 + kTI) {   // a grid cell of this block: is it the LF argmax?
+            double sx, sy;
+            wave_speeds<3>(s, a.gamma, sx, sy);
+            if ((unsigned long long)__double_as_longlong(sx) == abits) atomicMax(&a.ctl[0], ~unsigned(g));
         }
     }
-    for (int k = 0; k < 3; ++k) {
-        const double fpk[5] = {gp[k][0], gp[k][1], gp[k][2], gp[k][3], gp[k][4]};
-        const double fmk[5] = {gm[k][4], gm[k][3], gm[k][2], gm[k][1], gm[k][0]};
-        double fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
-        zn_vjp(fpk, ghb[k], eps4, A4, fpb);
-        zn_vjp(fmk, ghb[k], eps4, A4, fmb);
+    __syncthreads();
+
+    const int k = tid / kTI, i = tid % kTI, j = j0 + i;
+    const bool live = j <= n;
+    const int cl = i + 2, cr = i + 3;            // cells j-1, j
+    double ut = 0, Ht = 0, c = 0, rc = 0, b1 = 0, wl = 0, wr = 0, rS = 0;
+    if (live) {
+        // Roe state and row k of L, column k of R (R[0][k] = 1)
+        const double sl = sm.sq[cl], sr = sm.sq[cr];
+        rS = rcp_nr(sl + sr);
+        wl = sl * rS;
+        wr = sr * rS;
+        ut = fma(wl, sm.u[cl], wr * sm.u[cr]);
+        Ht = fma(wl, sm.H[cl], wr * sm.H[cr]);
+        c = sqrt(gm1 * fma(-0.5 * ut, ut, Ht));
+        rc = rcp_nr(c);
+        b1 = gm1 * rc * rc;
+        const double b2 = 0.5 * ut * ut * b1;
+        double L0, L1, L2, R1, R2;
+        if (k == 0) {
+            L0 = 0.5 * fma(ut, rc, b2); L1 = -0.5 * fma(b1, ut, rc); L2 = 0.5 * b1;
+            R1 = ut - c; R2 = fma(-ut, c, Ht);
+        } else if (k == 1) {
+            L0 = 1.0 - b2; L1 = b1 * ut; L2 = -b1;
+            R1 = ut; R2 = 0.5 * ut * ut;
+        } else {
+            L0 = 0.5 * fma(-ut, rc, b2); L1 = -0.5 * fma(b1, ut, -rc); L2 = 0.5 * b1;
+            R1 = ut + c; R2 = fma(ut, c, Ht);
+        }
+        double Fb[3];
+        for (int m = 0; m < 3; ++m) {
+            const double right = j < n ? a.lam[int64_t(m) * n + j] : 0.0;
+            const double left = j > 0 ? a.lam[int64_t(m) * n + j - 1] : 0.0;
+            Fb[m] = (right - left) * a.rdx;
+        }
+        const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
+        double fp[5], fm[5], fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
+#pragma unroll
         for (int s = 0; s < 5; ++s) {
-            const double gpb = fpb[s], gmb = fmb[4 - s];       // cotangents of gp[k][s], gm[k][s]
+            fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
+            fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
+        }
+        const double gh = zn_vjp(fp, ghb, a.eps4, a.A4, a.fast_rcp, fpb) +
+                          zn_vjp(fm, ghb, a.eps4, a.A4, a.fast_rcp, fmb);
+        double Lb[3] = {0, 0, 0};
+        const double Lk[3] = {L0, L1, L2};
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const double gpb = fpb[s], gmb = fmb[4 - s];     // cotangents of the projected h+_s, h-_{s+1}
+#pragma unroll
             for (int m = 0; m < 3; ++m) {
-                Lb[k][m] += gpb * hp[s][m] + gmb * hm[s + 1][m];
-                hpb[s][m] += gpb * Lm[k][m];
-                hmb[s + 1][m] += gmb * Lm[k][m];
+                Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
+                sm.red[k][s * 3 + m][i] = gpb * Lk[m];
+                sm.red[k][15 + s * 3 + m][i] = gmb * Lk[m];
             }
         }
+        const double Rb1 = Fb[1] * gh, Rb2 = Fb[2] * gh;
+        double b2b, b1b, rcb, utb, cb, Htb;
+        if (k == 0) {
+            b2b = 0.5 * Lb[0]; b1b = 0.5 * fma(-ut, Lb[1], Lb[2]); rcb = 0.5 * fma(ut, Lb[0], -Lb[1]);
+            utb = 0.5 * fma(rc, Lb[0], -b1 * Lb[1]) + fma(-c, Rb2, Rb1); cb = fma(-ut, Rb2, -Rb1); Htb = Rb2;
+        } else if (k == 1) {
+            b2b = -Lb[0]; b1b = fma(ut, Lb[1], -Lb[2]); rcb = 0.0;
+            utb = fma(b1, Lb[1], fma(ut, Rb2, Rb1)); cb = 0.0; Htb = 0.0;
+        } else {
+            b2b = 0.5 * Lb[0]; b1b = 0.5 * fma(-ut, Lb[1], Lb[2]); rcb = 0.5 * fma(-ut, Lb[0], Lb[1]);
+            utb = -0.5 * fma(rc, Lb[0], b1 * Lb[1]) + fma(c, Rb2, Rb1); cb = fma(ut, Rb2, Rb1); Htb = Rb2;
+        }
+        sm.red[k][30][i] = b2b; sm.red[k][31][i] = b1b; sm.red[k][32][i] = rcb;
+        sm.red[k][33][i] = utb; sm.red[k][34][i] = cb; sm.red[k][35][i] = Htb;
     }
-    // left eigenvectors -> (u~, rc, b1, b2)
-    double b2b = 0.5 * Lb[0][0] - Lb[1][0] + 0.5 * Lb[2][0];
-    double b1b = -0.5 * ut * Lb[0][1] + 0.5 * Lb[0][2] + ut * Lb[1][1] - Lb[1][2] - 0.5 * ut * Lb[2][1] +
-                 0.5 * Lb[2][2];
-    double rcb = 0.5 * ut * Lb[0][0] - 0.5 * Lb[0][1] - 0.5 * ut * Lb[2][0] + 0.5 * Lb[2][1];
-    double utb = 0.5 * rc * Lb[0][0] - 0.5 * b1 * Lb[0][1] + b1 * Lb[1][1] - 0.5 * rc * Lb[2][0] -
-                 0.5 * b1 * Lb[2][1];
-    utb += b2b * ut * b1;
-    b1b += b2b * 0.5 * ut * ut;
-    rcb += b1b * 2.0 * gm1 * rc;
-    double cb = -rcb * rc * rc;
-    // right eigenvectors -> (u~, c, H~)
-    utb += Rb[1][0] + Rb[1][1] + Rb[1][2] - c * Rb[2][0] + ut * Rb[2][1] + c * Rb[2][2];
-    cb += -Rb[1][0] + Rb[1][2] - ut * Rb[2][0] + ut * Rb[2][2];
-    double Htb = Rb[2][0] + Rb[2][2];
-    // c = sqrt((gamma-1)(H~ - u~^2/2))
-    Htb += cb * gm1 * 0.5 * rc;
-    utb -= cb * gm1 * 0.5 * rc * ut;
-    // Roe average -> u, H of cells 2 and 3 and sqrt(rho)
-    double ub[6] = {0, 0, 0, 0, 0, 0}, Hb2 = Htb * wl, Hb3 = Htb * wr;
-    ub[2] += utb * wl;
-    ub[3] += utb * wr;
-    const double slb = (utb * (u[2] - ut) + Htb * (HL - Ht)) / S;
-    const double srb = (utb * (u[3] - ut) + Htb * (HR - Ht)) / S;
-    Ub[2][0] += slb * 0.5 / sl;
-    Ub[3][0] += srb * 0.5 / sr;
-    // cells: split fluxes, enthalpy, primitives
+    __syncthreads();
+    if (!live) return;
+    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int s = 2 * k + t;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const double hpb = s <= 4 ? (sm.red[0][s * 3 + m][i] + sm.red[1][s * 3 + m][i]) + sm.red[2][s * 3 + m][i] : 0.0;
+            const double hmb = s >= 1 ? (sm.red[0][12 + s * 3 + m][i] + sm.red[1][12 + s * 3 + m][i]) +
+                                            sm.red[2][12 + s * 3 + m][i] : 0.0;
+            a.C[(s * 6 + m) * P + j] = 0.5 * (hpb + hmb);
+            a.C[(s * 6 + 3 + m) * P + j] = 0.5 * (hpb - hmb);
+        }
+    }
+    if (k == 0) return;
+    // Roe average (warps 1 and 2 both reverse it; 1 writes the left cell, 2 the right):
+    // b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2))
+    double sc[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
+    double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
+    utb = fma(b2b * ut, b1, utb);
+    b1b = fma(b2b * 0.5 * ut, ut, b1b);
+    rcb = fma(b1b * 2.0 * gm1, rc, rcb);
+    cb = fma(-rcb * rc, rc, cb);
+    const double cq = cb * gm1 * 0.5 * rc;
+    Htb += cq;
+    utb = fma(-cq, ut, utb);
+    // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
+    const int cc = k == 1 ? cl : cr;
+    const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
+    const double ub = utb * w, Hb = Htb * w;
+    const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
+    // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
+    const double Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
+    const double Um = r * fma(-gm1 * uc, Hb, ub);
+    const double UE = a.gamma * r * Hb;
+    double* roe = a.C + (kRoe + 3 * (k - 1)) * P + j;
+    roe[0] = Ur;
+    roe[P] = Um;
+    roe[2 * P] = UE;
+}
+
+__global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
+    __shared__ double hp[kCells], hm[kCells];
+    const int n = a.n, j0 = blockIdx.x * kTI, i = threadIdx.x, j = j0 + i;
+    const int64_t P = int64_t(n) + 1;
+    const double alpha = fabs(a.adv_speed);
+    for (int c = i; c < kCells; c += kTI) {
+        const double s = a.U[ghost_src(j0 - 3 + c, n, a.bc)];
+        const double f = a.adv_speed * s;
+        hp[c] = 0.5 * fma(alpha, s, f);
+        hm[c] = 0.5 * fma(-alpha, s, f);
+    }
+    __syncthreads();
+    if (j > n) return;
+    const double right = j < n ? a.lam[j] : 0.0, left = j > 0 ? a.lam[j - 1] : 0.0;
+    const double Fb = (right - left) * a.rdx;
+    double fp[5], fm[5], fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
+    for (int s = 0; s < 5; ++s) {
+        fp[s] = hp[i + s];
+        fm[4 - s] = hm[i + s + 1];
+    }
+    zn_vjp(fp, Fb, a.eps4, a.A4, a.fast_rcp, fpb);
+    zn_vjp(fm, Fb, a.eps4, a.A4, a.fast_rcp, fmb);
     for (int s = 0; s < 6; ++s) {
-        const double rho = Us[s][0], mom = Us[s][1];
-        double Fbc[3], pb = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            Fbc[k] = 0.5 * (hpb[s][k] + hmb[s][k]);
-            const double dh = 0.5 * (hpb[s][k] - hmb[s][k]);
-            Ub[s][k] += alpha * dh;
-            alphab += Us[s][k] * dh;
-        }
-        double mb = Fbc[0] + Fbc[1] * u[s];
-        double Eb = Fbc[2] * u[s];
-        ub[s] += Fbc[1] * mom + Fbc[2] * Ep[s];
-        pb += Fbc[1] + Fbc[2] * u[s];
-        if (s == 2 || s == 3) {
-            const double Hb = s == 2 ? Hb2 : Hb3;
-            Eb += Hb / rho;
-            pb += Hb / rho;
-            Ub[s][0] -= Hb * (Ep[s] / rho) / rho;
-        }
-        Eb += gm1 * pb;
-        mb -= gm1 * 0.5 * u[s] * pb;
-        ub[s] -= gm1 * 0.5 * mom * pb;
-        mb += ub[s] / rho;
-        Ub[s][0] -= ub[s] * u[s] / rho;
-        Ub[s][1] += mb;
-        Ub[s][2] += Eb;
+        const double hpb = s <= 4 ? fpb[s] : 0.0, hmb = s >= 1 ? fmb[5 - s] : 0.0;
+        a.C[(2 * s) * P + j] = 0.5 * (hpb + hmb);
+        a.C[(2 * s + 1) * P + j] = 0.5 * (hpb - hmb);
     }
 }
 
-// Per interface: cotangent contributions to its six stencil cells (C[j][s][k]) and a
-// per-block partial sum of the LF-speed cotangent.
-template <int NV>
-__global__ void __launch_bounds__(kThreads) vjp_interface_kernel(VjpArgs a) {
-    __shared__ double red[kThreads / 32];
-    const int n = a.n;
-    const int j = blockIdx.x * kThreads + threadIdx.x;
-    double alphab = 0.0;
-    if (j <= n) {
-        double Us[6][3];
-        for (int s = 0; s < 6; ++s) {
-            const int g = ghost_src(j - 3 + s, n, a.bc);
-            for (int k = 0; k < NV; ++k) Us[s][k] = a.U[int64_t(k) * n + g];
-        }
-        double Fb[NV];
-        for (int k = 0; k < NV; ++k) {
-            const double right = j < n ? a.lam[int64_t(k) * n + j] : 0.0;
-            const double left = j > 0 ? a.lam[int64_t(k) * n + j - 1] : 0.0;
-            Fb[k] = (right - left) * a.rdx;
-        }
-        const double alpha = NV == 1 ? fabs(a.adv_speed) : __longlong_as_double((long long)a.alpha_bits[0]);
-        double Ub[6][3];
-        interface_vjp<NV>(Us, alpha, a.adv_speed, a.gamma, a.eps4, a.A4, Fb, Ub, alphab);
-        double* out = a.C + int64_t(j) * 6 * NV;
-        for (int s = 0; s < 6; ++s)
-            for (int k = 0; k < NV; ++k) out[s * NV + k] = Ub[s][k];
-    }
-    // deterministic per-block partial of the LF-speed cotangent
-    double v = alphab;
+__device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-        a.partial[blockIdx.x] = t;
-    }
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kGather / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;                               // valid in thread 0
 }
 
-// Lowest cell index whose |u| + c equals the LF speed (bit-exact comparison).
+// Per cell i: sum the contributions of the stencil positions that map to it (ghost cells
+// included, fixed order), apply J_F^T to the flux part, add alpha times the LF part and the
+// Roe part, and write out_i = c1 X1_i + c2 X2_i + c3 X3_i + d (J^T lambda)_i.  For Euler the
+// LF-speed cotangent sum_i U_i . (LF part)_i is reduced in a fixed order; the last block to
+// finish adds its term at the argmax cell (d(|u| + c)/dU, |x|' = 0 at 0) and resets the
+// control words.
 template <int NV>
-__global__ void __launch_bounds__(256) argmax_kernel(VjpArgs a) {
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    if (i >= a.n || NV == 1) return;
-    double s[NV];
-    for (int k = 0; k < NV; ++k) s[k] = a.U[int64_t(k) * a.n + i];
-    double sx, sy;
-    wave_speeds<NV>(s, a.gamma, sx, sy);
-    if (__double_as_longlong(sx) == (long long)a.alpha_bits[0]) atomicMin(a.argmax, i);
-}
-
-// out_i = c1 X1_i + c2 X2_i + c3 X3_i + d (J^T lambda)_i with the gathered contributions.
-template <int NV>
-__global__ void __launch_bounds__(256) vjp_gather_kernel(VjpArgs a) {
+__global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
+    constexpr int Q = 2 * NV;
+    __shared__ double red[kGather / 32];
+    __shared__ bool last;
     const int n = a.n;
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    if (i >= n) return;
-    double acc[NV];
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    // stencil cells g (in -3 .. n+2) whose ghost map lands on i
-    int gs[16], ng = 0;
-    if (n <= 8) {
-        for (int g = -3; g <= n + 2; ++g)
-            if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
-    } else if (a.bc == 0) {
-        for (int g = i - n; g <= i + n; g += n)
-            if (g >= -3 && g <= n + 2) gs[ng++] = g;
-    } else {
-        gs[ng++] = i;
-        if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
-        if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
-    }
-    for (int q = 0; q < ng; ++q) {
-        const int g = gs[q];
-        for (int s = 0; s < 6; ++s) {
-            const int j = g + 3 - s;                 // interface whose stencil position s is g
-            if (j < 0 || j > n) continue;
-            const double* c = a.C + (int64_t(j) * 6 + s) * NV;
-            for (int k = 0; k < NV; ++k) acc[k] += c[k];
+    const int64_t P = int64_t(n) + 1;
+    const int i = blockIdx.x * kGather + threadIdx.x;
+    double ab = 0.0;
+    if (i < n) {
+        double Fs[NV], Ds[NV], Rs[NV];
+        for (int m = 0; m < NV; ++m) Fs[m] = Ds[m] = Rs[m] = 0.0;
+        int gs[16], ng = 0;                 // stencil cells g (in -3 .. n+2) that map to i
+        if (n <= 8) {
+            for (int g = -3; g <= n + 2; ++g)
+                if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
+        } else if (a.bc == 0) {
+            for (int g = i - n; g <= i + n; g += n)
+                if (g >= -3 && g <= n + 2) gs[ng++] = g;
+        } else {
+            gs[ng++] = i;
+            if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
+            if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
+        }
+        for (int q = 0; q < ng; ++q) {
+            const int g = gs[q];
+            for (int s = 0; s < 6; ++s) {
+                const int j = g + 3 - s;             // interface whose stencil position s is g
+                if (j < 0 || j > n) continue;
+                for (int m = 0; m < NV; ++m) {
+                    Fs[m] += a.C[(s * Q + m) * P + j];
+                    Ds[m] += a.C[(s * Q + NV + m) * P + j];
+                }
+                if (NV == 3 && (s == 2 || s == 3))
+                    for (int m = 0; m < NV; ++m) Rs[m] += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
+            }
+        }
+        double Ub[NV];
+        if (NV == 1) {
+            Ub[0] = fma(a.adv_speed, Fs[0], fabs(a.adv_speed) * Ds[0]);
+        } else {
+            const double alpha = __longlong_as_double((long long)a.alpha_bits[0]);
+            const double gm1 = a.gamma - 1.0;
+            const double rho = a.U[i], mom = a.U[n + i], E = a.U[2 * int64_t(n) + i];
+            const double r = 1.0 / rho, u = mom * r;
+            const double p = gm1 * (E - 0.5 * mom * u);
+            const double Ep = E + p;
+            // F = (mom, mom u + p, u (E + p)), u = mom/rho, p = (gamma-1)(E - mom u/2)
+            const double pb = fma(Fs[2], u, Fs[1]);
+            double mb = fma(Fs[1], u, Fs[0]) - gm1 * 0.5 * u * pb;
+            const double Eb = fma(Fs[2], u, gm1 * pb);
+            const double ub = fma(Fs[1], mom, Fs[2] * Ep) - gm1 * 0.5 * mom * pb;
+            mb = fma(ub, r, mb);
+            const double rb = -ub * u * r;
+            Ub[0] = fma(alpha, Ds[0], rb) + Rs[0];
+            Ub[1] = fma(alpha, Ds[1], mb) + Rs[1];
+            Ub[2] = fma(alpha, Ds[2], Eb) + Rs[2];
+            ab = fma(rho, Ds[0], fma(mom, Ds[1], E * Ds[2]));
+        }
+        for (int m = 0; m < NV; ++m) {
+            const int64_t idx = int64_t(m) * n + i;
+            double v = a.d * Ub[m];
+            if (a.X1) v = fma(a.c1, a.X1[idx], v);
+            if (a.X2) v = fma(a.c2, a.X2[idx], v);
+            if (a.X3) v = fma(a.c3, a.X3[idx], v);
+            a.out[idx] = v;
         }
     }
-    if (NV == 3 && i == *a.argmax) {
-        double ab = 0.0;
-        for (int b = 0; b < a.nblocks; ++b) ab += a.partial[b];
-        // d(|u| + c)/dU at this cell, |x|' = 0 at 0
-        const double rho = a.U[i], mom = a.U[n + i], E = a.U[2 * int64_t(n) + i];
+    if (NV == 1) return;
+    const double part = block_sum(ab, red);
+    if (threadIdx.x == 0) {
+        a.partial[blockIdx.x] = part;
+        __threadfence();
+        last = atomicAdd(&a.ctl[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < int(gridDim.x); b += kGather) v += static_cast<volatile double*>(a.partial)[b];
+    const double abar = block_sum(v, red);
+    if (threadIdx.x != 0) return;
+    const unsigned key = static_cast<volatile unsigned*>(a.ctl)[0];
+    if (key != 0u) {
+        const int im = int(~key);
+        const double rho = a.U[im], mom = a.U[n + im], E = a.U[2 * int64_t(n) + im];
         const double u = mom / rho;
         const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
         const double c = sqrt(a.gamma * p / rho);
         const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
-        const double k = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
-        acc[0] += ab * (sg * (-u / rho) + k * (gm1 * 0.5 * u * u - p / rho));
-        acc[1] += ab * (sg / rho - k * gm1 * u);
-        acc[2] += ab * (k * gm1);
+        const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
+        const double g3[3] = {sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho), sg / rho - kk * gm1 * u, kk * gm1};
+        volatile double* out = a.out;
+        for (int m = 0; m < 3; ++m) out[int64_t(m) * n + im] = fma(a.d * abar, g3[m], out[int64_t(m) * n + im]);
     }
-    for (int k = 0; k < NV; ++k) {
-        const int64_t idx = int64_t(k) * n + i;
-        double r = a.d * acc[k];
-        if (a.X1) r = fma(a.c1, a.X1[idx], r);
-        if (a.X2) r = fma(a.c2, a.X2[idx], r);
-        if (a.X3) r = fma(a.c3, a.X3[idx], r);
-        a.out[idx] = r;
-    }
+    a.ctl[0] = 0u;
+    a.ctl[1] = 0u;
 }
 
 }  // namespace
 
-int vjp_interface_blocks(int n) { return (n + 1 + kThreads - 1) / kThreads; }
+int vjp_partial_count(int n) { return (n + kGather - 1) / kGather; }
+
+size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12 : 42); }
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
-    const unsigned gi = unsigned(vjp_interface_blocks(a.n)), gc = unsigned((a.n + 255) / 256);
+    const unsigned gi = unsigned((a.n + 1 + kTI - 1) / kTI), gc = unsigned(vjp_partial_count(a.n));
     if (system == 0) {
-        vjp_interface_kernel<1><<<gi, kThreads, 0, s>>>(a);
-        vjp_gather_kernel<1><<<gc, 256, 0, s>>>(a);
-        return cudaGetLastError();
+        vjp_interface_advection<<<gi, kTI, 0, s>>>(a);
+        vjp_gather_kernel<1><<<gc, kGather, 0, s>>>(a);
+    } else {
+        vjp_interface_euler<<<gi, 3 * kTI, 0, s>>>(a);
+        vjp_gather_kernel<3><<<gc, kGather, 0, s>>>(a);
     }
-    cudaError_t e = cudaMemsetAsync(a.argmax, 0x7f, sizeof(int), s);   // a large positive int
-    if (e != cudaSuccess) return e;
-    argmax_kernel<3><<<gc, 256, 0, s>>>(a);
-    vjp_interface_kernel<3><<<gi, kThreads, 0, s>>>(a);
-    vjp_gather_kernel<3><<<gc, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

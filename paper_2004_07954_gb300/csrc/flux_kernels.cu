@@ -15,18 +15,21 @@ namespace wz {
 
 namespace {
 
-constexpr int kThreads = 256;
+// Tile shapes: TI interfaces along the sweep x TA lines across it, THREADS per block.
+// Long 1D lines use 512-interface tiles; short ones (fewer tiles than twice the SM count)
+// use 64-interface tiles of 64 threads so that every SM gets work.
+template <int NV, int DIR, bool SMALL = false> struct Tile;
+template <> struct Tile<1, 0, false> { static constexpr int TI = 512, TA = 1, THREADS = 256; };
+template <> struct Tile<3, 0, false> { static constexpr int TI = 512, TA = 1, THREADS = 256; };
+template <> struct Tile<1, 0, true> { static constexpr int TI = 64, TA = 1, THREADS = 64; };
+template <> struct Tile<3, 0, true> { static constexpr int TI = 64, TA = 1, THREADS = 64; };
+template <> struct Tile<4, 0, false> { static constexpr int TI = 128, TA = 4, THREADS = 256; };
+template <> struct Tile<4, 1, false> { static constexpr int TI = 32, TA = 16, THREADS = 256; };
 
-// Tile shapes (interfaces along the sweep x lines across it).
-template <int NV, int DIR> struct Tile;
-template <> struct Tile<1, 0> { static constexpr int TI = 512, TA = 1; };
-template <> struct Tile<3, 0> { static constexpr int TI = 512, TA = 1; };
-template <> struct Tile<4, 0> { static constexpr int TI = 128, TA = 4; };
-template <> struct Tile<4, 1> { static constexpr int TI = 32, TA = 16; };
-
-template <int NV, int DIR>
-__global__ void __launch_bounds__(kThreads, 2) flux_kernel(FluxArgs a) {
-    constexpr int TI = Tile<NV, DIR>::TI, TA = Tile<NV, DIR>::TA;
+template <int NV, int DIR, bool SMALL>
+__global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(FluxArgs a) {
+    constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
+    constexpr int kThreads = Tile<NV, DIR, SMALL>::THREADS;
     constexpr int CL = TI + 5;            // cells per line in the tile
     constexpr int NC = CL * TA;           // cells per tile
     extern __shared__ double smem[];
@@ -91,9 +94,9 @@ __global__ void __launch_bounds__(kThreads, 2) flux_kernel(FluxArgs a) {
     }
 }
 
-template <int NV, int DIR>
+template <int NV, int DIR, bool SMALL>
 cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
-    constexpr int TI = Tile<NV, DIR>::TI, TA = Tile<NV, DIR>::TA;
+    constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int NC = (TI + 5) * TA;
     constexpr size_t smem = size_t(NC) * CellPlanes<NV>::kPerCell * sizeof(double);
     // the dynamic shared-memory limit is a per-device function attribute
@@ -103,7 +106,7 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(flux_kernel<NV, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(flux_kernel<NV, DIR, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem));
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
@@ -113,16 +116,31 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     const unsigned along = unsigned((n + 1 + TI - 1) / TI);
     const unsigned across = unsigned((nlines + TA - 1) / TA);
     dim3 grid = DIR == 0 ? dim3(along, across) : dim3(across, along);
-    flux_kernel<NV, DIR><<<grid, kThreads, smem, s>>>(a);
+    flux_kernel<NV, DIR, SMALL><<<grid, Tile<NV, DIR, SMALL>::THREADS, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+int sm_count_cached() {
+    static int sms = 0;
+    if (sms > 0) return sms;
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+        sms = v;
+    return sms > 0 ? sms : 152;
 }
 
 }  // namespace
 
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s) {
-    if (system == 0) return launch_one<1, 0>(a, s);
-    if (system == 1) return launch_one<3, 0>(a, s);
-    return dir == 0 ? launch_one<4, 0>(a, s) : launch_one<4, 1>(a, s);
+    if (system != 2) {
+        // 1D: short lines take the small tiles so that every SM has work
+        const int64_t big_tiles = (int64_t(a.nx) + 512) / 512 * a.ny;
+        const bool small = big_tiles < 2 * sm_count_cached();
+        if (system == 0) return small ? launch_one<1, 0, true>(a, s) : launch_one<1, 0, false>(a, s);
+        return small ? launch_one<3, 0, true>(a, s) : launch_one<3, 0, false>(a, s);
+    }
+    return dir == 0 ? launch_one<4, 0, false>(a, s) : launch_one<4, 1, false>(a, s);
 }
 
 }  // namespace wz

@@ -19,10 +19,10 @@ inline int nvar_of(int system) { return system == WENOZN_ADVECTION_1D ? 1 : (sys
 
 // Workspace regions of wenozn_rhs / wenozn_rk3_step, followed by the extra regions the
 // adjoint entry points use (per-interface cotangent contributions, per-block partial sums,
-// the argmax index and two cotangent vectors).
+// two control words and two cotangent vectors).
 struct Layout {
     size_t ctrl, u1, u2, fx, gy, total;                 // forward
-    size_t C, partial, argmax, ub2, ub1, total_vjp;     // adjoint (1D only)
+    size_t C, partial, vjp_ctl, ub2, ub1, total_vjp;    // adjoint (1D only)
 };
 
 inline Layout layout_of(const wenozn_problem& p) {
@@ -36,9 +36,9 @@ inline Layout layout_of(const wenozn_problem& p) {
     L.gy = L.fx + align_up(nv * (nx + 1) * ny * sizeof(double));
     L.total = L.gy + (p.system == WENOZN_EULER_2D ? align_up(nv * nx * (ny + 1) * sizeof(double)) : 0);
     L.C = L.total;
-    L.partial = L.C + align_up((nx + 1) * 6 * nv * sizeof(double));
-    L.argmax = L.partial + align_up(size_t(vjp_interface_blocks(int(nx))) * sizeof(double));
-    L.ub2 = L.argmax + kAlign;
+    L.partial = L.C + align_up(vjp_contrib_doubles(int(nv), int(nx)) * sizeof(double));
+    L.vjp_ctl = L.partial + align_up(size_t(vjp_partial_count(int(nx))) * sizeof(double));
+    L.ub2 = L.vjp_ctl + kAlign;
     L.ub1 = L.ub2 + align_up(nv * nx * sizeof(double));
     L.total_vjp = L.ub1 + align_up(nv * nx * sizeof(double));
     return L;

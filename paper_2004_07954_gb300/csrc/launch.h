@@ -78,19 +78,20 @@ cudaError_t launch_batch_stage(int shape, const BatchArgs& a, int sms, cudaStrea
 struct VjpArgs {
     const double* U;                       // stage input, [nv][n]
     const double* lam;                     // cotangent of L(U), [nv][n]
-    double* C;                             // [n+1][6][nv] per-interface contributions
-    double* partial;                       // [nblocks] partial sums of the LF-speed cotangent
-    int* argmax;                           // lowest index of the LF-speed maximum
+    double* C;                             // per-interface contributions, vjp_contrib_doubles(nv, n)
+    double* partial;                       // [vjp_partial_count(n)] partial sums of the LF-speed cotangent
+    unsigned* ctl;                         // {~argmax of the LF speed, finished gather blocks}; zero between launches
     const unsigned long long* alpha_bits;  // LF speed of U (bit pattern)
     double* out;                           // c1 X1 + c2 X2 + c3 X3 + d J^T lam
     const double* X1;
     const double* X2;
     const double* X3;
     double c1, c2, c3, d;
-    int n, bc, nblocks;
+    int n, bc, fast_rcp;
     double rdx, gamma, eps4, A4, adv_speed;
 };
-int vjp_interface_blocks(int n);
+int vjp_partial_count(int n);
+size_t vjp_contrib_doubles(int nv, int n);
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
 
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);

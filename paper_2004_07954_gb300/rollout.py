@@ -4,9 +4,9 @@
 library's forward kernels and is differentiable with respect to U0: its backward pass runs
 the hand-written adjoint kernels (wenozn_rk3_step_vjp) step by step in reverse.  Forward
 states are kept every `checkpoint_every` steps; the backward pass recomputes the states of
-one segment from its checkpoint and walks it backwards, so memory holds
-steps/checkpoint_every + checkpoint_every states (checkpoint_every = 1 keeps every state and
-recomputes nothing).  The time step is an input, not a function of U0 (the adjoint's
+one segment from its checkpoint (with its stage inputs) and walks it backwards, so memory
+holds steps/checkpoint_every + 3 checkpoint_every states; checkpoint_every = 1 keeps every
+step's three stage inputs and LF speeds and recomputes nothing.  The time step is an input, not a function of U0 (the adjoint's
 convention); choose it from the initial state, e.g. with `cfl_step`.
 """
 from __future__ import annotations
@@ -23,30 +23,52 @@ class WenoZNRollout(torch.autograd.Function):
     def forward(ctx, U0, p, dt, steps, checkpoint_every, ws):
         U = U0.detach().clone().contiguous()
         every = max(1, int(checkpoint_every))
-        checkpoints = [U.clone()]
-        for k in range(steps):
-            W.wenozn_rk3_step(p, U, ws, dt=dt)
-            if (k + 1) % every == 0 and k + 1 < steps:
-                checkpoints.append(U.clone())
         ctx.p, ctx.dt, ctx.steps, ctx.every, ctx.ws = p, dt, steps, every, ws
-        ctx.checkpoints = checkpoints
+        if every == 1:
+            # keep every step's stage inputs and LF speeds: the reverse pass recomputes nothing
+            ctx.stages = _run_keep_stages(p, ws, U, dt, steps)
+        else:
+            checkpoints = [U.clone()]
+            for k in range(steps):
+                W.wenozn_rk3_step(p, U, ws, dt=dt)
+                if (k + 1) % every == 0 and k + 1 < steps:
+                    checkpoints.append(U.clone())
+            ctx.checkpoints = checkpoints
         return U
 
     @staticmethod
     def backward(ctx, gU):
         lam = gU.detach().clone().contiguous()
         p, dt, ws, every = ctx.p, ctx.dt, ctx.ws, ctx.every
+        if every == 1:
+            S0, S1, S2, A = ctx.stages
+            for k in reversed(range(ctx.steps)):
+                W.wenozn_rk3_step_vjp_stages(p, S0[k], S1[k], S2[k], A[k], dt, lam, ws)
+            return lam, None, None, None, None, None
         nseg = math.ceil(ctx.steps / every)
         for seg in reversed(range(nseg)):
             k0, k1 = seg * every, min(ctx.steps, (seg + 1) * every)
-            states = [ctx.checkpoints[seg]]
             U = ctx.checkpoints[seg].clone()
-            for _ in range(k0, k1 - 1):
-                W.wenozn_rk3_step(p, U, ws, dt=dt)
-                states.append(U.clone())
-            for k in reversed(range(k0, k1)):
-                W.wenozn_rk3_step_vjp(p, states[k - k0], dt, lam, ws)
+            S0, S1, S2, A = _run_keep_stages(p, ws, U, dt, k1 - k0)
+            for k in reversed(range(k1 - k0)):
+                W.wenozn_rk3_step_vjp_stages(p, S0[k], S1[k], S2[k], A[k], dt, lam, ws)
         return lam, None, None, None, None, None
+
+
+def _run_keep_stages(p, ws, U, dt, steps):
+    """Advances U in place by `steps` steps, returning every step's stage inputs
+    (U^n, U^(1), U^(2)) and LF speeds, copied out of the workspace."""
+    S0 = torch.empty((steps,) + tuple(U.shape), dtype=U.dtype, device=U.device)
+    S1, S2 = torch.empty_like(S0), torch.empty_like(S0)
+    A = torch.empty((steps, 3), dtype=U.dtype, device=U.device)
+    V1, V2, VA = W.workspace_stages(p, ws)
+    for k in range(steps):
+        S0[k].copy_(U)
+        W.wenozn_rk3_step(p, U, ws, dt=dt)
+        S1[k].copy_(V1)
+        S2[k].copy_(V2)
+        A[k].copy_(VA)
+    return S0, S1, S2, A
 
 
 def rollout(U0: torch.Tensor, p: W.wenozn_problem, dt: float, steps: int, checkpoint_every: int = 1,

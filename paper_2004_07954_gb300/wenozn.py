@@ -71,6 +71,9 @@ _SIGNATURES = {
     "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_step_vjp_stages": [_P, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_workspace_stages": [_VP, _P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                ctypes.POINTER(ctypes.c_void_p)],
     "wenozn_batch_shape": [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "wenozn_batch_workspace_size": [ctypes.POINTER(wenozn_batch_params), _VP, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_batch_init": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
@@ -279,6 +282,27 @@ def wenozn_rk3_step_vjp(p: wenozn_problem, U: torch.Tensor, dt: float, lam: torc
     _check("wenozn_rk3_step_vjp", lib().wenozn_rk3_step_vjp(ctypes.byref(p), _dev_ptr(U, "U"), float(dt),
                                                             _dev_ptr(lam, "lam"), _ws_ptr(ws), ws.numel(),
                                                             _stream(stream)))
+
+
+def wenozn_rk3_step_vjp_stages(p: wenozn_problem, U: torch.Tensor, U1: torch.Tensor, U2: torch.Tensor,
+                               alphas: torch.Tensor, dt: float, lam: torch.Tensor, ws: torch.Tensor,
+                               stream=None) -> None:
+    _check("wenozn_rk3_step_vjp_stages", lib().wenozn_rk3_step_vjp_stages(
+        ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(U1, "U1"), _dev_ptr(U2, "U2"), _dev_ptr(alphas, "alphas"),
+        float(dt), _dev_ptr(lam, "lam"), _ws_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def workspace_stages(p: wenozn_problem, ws: torch.Tensor):
+    """Views (U1, U2, alphas[3]) of the last forward RK3 step's stage inputs and LF speeds."""
+    u1, u2, al = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check("wenozn_workspace_stages", lib().wenozn_workspace_stages(_ws_ptr(ws), ctypes.byref(p), ctypes.byref(u1),
+                                                                    ctypes.byref(u2), ctypes.byref(al)))
+    nb = p.nvar * p.nx * p.ny * 8
+    base = ws.data_ptr()
+    U1 = ws[u1.value - base:u1.value - base + nb].view(torch.float64).view(p.shape)
+    U2 = ws[u2.value - base:u2.value - base + nb].view(torch.float64).view(p.shape)
+    A = ws[al.value - base:al.value - base + 48].view(torch.float64)[0::2]
+    return U1, U2, A
 
 
 # ------------------------------------------------------------------------- convenience

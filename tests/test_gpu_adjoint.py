@@ -90,6 +90,28 @@ def test_rk3_step_vjp_dot_product(wz, orc, system, bc):
         assert b == pytest.approx(a, rel=1e-10)
 
 
+@pytest.mark.parametrize("system,bc", [(1, 0), (1, 1), (0, 0)])
+def test_rk3_step_vjp_from_stored_stages_is_bit_identical(wz, system, bc):
+    """The reverse step fed with the forward step's stored stage inputs and LF speeds equals
+    the reverse step that recomputes them, bit for bit."""
+    n = 1000
+    p = wz.wenozn_problem_init(system, n, 1, 10.0 / n, 1.0, bc_x=bc)
+    U = dev(inputs.adjoint_ic(n, seed=14) if system == 1 else _state(0, n, 14))
+    dt = 0.3 * p.dx
+    lam = dev(np.random.default_rng(5).normal(size=tuple(U.shape)))
+    ws = wz.vjp_workspace(p)
+    l1 = lam.clone()
+    wz.wenozn_rk3_step_vjp(p, U, dt, l1, ws)
+    U1n = U.clone()
+    wz.wenozn_rk3_step(p, U1n, ws, dt=dt)
+    S1, S2, A = (t.clone() for t in wz.workspace_stages(p, ws))
+    l2 = lam.clone()
+    wz.wenozn_rk3_step_vjp_stages(p, U, S1, S2, A, dt, l2, ws)
+    assert torch.equal(l1, l2)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_rk3_step_vjp_stages(p, U, S1, S2, A, dt, S1, ws)
+
+
 def _loss_grad(wz, p, U0, dt, steps, target, every=1):
     from paper_2004_07954_gb300.rollout import rollout
     U = dev(U0).requires_grad_(True)
