@@ -161,6 +161,18 @@ wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const double* U, doubl
 wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, double t_remaining,
                               double* dt_out, void* ws, size_t ws_bytes, void* stream);
 
+/* One SSP-RK3 step with the fixed step dt > 0, out of place, keeping what its reverse
+ * (wenozn_rk3_step_vjp_stages) needs:
+ *   U       : device, [nvar][ny][nx], the state U^n (read only);
+ *   U_next  : device, same shape, receives U^{n+1};
+ *   U1, U2  : device, same shape, receive the stage inputs U^(1), U^(2);
+ *   alphas  : device, 3 doubles, receive the LF speeds of U^n, U^(1), U^(2) (x direction).
+ * The five state arrays must be pairwise distinct (EINVAL otherwise).  Results equal those
+ * of wenozn_rk3_step with the same dt bit for bit. */
+wenozn_status wenozn_rk3_step_keep(const wenozn_problem* p, const double* U, double* U_next, double dt,
+                                   double* U1, double* U2, double* alphas, void* ws, size_t ws_bytes,
+                                   void* stream);
+
 /* Device address of the FP64 time step the last wenozn_rk3_step on this workspace took. */
 const double* wenozn_workspace_dt(const void* ws);
 
@@ -178,8 +190,9 @@ wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, 
  * --------------------------------------------------------------------------------------- */
 
 /* Workspace bytes of wenozn_rhs_vjp / wenozn_rk3_step_vjp: the forward workspace of
- * wenozn_workspace_size followed by per-interface cotangent contributions ([n+1][6][nvar]),
- * per-block partial sums, an index and two state-sized cotangent vectors.  A workspace of
+ * wenozn_workspace_size followed by per-interface cotangent contributions (12 doubles per
+ * interface for advection, 42 for Euler), per-block partial sums, two control words and two
+ * state-sized cotangent vectors.  A workspace of
  * this size also serves wenozn_rhs and wenozn_rk3_step. */
 wenozn_status wenozn_vjp_workspace_size(const wenozn_problem* p, size_t* bytes);
 

@@ -14,6 +14,7 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     v.n = p.nx;
     v.bc = p.bc_x;
     v.fast_rcp = zn_fast_rcp(p.eps, p.A);
+    v.nblocks = vjp_partial_count(p.nx);
     v.rdx = 1.0 / p.dx;
     v.gamma = p.gamma;
     v.eps4 = 4.0 * p.eps;
@@ -41,7 +42,7 @@ wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws,
     double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
     double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
     VjpArgs v = vjp_args(p, L, ws);
-    cudaError_t e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return WENOZN_ECUDA;
     // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
     v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
@@ -84,7 +85,7 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
     VjpArgs v = vjp_args(*p, L, ws);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) {
         v.U = U;
         v.lam = lam;

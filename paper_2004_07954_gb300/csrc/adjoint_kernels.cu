@@ -17,8 +17,8 @@ namespace wz {
 
 namespace {
 
-// Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), adds dW/df * Wb to fb
-// and returns W(f).
+// Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), writes dW/df * Wb to
+// fb[0..4] and returns W(f).
 __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double A4, int fast,
                                                   double* fb) {
     const double a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
@@ -28,57 +28,73 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
     const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
     const double k13_3 = 13.0 / 3.0;
-    const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));
-    const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
-    const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
+    const double ks0 = k13_3 * s0, ks1 = k13_3 * s1, ks2 = k13_3 * s2;
+    const double b0 = fma(ks0, s0, fma(t0, t0, eps4));
+    const double b1 = fma(ks1, s1, fma(t1, t1, eps4));
+    const double b2 = fma(ks2, s2, fma(t2, t2, eps4));
     const double d4 = t0 + t2;
-    const double sg = b0 > b2 ? 1.0 : (b0 < b2 ? -1.0 : 0.0);   // sign(IS_0 - IS_2), 0 on ties
-    const double mn = fmin(b0, b2), mx = fmax(b0, b2);
+    // b0, b2 > 0 order like their bit patterns: min/max and sign(IS_0 - IS_2) (0 on ties) on
+    // the integer pipe
+#ifdef __CUDA_ARCH__
+    const long long i0 = __double_as_longlong(b0), i2 = __double_as_longlong(b2);
+#else
+    const double i0 = b0, i2 = b2;
+#endif
+    const double mn = i0 < i2 ? b0 : b2, mx = i0 < i2 ? b2 : b0;
+    const double sg = i0 > i2 ? 1.0 : (i0 < i2 ? -1.0 : 0.0);
     const double P = (mx - mn) + eps4;
     const double m = fma(2.0, mn, -eps4);
-    const double b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1;
-    const double K = (A4 * m) * m;
-    const double X = K * (b01 * b2);
+    const double b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1, b012 = b01 * b2;
+    const double Am = A4 * m;
+    const double K = Am * m;
+    const double X = K * b012;
     const double z = d4 * P;
     const double Y = z * z;
     const double a0 = fma(Y, b12, X), a1 = fma(Y, b02, X), a2 = fma(Y, b01, X);
+    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
     const double q0 = fma(1.0 / 12.0, s0, fma(0.25, t0, c));
-    const double q1 = fma(0.5, s1, fma(-1.5, t1, 6.0 * c));
-    const double q2 = fma(0.25, s2, fma(-0.75, t2, 3.0 * c));
+    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
+    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
     const double N = fma(a0, q0, fma(a1, q1, a2 * q2));
     const double D = fma(6.0, a1, fma(3.0, a2, a0));
     const double rD = fast ? rcp_nr(D) : 1.0 / D;
     const double W = N * rD;
     // reverse
-    const double Nb = Wb * rD, Db = -Wb * W * rD;
+    const double Nb = Wb * rD, Db = -Nb * W;
     const double a0b = fma(Nb, q0, Db), a1b = fma(Nb, q1, 6.0 * Db), a2b = fma(Nb, q2, 3.0 * Db);
     const double q0b = Nb * a0, q1b = Nb * a1, q2b = Nb * a2;
-    const double Xb = a0b + a1b + a2b;
+    const double Xb = (a0b + a1b) + a2b;
     const double Yb = fma(a0b, b12, fma(a1b, b02, a2b * b01));
     const double XK = Xb * K;
     double b0b = fma(Y, fma(a1b, b2, a2b * b1), XK * b12);
-    double b1b = fma(Y, fma(a0b, b2, a2b * b0), XK * b02);
+    const double b1b = fma(Y, fma(a0b, b2, a2b * b0), XK * b02);
     double b2b = fma(Y, fma(a0b, b1, a1b * b0), XK * b01);
-    const double mb = Xb * (b01 * b2) * (2.0 * A4 * m);
-    const double zb = 2.0 * z * Yb;
+    const double mb = (Xb * b012) * (Am + Am);      // X = A4 m^2 b0 b1 b2
+    const double zb = (z + z) * Yb;
     const double d4b = zb * P, Pb = zb * d4;
-    const double taub = Pb - mb;                    // P = tau + eps4, m = b0 + b2 - tau - eps4
-    b0b += mb + sg * taub;
-    b2b += mb - sg * taub;
-    double s0b = b0b * (2.0 * k13_3) * s0, s1b = b1b * (2.0 * k13_3) * s1, s2b = b2b * (2.0 * k13_3) * s2;
-    double t0b = b0b * 2.0 * t0 + d4b, t1b = b1b * 2.0 * t1, t2b = b2b * 2.0 * t2 + d4b;
-    const double cb = q0b + 6.0 * q1b + 3.0 * q2b;
-    s0b += q0b / 12.0;
-    t0b += 0.25 * q0b;
-    s1b += 0.5 * q1b;
-    t1b -= 1.5 * q1b;
-    s2b += 0.25 * q2b;
-    t2b -= 0.75 * q2b;
-    fb[0] += s0b + t0b;
-    fb[1] += -2.0 * s0b + s1b - 4.0 * t0b + t1b;
-    fb[2] += cb + s0b - 2.0 * s1b + s2b + 3.0 * t0b + 3.0 * t2b;
-    fb[3] += s1b - 2.0 * s2b - t1b - 4.0 * t2b;
-    fb[4] += s2b + t2b;
+    // P = tau + eps4, m = b0 + b2 - tau - eps4, tau = |b0 - b2|
+    const double taub = Pb - mb;
+    b0b = fma(sg, taub, b0b + mb);
+    b2b = fma(-sg, taub, b2b + mb);
+    // b_k = (13/3) s_k^2 + t_k^2 + eps4; q_k; d4 = t0 + t2
+    const double s0b = fma(1.0 / 12.0, q0b, (b0b + b0b) * ks0);
+    const double s1b = fma(0.5, q1b, (b1b + b1b) * ks1);
+    const double s2b = fma(0.25, q2b, (b2b + b2b) * ks2);
+    const double t0b = fma(0.25, q0b, fma(b0b + b0b, t0, d4b));
+    const double t1b = fma(-1.5, q1b, (b1b + b1b) * t1);
+    const double t2b = fma(-0.75, q2b, fma(b2b + b2b, t2, d4b));
+    const double cb = fma(3.0, q2b, fma(6.0, q1b, q0b));
+    // back through the differences: s_k = D_{k+1} - D_{k+2}, t0 = D1 - 3 D2, t1 = D2 + D3,
+    // t2 = 3 D3 - D4, D_k = f_{k-1} - f_k
+    const double D1b = s0b + t0b;
+    const double D2b = fma(-3.0, t0b, (s1b - s0b) + t1b);
+    const double D3b = fma(3.0, t2b, (s2b - s1b) + t1b);
+    const double D4b = -(s2b + t2b);
+    fb[0] = D1b;
+    fb[1] = D2b - D1b;
+    fb[2] = (D3b - D2b) + cb;
+    fb[3] = D4b - D3b;
+    fb[4] = -D4b;
     return W;
 }
 
@@ -103,10 +119,11 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
 // ---------------------------------------------------------------------------------------
 constexpr int kTI = 32;                 // interfaces per block (one warp per field)
 constexpr int kCells = kTI + 5;         // cells j0-3 .. j0+kTI+1
-constexpr int kGather = 256;            // cells per gather block
+constexpr int kGather = 64;             // cells per gather block (small blocks spread the FP64 work)
 constexpr int kRoe = 36;                // first Roe plane (Euler)
 
 struct EulerSmem {
+    double U[3][kCells];
     double hp[3][kCells], hm[3][kCells];
     double u[kCells], H[kCells], sq[kCells], r[kCells];
     double red[3][36][kTI];             // per field: hbar+ (5 x 3), hbar- (5 x 3), 6 Roe scalars
@@ -123,7 +140,10 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         const int g = j0 - 3 + c;
         const int src = ghost_src(g, n, a.bc);
         double s[3];
-        for (int m = 0; m < 3; ++m) s[m] = a.U[int64_t(m) * n + src];
+        for (int m = 0; m < 3; ++m) {
+            s[m] = a.U[int64_t(m) * n + src];
+            sm.U[m][c] = s[m];
+        }
         const double r = 1.0 / s[0];
         const double u = s[1] * r;
         const double p = gm1 * (s[2] - 0.5 * s[1] * u);
@@ -157,8 +177,9 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         wr = sr * rS;
         ut = fma(wl, sm.u[cl], wr * sm.u[cr]);
         Ht = fma(wl, sm.H[cl], wr * sm.H[cr]);
-        c = sqrt(gm1 * fma(-0.5 * ut, ut, Ht));
-        rc = rcp_nr(c);
+        const double c2 = gm1 * fma(-0.5 * ut, ut, Ht);
+        rc = rsqrt(c2);
+        c = c2 * rc;
         b1 = gm1 * rc * rc;
         const double b2 = 0.5 * ut * ut * b1;
         double L0, L1, L2, R1, R2;
@@ -179,7 +200,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             Fb[m] = (right - left) * a.rdx;
         }
         const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
-        double fp[5], fm[5], fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
+        double fp[5], fm[5], fpb[5], fmb[5];
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
@@ -215,47 +236,61 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         sm.red[k][33][i] = utb; sm.red[k][34][i] = cb; sm.red[k][35][i] = Htb;
     }
     __syncthreads();
-    if (!live) return;
-    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-
+    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-, and this
+    // interface's share sum_s U_s . (hbar+ - hbar-)_s / 2 of the LF-speed cotangent
+    double ab = 0.0;
+    if (live) {
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int s = 2 * k + t;
+        for (int t = 0; t < 2; ++t) {
+            const int s = 2 * k + t;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const double hpb = s <= 4 ? (sm.red[0][s * 3 + m][i] + sm.red[1][s * 3 + m][i]) + sm.red[2][s * 3 + m][i] : 0.0;
-            const double hmb = s >= 1 ? (sm.red[0][12 + s * 3 + m][i] + sm.red[1][12 + s * 3 + m][i]) +
-                                            sm.red[2][12 + s * 3 + m][i] : 0.0;
-            a.C[(s * 6 + m) * P + j] = 0.5 * (hpb + hmb);
-            a.C[(s * 6 + 3 + m) * P + j] = 0.5 * (hpb - hmb);
+            for (int m = 0; m < 3; ++m) {
+                const double hpb = s <= 4 ? (sm.red[0][s * 3 + m][i] + sm.red[1][s * 3 + m][i]) + sm.red[2][s * 3 + m][i]
+                                          : 0.0;
+                const double hmb = s >= 1 ? (sm.red[0][12 + s * 3 + m][i] + sm.red[1][12 + s * 3 + m][i]) +
+                                                sm.red[2][12 + s * 3 + m][i] : 0.0;
+                const double dh = 0.5 * (hpb - hmb);
+                a.C[(s * 6 + m) * P + j] = 0.5 * (hpb + hmb);
+                a.C[(s * 6 + 3 + m) * P + j] = dh;
+                ab = fma(sm.U[m][i + s], dh, ab);
+            }
         }
     }
-    if (k == 0) return;
-    // Roe average (warps 1 and 2 both reverse it; 1 writes the left cell, 2 the right):
-    // b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2))
-    double sc[6];
+    if (live && k > 0) {
+        // Roe average (warps 1 and 2 both reverse it; 1 writes the left cell, 2 the right):
+        // b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2))
+        double sc[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
-    double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
-    utb = fma(b2b * ut, b1, utb);
-    b1b = fma(b2b * 0.5 * ut, ut, b1b);
-    rcb = fma(b1b * 2.0 * gm1, rc, rcb);
-    cb = fma(-rcb * rc, rc, cb);
-    const double cq = cb * gm1 * 0.5 * rc;
-    Htb += cq;
-    utb = fma(-cq, ut, utb);
-    // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
-    const int cc = k == 1 ? cl : cr;
-    const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
-    const double ub = utb * w, Hb = Htb * w;
-    const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
-    // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
-    const double Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
-    const double Um = r * fma(-gm1 * uc, Hb, ub);
-    const double UE = a.gamma * r * Hb;
-    double* roe = a.C + (kRoe + 3 * (k - 1)) * P + j;
-    roe[0] = Ur;
-    roe[P] = Um;
-    roe[2 * P] = UE;
+        for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
+        double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
+        utb = fma(b2b * ut, b1, utb);
+        b1b = fma(b2b * 0.5 * ut, ut, b1b);
+        rcb = fma(b1b * 2.0 * gm1, rc, rcb);
+        cb = fma(-rcb * rc, rc, cb);
+        const double cq = cb * gm1 * 0.5 * rc;
+        Htb += cq;
+        utb = fma(-cq, ut, utb);
+        // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
+        const int cc = k == 1 ? cl : cr;
+        const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
+        const double ub = utb * w, Hb = Htb * w;
+        const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
+        // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
+        const double Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
+        const double Um = r * fma(-gm1 * uc, Hb, ub);
+        const double UE = a.gamma * r * Hb;
+        double* roe = a.C + (kRoe + 3 * (k - 1)) * P + j;
+        roe[0] = Ur;
+        roe[P] = Um;
+        roe[2 * P] = UE;
+    }
+    // deterministic per-block partial of the LF-speed cotangent (sm.red is free again)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ab += __shfl_down_sync(0xffffffffu, ab, o);
+    __syncthreads();
+    if (i == 0) sm.red[0][0][k] = ab;
+    __syncthreads();
+    if (tid == 0) a.partial[blockIdx.x] = (sm.red[0][0][0] + sm.red[0][0][1]) + sm.red[0][0][2];
 }
 
 __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
@@ -273,7 +308,7 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
     if (j > n) return;
     const double right = j < n ? a.lam[j] : 0.0, left = j > 0 ? a.lam[j - 1] : 0.0;
     const double Fb = (right - left) * a.rdx;
-    double fp[5], fm[5], fpb[5] = {0, 0, 0, 0, 0}, fmb[5] = {0, 0, 0, 0, 0};
+    double fp[5], fm[5], fpb[5], fmb[5];
     for (int s = 0; s < 5; ++s) {
         fp[s] = hp[i + s];
         fm[4 - s] = hm[i + s + 1];
@@ -287,62 +322,63 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kGather / 32; ++w) t += red[w];
-    __syncthreads();
-    return t;                               // valid in thread 0
-}
-
 // Per cell i: sum the contributions of the stencil positions that map to it (ghost cells
 // included, fixed order), apply J_F^T to the flux part, add alpha times the LF part and the
 // Roe part, and write out_i = c1 X1_i + c2 X2_i + c3 X3_i + d (J^T lambda)_i.  For Euler the
-// LF-speed cotangent sum_i U_i . (LF part)_i is reduced in a fixed order; the last block to
-// finish adds its term at the argmax cell (d(|u| + c)/dU, |x|' = 0 at 0) and resets the
-// control words.
+// block holding the argmax cell of the LF speed also sums the interface kernel's partials of
+// the LF-speed cotangent (fixed order), adds its term d(|u| + c)/dU there (|x|' = 0 at 0) and
+// clears the argmax word.
 template <int NV>
 __global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
     constexpr int Q = 2 * NV;
-    __shared__ double red[kGather / 32];
-    __shared__ bool last;
     const int n = a.n;
     const int64_t P = int64_t(n) + 1;
     const int i = blockIdx.x * kGather + threadIdx.x;
-    double ab = 0.0;
+    double Ub[NV];
     if (i < n) {
         double Fs[NV], Ds[NV], Rs[NV];
         for (int m = 0; m < NV; ++m) Fs[m] = Ds[m] = Rs[m] = 0.0;
-        int gs[16], ng = 0;                 // stencil cells g (in -3 .. n+2) that map to i
-        if (n <= 8) {
-            for (int g = -3; g <= n + 2; ++g)
-                if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
-        } else if (a.bc == 0) {
-            for (int g = i - n; g <= i + n; g += n)
-                if (g >= -3 && g <= n + 2) gs[ng++] = g;
-        } else {
-            gs[ng++] = i;
-            if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
-            if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
-        }
-        for (int q = 0; q < ng; ++q) {
-            const int g = gs[q];
+        if (i >= 3 && i <= n - 4) {
+            // interior: the cell is stencil position s of interface i + 3 - s only
+#pragma unroll
             for (int s = 0; s < 6; ++s) {
-                const int j = g + 3 - s;             // interface whose stencil position s is g
-                if (j < 0 || j > n) continue;
+                const int64_t j = i + 3 - s;
+#pragma unroll
                 for (int m = 0; m < NV; ++m) {
                     Fs[m] += a.C[(s * Q + m) * P + j];
                     Ds[m] += a.C[(s * Q + NV + m) * P + j];
                 }
-                if (NV == 3 && (s == 2 || s == 3))
-                    for (int m = 0; m < NV; ++m) Rs[m] += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
+            }
+            if (NV == 3)
+#pragma unroll
+                for (int m = 0; m < NV; ++m) Rs[m] = a.C[(kRoe + 3 + m) * P + i] + a.C[(kRoe + m) * P + i + 1];
+        } else {
+            int gs[16], ng = 0;             // stencil cells g (in -3 .. n+2) that map to i
+            if (n <= 8) {
+                for (int g = -3; g <= n + 2; ++g)
+                    if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
+            } else if (a.bc == 0) {
+                for (int g = i - n; g <= i + n; g += n)
+                    if (g >= -3 && g <= n + 2) gs[ng++] = g;
+            } else {
+                gs[ng++] = i;
+                if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
+                if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
+            }
+            for (int q = 0; q < ng; ++q) {
+                const int g = gs[q];
+                for (int s = 0; s < 6; ++s) {
+                    const int j = g + 3 - s;         // interface whose stencil position s is g
+                    if (j < 0 || j > n) continue;
+                    for (int m = 0; m < NV; ++m) {
+                        Fs[m] += a.C[(s * Q + m) * P + j];
+                        Ds[m] += a.C[(s * Q + NV + m) * P + j];
+                    }
+                    if (NV == 3 && (s == 2 || s == 3))
+                        for (int m = 0; m < NV; ++m) Rs[m] += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
+                }
             }
         }
-        double Ub[NV];
         if (NV == 1) {
             Ub[0] = fma(a.adv_speed, Fs[0], fabs(a.adv_speed) * Ds[0]);
         } else {
@@ -362,56 +398,54 @@ __global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
             Ub[0] = fma(alpha, Ds[0], rb) + Rs[0];
             Ub[1] = fma(alpha, Ds[1], mb) + Rs[1];
             Ub[2] = fma(alpha, Ds[2], Eb) + Rs[2];
-            ab = fma(rho, Ds[0], fma(mom, Ds[1], E * Ds[2]));
-        }
-        for (int m = 0; m < NV; ++m) {
-            const int64_t idx = int64_t(m) * n + i;
-            double v = a.d * Ub[m];
-            if (a.X1) v = fma(a.c1, a.X1[idx], v);
-            if (a.X2) v = fma(a.c2, a.X2[idx], v);
-            if (a.X3) v = fma(a.c3, a.X3[idx], v);
-            a.out[idx] = v;
         }
     }
-    if (NV == 1) return;
-    const double part = block_sum(ab, red);
-    if (threadIdx.x == 0) {
-        a.partial[blockIdx.x] = part;
-        __threadfence();
-        last = atomicAdd(&a.ctl[1], 1u) == gridDim.x - 1;
+    if (NV == 3) {
+        const unsigned key = a.ctl[0];
+        const int im = key ? int(~key) : -1;
+        if (im >= 0 && im / kGather == int(blockIdx.x)) {     // uniform over the block
+            __shared__ double red[kGather / 32];
+            double v = 0.0;
+            for (int b = threadIdx.x; b < a.nblocks; b += kGather) v += a.partial[b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (i == im) {
+                double abar = 0.0;
+                for (int w = 0; w < kGather / 32; ++w) abar += red[w];
+                const double rho = a.U[i], mom = a.U[n + i], E = a.U[2 * int64_t(n) + i];
+                const double u = mom / rho;
+                const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
+                const double c = sqrt(a.gamma * p / rho);
+                const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
+                const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
+                Ub[0] += abar * (sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho));
+                Ub[1] += abar * (sg / rho - kk * gm1 * u);
+                Ub[2] += abar * (kk * gm1);
+                a.ctl[0] = 0u;
+            }
+        }
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int b = threadIdx.x; b < int(gridDim.x); b += kGather) v += static_cast<volatile double*>(a.partial)[b];
-    const double abar = block_sum(v, red);
-    if (threadIdx.x != 0) return;
-    const unsigned key = static_cast<volatile unsigned*>(a.ctl)[0];
-    if (key != 0u) {
-        const int im = int(~key);
-        const double rho = a.U[im], mom = a.U[n + im], E = a.U[2 * int64_t(n) + im];
-        const double u = mom / rho;
-        const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
-        const double c = sqrt(a.gamma * p / rho);
-        const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
-        const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
-        const double g3[3] = {sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho), sg / rho - kk * gm1 * u, kk * gm1};
-        volatile double* out = a.out;
-        for (int m = 0; m < 3; ++m) out[int64_t(m) * n + im] = fma(a.d * abar, g3[m], out[int64_t(m) * n + im]);
+    if (i >= n) return;
+    for (int m = 0; m < NV; ++m) {
+        const int64_t idx = int64_t(m) * n + i;
+        double v = a.d * Ub[m];
+        if (a.X1) v = fma(a.c1, a.X1[idx], v);
+        if (a.X2) v = fma(a.c2, a.X2[idx], v);
+        if (a.X3) v = fma(a.c3, a.X3[idx], v);
+        a.out[idx] = v;
     }
-    a.ctl[0] = 0u;
-    a.ctl[1] = 0u;
 }
 
 }  // namespace
 
-int vjp_partial_count(int n) { return (n + kGather - 1) / kGather; }
+int vjp_partial_count(int n) { return (n + 1 + kTI - 1) / kTI; }
 
 size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12 : 42); }
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
-    const unsigned gi = unsigned((a.n + 1 + kTI - 1) / kTI), gc = unsigned(vjp_partial_count(a.n));
+    const unsigned gi = unsigned(vjp_partial_count(a.n)), gc = unsigned((a.n + kGather - 1) / kGather);
     if (system == 0) {
         vjp_interface_advection<<<gi, kTI, 0, s>>>(a);
         vjp_gather_kernel<1><<<gc, kGather, 0, s>>>(a);

@@ -8,6 +8,41 @@
 using namespace wz;
 
 
+namespace {
+
+// The three SSP-RK3 stages: U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
+// U_out = 1/3 U + 2/3 (U2 + dt L(U2)); U_out may alias U.  The LF speeds of U, U1, U2 land in
+// the control block's slots 0, 1, 2 and the step taken in its dt word.
+cudaError_t rk3_stages(const wenozn_problem& p, const Layout& lay, void* ws, const double* U, double* U_out,
+                       double* u1, double* u2, double dt, double t_remaining, cudaStream_t s) {
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    double* fx = reinterpret_cast<double*>(ws_base(ws) + lay.fx);
+    double* gy = reinterpret_cast<double*>(ws_base(ws) + lay.gy);
+    const bool euler = p.system != WENOZN_ADVECTION_1D;
+    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p.system, U, int64_t(p.nx) * p.ny, p.gamma, p.adv_speed, ctrl->alpha[0],
+                                 &ctrl->status, s);
+    const double* stage_in[3] = {U, u1, u2};
+    double* stage_out[3] = {u1, u2, U_out};
+    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+        e = launch_fluxes(p, stage_in[stage], ctrl->alpha[stage], fx, gy, s);
+        if (e != cudaSuccess) break;
+        UpdateArgs u = update_args(p, ctrl, fx, gy);
+        u.mode = stage + 1;
+        u.Us = stage_in[stage];
+        u.Un = U;
+        u.out = stage_out[stage];
+        u.next_slot = (euler && stage < 2) ? stage + 1 : -1;
+        u.dt_fixed = dt;
+        u.t_remaining = t_remaining;
+        e = launch_update(p.system, u, s);
+    }
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 wenozn_status wenozn_problem_init(wenozn_problem* p, int32_t system, int32_t nx, int32_t ny,
@@ -128,36 +163,33 @@ wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, dou
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
     double* u1 = reinterpret_cast<double*>(ws_base(ws) + lay.u1);
     double* u2 = reinterpret_cast<double*>(ws_base(ws) + lay.u2);
-    double* fx = reinterpret_cast<double*>(ws_base(ws) + lay.fx);
-    double* gy = reinterpret_cast<double*>(ws_base(ws) + lay.gy);
-    const bool euler = p->system != WENOZN_ADVECTION_1D;
-
-    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
-    if (e == cudaSuccess)
-        e = launch_max_wavespeed(p->system, U, int64_t(p->nx) * p->ny, p->gamma, p->adv_speed,
-                                 ctrl->alpha[0], &ctrl->status, s);
-    const double* stage_in[3] = {U, u1, u2};
-    double* stage_out[3] = {u1, u2, U};
-    for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
-        e = launch_fluxes(*p, stage_in[stage], ctrl->alpha[stage], fx, gy, s);
-        if (e != cudaSuccess) break;
-        UpdateArgs u = update_args(*p, ctrl, fx, gy);
-        u.mode = stage + 1;
-        u.Us = stage_in[stage];
-        u.Un = U;
-        u.out = stage_out[stage];
-        u.next_slot = (euler && stage < 2) ? stage + 1 : -1;
-        u.dt_fixed = dt;
-        u.t_remaining = t_remaining;
-        e = launch_update(p->system, u, s);
-    }
-    if (e != cudaSuccess) return WENOZN_ECUDA;
+    if (rk3_stages(*p, lay, ws, U, U, u1, u2, dt, t_remaining, s) != cudaSuccess) return WENOZN_ECUDA;
     if (dt_out) {
-        e = cudaMemcpyAsync(dt_out, &ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(dt_out, &ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return WENOZN_ECUDA;
     }
     return WENOZN_OK;
+}
+
+wenozn_status wenozn_rk3_step_keep(const wenozn_problem* p, const double* U, double* U_next, double dt,
+                                   double* U1, double* U2, double* alphas, void* ws, size_t ws_bytes,
+                                   void* stream) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!U || !U_next || !U1 || !U2 || !alphas || !ws || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
+    if (U_next == U || U1 == U || U2 == U || U1 == U_next || U2 == U_next || U1 == U2) return WENOZN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    const Layout lay = layout_of(*p);
+    if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    cudaError_t e = rk3_stages(*p, lay, ws, U, U_next, U1, U2, dt, 0.0, s);
+    // the three stages' x speeds: alpha[s][0], s = 0, 1, 2 (a stride of two words)
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(alphas, sizeof(double), &ctrl->alpha[0][0], 2 * sizeof(unsigned long long),
+                              sizeof(double), 3, cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
 }
 
 const double* wenozn_workspace_dt(const void* ws) {

@@ -79,15 +79,15 @@ struct VjpArgs {
     const double* U;                       // stage input, [nv][n]
     const double* lam;                     // cotangent of L(U), [nv][n]
     double* C;                             // per-interface contributions, vjp_contrib_doubles(nv, n)
-    double* partial;                       // [vjp_partial_count(n)] partial sums of the LF-speed cotangent
-    unsigned* ctl;                         // {~argmax of the LF speed, finished gather blocks}; zero between launches
+    double* partial;                       // [nblocks] per-interface-block partial sums of the LF-speed cotangent
+    unsigned* ctl;                         // ctl[0]: ~(argmax of the LF speed); zero between launches
     const unsigned long long* alpha_bits;  // LF speed of U (bit pattern)
     double* out;                           // c1 X1 + c2 X2 + c3 X3 + d J^T lam
     const double* X1;
     const double* X2;
     const double* X3;
     double c1, c2, c3, d;
-    int n, bc, fast_rcp;
+    int n, bc, fast_rcp, nblocks;          // nblocks = vjp_partial_count(n)
     double rdx, gamma, eps4, A4, adv_speed;
 };
 int vjp_partial_count(int n);

@@ -36,8 +36,8 @@ __device__ __forceinline__ double step_dt(const UpdateArgs& a, int system) {
     return dt;
 }
 
-template <int NV>
-__global__ void __launch_bounds__(kThreads) update_kernel(UpdateArgs a) {
+template <int NV, int T>
+__global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
     const int system = NV == 1 ? 0 : (NV == 3 ? 1 : 2);
     double dt = 0.0;
     if (a.mode == 1) {
@@ -51,8 +51,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(UpdateArgs a) {
     const int64_t sy = int64_t(a.ny + 1) * a.nx;         // y-flux plane stride
     double mx = 0.0, my = 0.0;
     bool bad = false;
-    for (int64_t cell = blockIdx.x * int64_t(kThreads) + threadIdx.x; cell < nc;
-         cell += int64_t(gridDim.x) * kThreads) {
+    for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
         const int64_t j = cell / a.nx, i = cell - j * a.nx;
         const int64_t fx = j * (a.nx + 1) + i;
         double o[NV];
@@ -88,15 +87,12 @@ __global__ void __launch_bounds__(kThreads) update_kernel(UpdateArgs a) {
     if (NV != 1 && a.next_slot >= 0) block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
 }
 
-template <int NV>
-__global__ void __launch_bounds__(kThreads) max_wavespeed_kernel(const double* U, int64_t nc,
-                                                                  double gamma,
-                                                                  unsigned long long* dst,
-                                                                  int32_t* status) {
+template <int NV, int T>
+__global__ void __launch_bounds__(T) max_wavespeed_kernel(const double* U, int64_t nc, double gamma,
+                                                          unsigned long long* dst, int32_t* status) {
     double mx = 0.0, my = 0.0;
     bool bad = false;
-    for (int64_t cell = blockIdx.x * int64_t(kThreads) + threadIdx.x; cell < nc;
-         cell += int64_t(gridDim.x) * kThreads) {
+    for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
         double s[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] = U[k * nc + cell];
@@ -160,8 +156,8 @@ __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int 
     }
 }
 
-unsigned grid_for(int64_t items, int cap) {
-    int64_t b = (items + kThreads - 1) / kThreads;
+unsigned grid_for(int64_t items, int cap, int threads = kThreads) {
+    int64_t b = (items + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > cap) b = cap;
     return unsigned(b);
@@ -176,12 +172,32 @@ int sm_count() {
 
 }  // namespace
 
+// The per-cell kernels are FP64-pipe bound: with fewer than two 256-thread blocks per SM
+// they run 64-thread blocks instead, so that the work spreads over all SMs.
+bool few_cells(int64_t nc, int sms) { return nc < int64_t(sms) * 2 * kThreads; }
+
+template <int NV>
+void update_nv(const UpdateArgs& a, int64_t nc, cudaStream_t s) {
+    const int sms = sm_count();
+    if (few_cells(nc, sms)) update_kernel<NV, 64><<<grid_for(nc, sms * 32, 64), 64, 0, s>>>(a);
+    else update_kernel<NV, kThreads><<<grid_for(nc, sms * 8), kThreads, 0, s>>>(a);
+}
+
+template <int NV>
+void max_wavespeed_nv(const double* U, int64_t nc, double gamma, unsigned long long* dst, int32_t* status,
+                      cudaStream_t s) {
+    const int sms = sm_count();
+    if (few_cells(nc, sms))
+        max_wavespeed_kernel<NV, 64><<<grid_for(nc, sms * 16, 64), 64, 0, s>>>(U, nc, gamma, dst, status);
+    else
+        max_wavespeed_kernel<NV, kThreads><<<grid_for(nc, sms * 4), kThreads, 0, s>>>(U, nc, gamma, dst, status);
+}
+
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
     const int64_t nc = int64_t(a.nx) * a.ny;
-    const unsigned grid = grid_for(nc, sm_count() * 8);
-    if (system == 0) update_kernel<1><<<grid, kThreads, 0, s>>>(a);
-    else if (system == 1) update_kernel<3><<<grid, kThreads, 0, s>>>(a);
-    else update_kernel<4><<<grid, kThreads, 0, s>>>(a);
+    if (system == 0) update_nv<1>(a, nc, s);
+    else if (system == 1) update_nv<3>(a, nc, s);
+    else update_nv<4>(a, nc, s);
     return cudaGetLastError();
 }
 
@@ -192,9 +208,8 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
         abs_speed_kernel<<<1, 32, 0, s>>>(adv_speed, dst);
         return cudaGetLastError();
     }
-    const unsigned grid = grid_for(ncells, sm_count() * 4);
-    if (system == 1) max_wavespeed_kernel<3><<<grid, kThreads, 0, s>>>(U, ncells, gamma, dst, status);
-    else max_wavespeed_kernel<4><<<grid, kThreads, 0, s>>>(U, ncells, gamma, dst, status);
+    if (system == 1) max_wavespeed_nv<3>(U, ncells, gamma, dst, status, s);
+    else max_wavespeed_nv<4>(U, ncells, gamma, dst, status, s);
     return cudaGetLastError();
 }
 

@@ -57,18 +57,15 @@ class WenoZNRollout(torch.autograd.Function):
 
 def _run_keep_stages(p, ws, U, dt, steps):
     """Advances U in place by `steps` steps, returning every step's stage inputs
-    (U^n, U^(1), U^(2)) and LF speeds, copied out of the workspace."""
-    S0 = torch.empty((steps,) + tuple(U.shape), dtype=U.dtype, device=U.device)
-    S1, S2 = torch.empty_like(S0), torch.empty_like(S0)
+    (U^n, U^(1), U^(2)) and LF speeds, written there by the out-of-place step."""
+    X = torch.empty((steps + 1,) + tuple(U.shape), dtype=U.dtype, device=U.device)
+    S1, S2 = torch.empty_like(X[:steps]), torch.empty_like(X[:steps])
     A = torch.empty((steps, 3), dtype=U.dtype, device=U.device)
-    V1, V2, VA = W.workspace_stages(p, ws)
+    X[0].copy_(U)
     for k in range(steps):
-        S0[k].copy_(U)
-        W.wenozn_rk3_step(p, U, ws, dt=dt)
-        S1[k].copy_(V1)
-        S2[k].copy_(V2)
-        A[k].copy_(VA)
-    return S0, S1, S2, A
+        W.wenozn_rk3_step_keep(p, X[k], X[k + 1], dt, S1[k], S2[k], A[k], ws)
+    U.copy_(X[steps])
+    return X[:steps], S1, S2, A
 
 
 def rollout(U0: torch.Tensor, p: W.wenozn_problem, dt: float, steps: int, checkpoint_every: int = 1,

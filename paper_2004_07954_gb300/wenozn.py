@@ -71,6 +71,7 @@ _SIGNATURES = {
     "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_step_keep": [_P, _VP, _VP, ctypes.c_double, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp_stages": [_P, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_stages": [_VP, _P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                 ctypes.POINTER(ctypes.c_void_p)],
@@ -282,6 +283,14 @@ def wenozn_rk3_step_vjp(p: wenozn_problem, U: torch.Tensor, dt: float, lam: torc
     _check("wenozn_rk3_step_vjp", lib().wenozn_rk3_step_vjp(ctypes.byref(p), _dev_ptr(U, "U"), float(dt),
                                                             _dev_ptr(lam, "lam"), _ws_ptr(ws), ws.numel(),
                                                             _stream(stream)))
+
+
+def wenozn_rk3_step_keep(p: wenozn_problem, U: torch.Tensor, U_next: torch.Tensor, dt: float, U1: torch.Tensor,
+                         U2: torch.Tensor, alphas: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    _check("wenozn_rk3_step_keep", lib().wenozn_rk3_step_keep(
+        ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(U_next, "U_next"), float(dt), _dev_ptr(U1, "U1"),
+        _dev_ptr(U2, "U2"), _dev_ptr(alphas, "alphas"), _ws_ptr(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
 
 
 def wenozn_rk3_step_vjp_stages(p: wenozn_problem, U: torch.Tensor, U1: torch.Tensor, U2: torch.Tensor,

@@ -112,6 +112,28 @@ def test_rk3_step_vjp_from_stored_stages_is_bit_identical(wz, system, bc):
         wz.wenozn_rk3_step_vjp_stages(p, U, S1, S2, A, dt, S1, ws)
 
 
+@pytest.mark.parametrize("system,bc", [(1, 0), (1, 1), (0, 0)])
+def test_rk3_step_keep_matches_in_place_step(wz, system, bc):
+    """The out-of-place step that keeps its stage inputs gives the in-place step's state,
+    stage buffers and LF speeds bit for bit, and leaves its input untouched."""
+    n = 777
+    p = wz.wenozn_problem_init(system, n, 1, 10.0 / n, 1.0, bc_x=bc)
+    U = dev(inputs.adjoint_ic(n, seed=15) if system == 1 else _state(0, n, 15))
+    U0 = U.clone()
+    dt = 0.3 * p.dx
+    ws = wz.vjp_workspace(p)
+    Un, S1, S2 = torch.empty_like(U), torch.empty_like(U), torch.empty_like(U)
+    A = torch.empty(3, dtype=torch.float64, device="cuda")
+    wz.wenozn_rk3_step_keep(p, U, Un, dt, S1, S2, A, ws)
+    assert torch.equal(U, U0)
+    V = U.clone()
+    wz.wenozn_rk3_step(p, V, ws, dt=dt)
+    W1, W2, WA = wz.workspace_stages(p, ws)
+    assert torch.equal(Un, V) and torch.equal(S1, W1) and torch.equal(S2, W2) and torch.equal(A, WA)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_rk3_step_keep(p, U, U, dt, S1, S2, A, ws)
+
+
 def _loss_grad(wz, p, U0, dt, steps, target, every=1):
     from paper_2004_07954_gb300.rollout import rollout
     U = dev(U0).requires_grad_(True)
