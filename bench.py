@@ -40,7 +40,7 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "ef47758b859bdf82", "n": 4096, "bytes": 966e6}
+TRAFFIC_CAPTURE = {"sha256_16": "69e1410c0a104936", "n": 4096, "bytes": 964.3e6}
 
 
 def kernel_source_hash() -> str:
@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-fd-dirs", type=int, default=20)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--only", choices=["batched", "adjoint"], default=None,
+                    help="run only this part and print its object (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
 
@@ -257,9 +260,16 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
     h = 1e-7
     x = (np.arange(n) + 0.5) * (10.0 / n) - 5.0
     checks = {}
+
+    def fd_at(v, hh):
+        vt = torch.from_numpy(v).cuda()
+        lp = 0.5 * float(((fwd_only(U0 + hh * vt)[0] - target) ** 2).sum())
+        lm = 0.5 * float(((fwd_only(U0 - hh * vt)[0] - target) ** 2).sum())
+        return (lp - lm) / (2 * hh)
+
     with torch.no_grad():
-        for kind in ("smooth", "white"):
-            worst = 0.0
+        for kind in (("smooth", "white") if fd_dirs > 0 else ()):
+            worst, worst_big_h = 0.0, 0.0
             for _ in range(fd_dirs):
                 if kind == "smooth":      # a few random Fourier modes per variable, scaled like U0
                     v = np.zeros_like(u0)
@@ -269,13 +279,17 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
                         v[k, 0] *= np.abs(u0[k, 0]).mean()
                 else:
                     v = gen.normal(size=u0.shape) * np.abs(u0)
-                vt = torch.from_numpy(v).cuda()
-                lp = 0.5 * float(((fwd_only(U0 + h * vt)[0] - target) ** 2).sum())
-                lm = 0.5 * float(((fwd_only(U0 - h * vt)[0] - target) ** 2).sum())
-                fd = (lp - lm) / (2 * h)
                 gv = float(np.sum(grad * v))
+                fd = fd_at(v, h)
                 worst = max(worst, abs(gv - fd) / abs(fd))
+                if kind == "white":
+                    # the loss barely responds to cell-to-cell noise, so at h = 1e-7 the
+                    # difference of the two rollouts is near their rounding; h = 1e-5 shows it
+                    fd5 = fd_at(v, 1e-5)
+                    worst_big_h = max(worst_big_h, abs(gv - fd5) / abs(fd5))
             checks[kind] = {"directions": fd_dirs, "max_rel_err": worst}
+            if kind == "white":
+                checks[kind]["max_rel_err_h_1e-5"] = worst_big_h
     return {"workload": f"1D Euler N={n}, seeded smooth periodic multi-wave state, {steps} SSP-RK3 steps of "
                         f"fixed dt (CFL 0.5 of U0), loss 1/2||rho(T) - rho_target||^2, rho_target from seed+1",
             "forward_s": round(t_fwd, 4), "store_all": res[1], "checkpoint_every_50": res[50],
@@ -369,6 +383,17 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _b.build()
+    if args.only is not None:
+        if args.only == "batched":
+            part = bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
+        else:
+            part = bench_adjoint(wenozn, inputs, args.seed + rank, steps=args.adjoint_steps,
+                                 fd_dirs=args.adjoint_fd_dirs)
+        if rank == 0:
+            print(json.dumps({"part": args.only, **part}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     def barrier():
         if world > 1:
@@ -467,7 +492,7 @@ def main():
 
     batched = None if args.no_batched else bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
     adjoint = None if args.no_adjoint else bench_adjoint(wenozn, inputs, args.seed + rank,
-                                                         fd_dirs=args.adjoint_fd_dirs)
+                                                         steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
