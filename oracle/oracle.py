@@ -22,9 +22,10 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-W_ZN, W_Z, W_LINEAR = 0, 1, 2
+W_ZN, W_Z, W_LINEAR, W_JS = 0, 1, 2, 3
 ADV1D, EULER1D, EULER2D = 0, 1, 2
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, REFLECTIVE = 0, 1, 2
+S_LF, S_LF_FIELD, S_LLF, S_SW = 0, 1, 2, 3      # flux splittings
 
 
 def build(force: bool = False) -> str:
@@ -41,14 +42,14 @@ def build(force: bool = False) -> str:
 class Problem(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("weights", ctypes.c_int32),
-                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("split", ctypes.c_int32), ("pad", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("eps", ctypes.c_double), ("A", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("adv_speed", ctypes.c_double)]
 
 
 def problem(system, nx, ny=1, dx=1.0, dy=1.0, bc_x=OUTFLOW, bc_y=OUTFLOW, weights=W_ZN,
-            gamma=1.4, eps=1e-40, A=10.0, cfl=0.5, adv_speed=1.0) -> Problem:
-    return Problem(system, nx, ny, bc_x, bc_y, weights, dx, dy, gamma, eps, A, cfl, adv_speed)
+            gamma=1.4, eps=1e-40, A=10.0, cfl=0.5, adv_speed=1.0, split=S_LF) -> Problem:
+    return Problem(system, nx, ny, bc_x, bc_y, weights, split, 0, dx, dy, gamma, eps, A, cfl, adv_speed)
 
 
 def nvar(system: int) -> int:
@@ -85,6 +86,9 @@ def lib():
                 "oracle_opcount_rhs": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
                 "oracle_opcount_parts": (None, [ctypes.c_int, _D]),
                 "oracle_rhs_jvp": (None, [_P, _D, _D, _D, _D]),
+                "oracle_steger_warming": (None, [_D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]),
+                "oracle_field_speed": (ctypes.c_double, [_P, _D, ctypes.c_int, ctypes.c_int]),
+                "oracle_rhs_speeds": (None, [_P, _D, _D, _D]),
                 "oracle_rhs_jvp_quad": (None, [_P, _D, _D, _D, _D]),
                 "oracle_rollout_jvp_quad": (None, [_P, _D, _D, ctypes.c_double, ctypes.c_int64]),
                 "oracle_rollout_jvp": (None, [_P, _D, _D, ctypes.c_double, ctypes.c_int64]),
@@ -241,3 +245,26 @@ def rollout_jvp_quad(P: Problem, U, dU, dt, steps):
     u, du = _f64(U).copy(), _f64(dU).copy()
     lib().oracle_rollout_jvp_quad(ctypes.byref(P), _ptr(u), _ptr(du), float(dt), int(steps))
     return u, du
+
+
+def steger_warming(U, sign, gamma=1.4) -> np.ndarray:
+    """Steger-Warming F+ (sign > 0) or F- (sign < 0) of one state in the direction frame."""
+    u = _f64(U)
+    out = np.zeros_like(u)
+    lib().oracle_steger_warming(_ptr(u), u.shape[0], gamma, int(sign), _ptr(out))
+    return out
+
+
+def field_speed(P: Problem, U, direction=0, kind=0) -> float:
+    """max |lambda_kind| over the grid, kind 0: u_n - c, 1: u_n, 2: u_n + c."""
+    u = _f64(U)
+    return lib().oracle_field_speed(ctypes.byref(P), _ptr(u), int(direction), int(kind))
+
+
+def rhs_speeds(P: Problem, U, ax, ay=0.0, fx=(0.0, 0.0, 0.0), fy=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """RHS with the LF speeds given instead of computed from U."""
+    u = _f64(U)
+    sp = _f64([ax, ay, *fx, *fy])
+    out = np.zeros_like(u)
+    lib().oracle_rhs_speeds(ctypes.byref(P), _ptr(u), _ptr(sp), _ptr(out))
+    return out

@@ -126,7 +126,7 @@ template <> inline DualQ tabs<DualQ>(DualQ x) { return tabs_dual(x); }
 // ---------------------------------------------------------------------------------------
 // Sec. 2.1 / Sec. 3: one fifth-order reconstruction f^+_{i+1/2} from (f_{i-2},...,f_{i+2}).
 // ---------------------------------------------------------------------------------------
-enum WeightKind { W_ZN = 0, W_Z = 1, W_LINEAR = 2 };
+enum WeightKind { W_ZN = 0, W_Z = 1, W_LINEAR = 2, W_JS = 3 };
 
 template <class T> struct WenoParts {
     T q[3], IS[3], tau5, tau8, C, alpha[3], omega[3], fhat;
@@ -175,6 +175,8 @@ WenoParts<T> weno5(const T f[5], T eps, T A, int kind) {
             r.alpha[k] = c[k] * (r.C + r.tau8 / (r.IS[k] + eps));
         else if (kind == W_Z)    // Eq. (15) with q = 1
             r.alpha[k] = c[k] * (T(1) + r.tau5 / (r.IS[k] + eps));
+        else if (kind == W_JS)   // Sec. 2.1, the Jiang-Shu weights c_k / (IS_k + eps)^2
+            r.alpha[k] = c[k] / ((r.IS[k] + eps) * (r.IS[k] + eps));
         else                     // linear fifth-order upwind scheme
             r.alpha[k] = c[k];
     }
@@ -198,17 +200,34 @@ T weno5_minus(const T f_im1_to_ip3[5], T eps, T A, int kind) {
 // ---------------------------------------------------------------------------------------
 struct Problem {
     int32_t system, nx, ny, bc_x, bc_y, weights;   // weights: WeightKind
+    int32_t split, pad;                            // split: SplitKind
     double dx, dy, gamma, eps, A, cfl, adv_speed;
 };
 enum { SYS_ADV1D = 0, SYS_EULER1D = 1, SYS_EULER2D = 2 };
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2 };
+// Flux splitting: global Lax-Friedrichs with one speed per direction (the hot path), global
+// LF with one speed per characteristic field, local LF with the largest |u| + c of the
+// interface's six stencil cells, and Steger-Warming flux-vector splitting (Sec. 4.4).
+enum SplitKind { S_LF = 0, S_LF_FIELD = 1, S_LLF = 2, S_SW = 3 };
 
 inline int nvar_of(int system) { return system == SYS_ADV1D ? 1 : (system == SYS_EULER1D ? 3 : 4); }
 
-// Ghost-cell index map: periodic wrap (Sec. 4.2) or zero-order extrapolation (outflow).
+// Ghost-cell index map: periodic wrap (Sec. 4.2), zero-order extrapolation (outflow), or
+// the mirror image across the wall (reflective: cell -1-i for i < 0, 2n-1-i for i >= n,
+// repeated, i.e. the grid continued with period 2n and mirrored in every other copy).
 inline int64_t ghost_src(int64_t i, int64_t n, int bc) {
     if (bc == BC_PERIODIC) return ((i % n) + n) % n;
+    if (bc == BC_REFLECTIVE) {
+        const int64_t m = ((i % (2 * n)) + 2 * n) % (2 * n);
+        return m < n ? m : 2 * n - 1 - m;
+    }
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+// A reflective ghost that is a mirror image carries the opposite normal momentum.
+inline bool ghost_mirrored(int64_t i, int64_t n, int bc) {
+    if (bc != BC_REFLECTIVE) return false;
+    const int64_t m = ((i % (2 * n)) + 2 * n) % (2 * n);
+    return m >= n;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -307,11 +326,42 @@ Eigen<T> roe_eigen(const T* UL, const T* UR, int nv, T gamma) {
                           enthalpy(r), nv, gamma);
 }
 
-// Per-cell quantities of one padded grid line, each computed once per cell:
-// the split fluxes h+- = (F +- alpha U)/2 (LF splitting, Sec. 2 and Sec. 4.3) and, for the
-// Euler systems, the Roe-average ingredients sqrt(rho), u_n, u_t, H.
+// Steger-Warming splitting of the flux normal to the interface (Steger & Warming 1981, the
+// splitting of Sec. 4.4): with the eigenvalues l1 = u - c, l2 = u, l3 = u + c and
+// l+- = (l +- |l|)/2,
+//   F+- = rho/(2 gamma) ( 2(gamma-1) l2 + l1 + l3,
+//                         2(gamma-1) l2 u + l1 (u - c) + l3 (u + c),
+//                        [2(gamma-1) l2 v + l1 v + l3 v,]
+//                         (gamma-1) l2 q^2 + l1 ((u-c)^2 + v^2)/2 + l3 ((u+c)^2 + v^2)/2
+//                           + (3 - gamma)(l1 + l3) c^2 / (2 (gamma - 1)) )      (l = l+-),
+// q^2 = u^2 + v^2 (v = 0 in 1D); F+ + F- = F.
+template <class T>
+void steger_warming(const Prim<T>& w, int nv, T gamma, int sign, T* Fs) {
+    const T c = sound_speed(w, gamma);
+    const T u = w.un, v = w.ut;
+    const T lam[3] = {u - c, u, u + c};
+    T l[3];
+    for (int k = 0; k < 3; ++k) l[k] = cst<T>(1, 2) * (lam[k] + T(sign) * tabs(lam[k]));
+    const T g1 = gamma - T(1);
+    const T q2 = nv == 4 ? u * u + v * v : u * u;
+    const T k0 = w.rho / (T(2) * gamma);
+    Fs[0] = k0 * (T(2) * g1 * l[1] + l[0] + l[2]);
+    Fs[1] = k0 * (T(2) * g1 * l[1] * u + l[0] * (u - c) + l[2] * (u + c));
+    if (nv == 4) Fs[2] = k0 * (T(2) * g1 * l[1] * v + l[0] * v + l[2] * v);
+    const T um = u - c, up = u + c;
+    const T vv = nv == 4 ? v * v : T(0);
+    Fs[nv - 1] = k0 * (g1 * l[1] * q2 + cst<T>(1, 2) * l[0] * (um * um + vv) + cst<T>(1, 2) * l[2] * (up * up + vv)
+                       + (T(3) - gamma) * (l[0] + l[2]) * c * c / (T(2) * g1));
+}
+
+// Per-cell quantities of one padded grid line, each computed once per cell, by splitting:
+//   S_LF       hp, hm = (F +- alpha U)/2 (LF splitting, Sec. 2 and Sec. 4.3);
+//   S_LF_FIELD, S_LLF: hp = F, hm = U (split per field or per interface after projection),
+//              and for S_LLF the cell's |u_n| + c in `speed`;
+//   S_SW       hp, hm = F+, F- (Steger-Warming);
+// and, for the Euler systems, the Roe-average ingredients sqrt(rho), u_n, u_t, H.
 template <class T> struct LineCells {
-    std::vector<T> hp, hm, srho, un, ut, H;
+    std::vector<T> hp, hm, srho, un, ut, H, speed;
 };
 
 template <class T>
@@ -327,15 +377,26 @@ void line_cells(const Problem& P, const T* Ul, int64_t np, int nv, T alpha, Line
         return;
     }
     const T gamma = T(P.gamma);
-    lc.srho.resize(np); lc.un.resize(np); lc.ut.resize(np); lc.H.resize(np);
+    lc.srho.resize(np); lc.un.resize(np); lc.ut.resize(np); lc.H.resize(np); lc.speed.resize(np);
     for (int64_t p = 0; p < np; ++p) {
         const T* U = &Ul[p * nv];
         Prim<T> w = primitives(U, nv, gamma);
         T F[4];
         normal_flux(U, w, nv, F);
-        for (int m = 0; m < nv; ++m) {
-            lc.hp[p * nv + m] = cst<T>(1, 2) * (F[m] + alpha * U[m]);
-            lc.hm[p * nv + m] = cst<T>(1, 2) * (F[m] - alpha * U[m]);
+        if (P.split == S_LF) {
+            for (int m = 0; m < nv; ++m) {
+                lc.hp[p * nv + m] = cst<T>(1, 2) * (F[m] + alpha * U[m]);
+                lc.hm[p * nv + m] = cst<T>(1, 2) * (F[m] - alpha * U[m]);
+            }
+        } else if (P.split == S_SW) {
+            steger_warming(w, nv, gamma, +1, &lc.hp[p * nv]);
+            steger_warming(w, nv, gamma, -1, &lc.hm[p * nv]);
+        } else {
+            for (int m = 0; m < nv; ++m) {
+                lc.hp[p * nv + m] = F[m];
+                lc.hm[p * nv + m] = U[m];
+            }
+            lc.speed[p] = tabs(w.un) + sound_speed(w, gamma);
         }
         lc.srho[p] = tsqrt(w.rho);
         lc.un[p] = w.un;
@@ -345,8 +406,11 @@ void line_cells(const Problem& P, const T* Ul, int64_t np, int nv, T alpha, Line
 }
 
 // Numerical flux at the interface between padded cells i and i+1 of one grid line.
+// alpha_f: the per-field LF speeds of the sweep (S_LF_FIELD), indexed by eigenvalue kind
+// (0: u - c, 1: u, 2: u + c).
 template <class T>
-void interface_flux(const Problem& P, const LineCells<T>& lc, int nv, int64_t i, T* Fhat) {
+void interface_flux(const Problem& P, const LineCells<T>& lc, int nv, int64_t i, T* Fhat,
+                    const T* alpha_f = nullptr) {
     const T eps = T(P.eps), A = T(P.A);
     if (P.system == SYS_ADV1D) {
         // f^+ from cells i-2..i+2, f^- from the mirrored cells i+3..i-1
@@ -360,16 +424,40 @@ void interface_flux(const Problem& P, const LineCells<T>& lc, int nv, int64_t i,
     // characteristic projection with the interface's left eigenvectors:
     // g+ of cells i-2..i+2 and g- of cells i-1..i+3
     T gp[5][4], gm[5][4];
-    for (int s = 0; s < 5; ++s)
-        for (int k = 0; k < nv; ++k) {
-            T accp = T(0), accm = T(0);
-            for (int m = 0; m < nv; ++m) {
-                accp += e.Lm[k][m] * lc.hp[(i - 2 + s) * nv + m];
-                accm += e.Lm[k][m] * lc.hm[(i - 1 + s) * nv + m];
+    if (P.split == S_LF || P.split == S_SW) {
+        for (int s = 0; s < 5; ++s)
+            for (int k = 0; k < nv; ++k) {
+                T accp = T(0), accm = T(0);
+                for (int m = 0; m < nv; ++m) {
+                    accp += e.Lm[k][m] * lc.hp[(i - 2 + s) * nv + m];
+                    accm += e.Lm[k][m] * lc.hm[(i - 1 + s) * nv + m];
+                }
+                gp[s][k] = accp;
+                gm[s][k] = accm;
             }
-            gp[s][k] = accp;
-            gm[s][k] = accm;
+    } else {
+        // project F and U of cells i-2..i+3, then split each field with its own speed:
+        // g+- = (l_k.F +- alpha_k l_k.U)/2
+        T alpha_k[4];
+        const int kind3[3] = {0, 1, 2}, kind4[4] = {0, 1, 1, 2};   // eigenvalue of each field
+        if (P.split == S_LLF) {
+            T a = lc.speed[i - 2];
+            for (int s = 1; s < 6; ++s) a = tmax(a, lc.speed[i - 2 + s]);
+            for (int k = 0; k < nv; ++k) alpha_k[k] = a;
+        } else {
+            for (int k = 0; k < nv; ++k) alpha_k[k] = alpha_f[nv == 3 ? kind3[k] : kind4[k]];
         }
+        for (int s = 0; s < 6; ++s)
+            for (int k = 0; k < nv; ++k) {
+                T gF = T(0), gU = T(0);
+                for (int m = 0; m < nv; ++m) {
+                    gF += e.Lm[k][m] * lc.hp[(i - 2 + s) * nv + m];
+                    gU += e.Lm[k][m] * lc.hm[(i - 2 + s) * nv + m];
+                }
+                if (s <= 4) gp[s][k] = cst<T>(1, 2) * (gF + alpha_k[k] * gU);
+                if (s >= 1) gm[s - 1][k] = cst<T>(1, 2) * (gF - alpha_k[k] * gU);
+            }
+    }
     T ghat[4];
     for (int k = 0; k < nv; ++k) {
         T fp[5] = {gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k]};
@@ -401,11 +489,47 @@ T max_wavespeed(const Problem& P, const T* U, int dir) {
     return best;
 }
 
+// Largest |lambda| of one eigenvalue kind (0: u_n - c, 1: u_n, 2: u_n + c) over the
+// interior: the per-field LF speeds.
+template <class T>
+T max_field_speed(const Problem& P, const T* U, int dir, int kind) {
+    const int nv = nvar_of(P.system);
+    const int64_t nc = int64_t(P.nx) * P.ny;
+    T best = T(0);
+    for (int64_t c = 0; c < nc; ++c) {
+        T s[4];
+        for (int k = 0; k < nv; ++k) s[k] = U[k * nc + c];
+        if (dir == 1) std::swap(s[1], s[2]);
+        Prim<T> w = primitives(s, nv, T(P.gamma));
+        const T cs = sound_speed(w, T(P.gamma));
+        const T lam = kind == 0 ? w.un - cs : (kind == 1 ? w.un : w.un + cs);
+        best = tmax(best, tabs(lam));
+    }
+    return best;
+}
+
+// The speeds a splitting needs for one stage input: the global LF speeds per direction and,
+// for S_LF_FIELD, the per-field ones (x then y, three kinds each).
+template <class T> struct Speeds { T ax, ay; T fx[3], fy[3]; };
+
+template <class T>
+Speeds<T> stage_speeds(const Problem& P, const T* U) {
+    Speeds<T> a{};
+    a.ax = max_wavespeed(P, U, 0);
+    a.ay = P.system == SYS_EULER2D ? max_wavespeed(P, U, 1) : T(0);
+    if (P.split == S_LF_FIELD && P.system != SYS_ADV1D)
+        for (int k = 0; k < 3; ++k) {
+            a.fx[k] = max_field_speed(P, U, 0, k);
+            if (P.system == SYS_EULER2D) a.fy[k] = max_field_speed(P, U, 1, k);
+        }
+    return a;
+}
+
 // Semi-discrete right-hand side, Eq. (2) (and its 2D form, Sec. 4.4):
 // Lout = -(F^_{i+1/2} - F^_{i-1/2})/dx [- (G^_{j+1/2} - G^_{j-1/2})/dy].
-// alpha_x/alpha_y are the global LF speeds of this stage input.
+// `a` holds the LF speeds of this stage input.
 template <class T>
-void rhs_with_alpha(const Problem& P, const T* U, T* Lout, T alpha_x, T alpha_y) {
+void rhs_with_speeds(const Problem& P, const T* U, T* Lout, const Speeds<T>& a) {
     const int nv = nvar_of(P.system);
     const int64_t nx = P.nx, ny = P.ny, nc = nx * ny;
     // x-sweep, one grid row at a time
@@ -416,10 +540,11 @@ void rhs_with_alpha(const Problem& P, const T* U, T* Lout, T alpha_x, T alpha_y)
         for (int64_t p = 0; p < nx + 6; ++p) {
             int64_t src = ghost_src(p - 3, nx, P.bc_x);
             for (int k = 0; k < nv; ++k) line[p * nv + k] = U[k * nc + j * nx + src];
+            if (nv > 1 && ghost_mirrored(p - 3, nx, P.bc_x)) line[p * nv + 1] = -line[p * nv + 1];
         }
-        line_cells(P, line.data(), nx + 6, nv, alpha_x, lc);
+        line_cells(P, line.data(), nx + 6, nv, a.ax, lc);
         for (int64_t f = 0; f <= nx; ++f)   // interface f - 1/2, between padded cells f+2, f+3
-            interface_flux(P, lc, nv, f + 2, &flux[f * nv]);
+            interface_flux(P, lc, nv, f + 2, &flux[f * nv], a.fx);
         for (int64_t i = 0; i < nx; ++i)
             for (int k = 0; k < nv; ++k)
                 Lout[k * nc + j * nx + i] = -((flux[(i + 1) * nv + k] - flux[i * nv + k]) / T(P.dx));
@@ -434,10 +559,11 @@ void rhs_with_alpha(const Problem& P, const T* U, T* Lout, T alpha_x, T alpha_y)
         for (int64_t p = 0; p < ny + 6; ++p) {
             int64_t src = ghost_src(p - 3, ny, P.bc_y);
             for (int k = 0; k < nv; ++k) line[p * nv + k] = U[perm[k] * nc + src * nx + i];
+            if (ghost_mirrored(p - 3, ny, P.bc_y)) line[p * nv + 1] = -line[p * nv + 1];
         }
-        line_cells(P, line.data(), ny + 6, nv, alpha_y, lc);
+        line_cells(P, line.data(), ny + 6, nv, a.ay, lc);
         for (int64_t f = 0; f <= ny; ++f)
-            interface_flux(P, lc, nv, f + 2, &flux[f * nv]);
+            interface_flux(P, lc, nv, f + 2, &flux[f * nv], a.fy);
         for (int64_t j = 0; j < ny; ++j)
             for (int k = 0; k < nv; ++k)
                 Lout[perm[k] * nc + j * nx + i] = Lout[perm[k] * nc + j * nx + i]
@@ -447,9 +573,7 @@ void rhs_with_alpha(const Problem& P, const T* U, T* Lout, T alpha_x, T alpha_y)
 
 template <class T>
 void rhs(const Problem& P, const T* U, T* Lout) {
-    T ax = max_wavespeed(P, U, 0);
-    T ay = P.system == SYS_EULER2D ? max_wavespeed(P, U, 1) : T(0);
-    rhs_with_alpha(P, U, Lout, ax, ay);
+    rhs_with_speeds(P, U, Lout, stage_speeds(P, U));
 }
 
 // CFL time step: 1D Sec. 4.3, 2D Sec. 4.4, advection dx*cfl/|a|.
@@ -714,6 +838,25 @@ void oracle_opcount_parts(int system, double* out) {
     OpCount d = -((F[0] - F[0]) / OpCount(0.1));
     (void)d;
     out[3] = total(g_tally) * nv; out[7] = 0.0; out[8] = 0.0;
+}
+
+// Steger-Warming split flux F+ (sign > 0) or F- (sign < 0) of one state (direction frame).
+void oracle_steger_warming(const double* U, int nv, double gamma, int sign, double* F) {
+    Prim<double> w = primitives<double>(U, nv, gamma);
+    steger_warming<double>(w, nv, gamma, sign > 0 ? 1 : -1, F);
+}
+
+// Largest |lambda| of eigenvalue kind (0: u_n - c, 1: u_n, 2: u_n + c) over the grid.
+double oracle_field_speed(const Problem* P, const double* U, int dir, int kind) {
+    return max_field_speed<double>(*P, U, dir, kind);
+}
+
+// RHS with the LF speeds given: sp = (alpha_x, alpha_y, fx0, fx1, fx2, fy0, fy1, fy2).
+void oracle_rhs_speeds(const Problem* P, const double* U, const double* sp, double* Lout) {
+    Speeds<double> a{};
+    a.ax = sp[0]; a.ay = sp[1];
+    for (int k = 0; k < 3; ++k) { a.fx[k] = sp[2 + k]; a.fy[k] = sp[5 + k]; }
+    rhs_with_speeds<double>(*P, U, Lout, a);
 }
 
 // Jacobian-vector products of the discrete scheme (forward mode, Dual scalars).

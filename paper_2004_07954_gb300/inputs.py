@@ -19,7 +19,9 @@ Families (each a seeded generalisation of a paper set-up):
   * smooth entropy waves (density sine carried by a constant velocity at constant pressure)
     whose exact solution is the translated profile;
   * the adjoint workload: a seeded smooth multi-wave state on the periodic domain [-5, 5]
-    in which density, velocity and pressure all vary (no flat or resting region).
+    in which density, velocity and pressure all vary (no flat or resting region);
+  * the four-wave advection profile of Sec. 4.2 (Gaussians, square, triangle, half ellipse)
+    scaled by 1/A, and the two interacting blast waves of Sec. 4.3.2.
 """
 from __future__ import annotations
 
@@ -181,6 +183,41 @@ def adjoint_ic(n: int, seed: int) -> np.ndarray:
     u = q["u0"] + q["B"] * np.sin(k[2] * x + ph[2])
     p = 1.0 + q["C"] * np.sin(k[3] * x + ph[3])
     return cons_from_prim(rho, u, p).reshape(3, 1, n).copy()
+
+
+def four_wave_profile(x, A: float = 1.0):
+    """Sec. 4.2, case 1: on [-1, 1], (1/A) times a smooth combination of Gaussians on
+    [-0.8, -0.6], a square wave on [-0.4, -0.2], a triangle on [0, 0.2] and a half ellipse on
+    [0.4, 0.6], zero elsewhere; a = 0.5, z = -0.7, delta = 0.005, alpha = 10,
+    beta = log 2 / (36 delta^2).  The ellipse term is centred at a -+ delta (the printed
+    F(x, alpha, alpha -+ delta) reads a for alpha, as the centre a of the other term shows)."""
+    x = np.asarray(x, dtype=np.float64)
+    a, z, delta, alpha = 0.5, -0.7, 0.005, 10.0
+    beta = math.log(2.0) / (36.0 * delta * delta)
+    G = lambda zz: np.exp(-beta * (x - zz) ** 2)
+    F = lambda aa: np.sqrt(np.maximum(1.0 - alpha * alpha * (x - aa) ** 2, 0.0))
+    u = np.zeros_like(x)
+    m = (x >= -0.8) & (x <= -0.6)
+    u = np.where(m, (G(z - delta) + G(z + delta) + 4.0 * G(z)) / 6.0, u)
+    u = np.where((x >= -0.4) & (x <= -0.2), 1.0, u)
+    u = np.where((x >= 0.0) & (x <= 0.2), 1.0 - np.abs(10.0 * (x - 0.1)), u)
+    m = (x >= 0.4) & (x <= 0.6)
+    u = np.where(m, (F(a - delta) + F(a + delta) + 4.0 * F(a)) / 6.0, u)
+    return u / A
+
+
+def four_wave_ic(n: int, A: float = 1.0) -> np.ndarray:
+    """The four-wave profile on the periodic advection grid x_j = -1 + j dx, dx = 2/n."""
+    x, _ = advection_grid(n)
+    return four_wave_profile(x, A).reshape(1, 1, n).copy()
+
+
+def blast_wave_ic(n: int) -> np.ndarray:
+    """Sec. 4.3.2, two interacting blast waves on [0, 1] (cell centres): rho = 1, u = 0,
+    p = 1000 for x < 0.1, 0.01 for 0.1 <= x < 0.9, 100 for x >= 0.9."""
+    x = (np.arange(n) + 0.5) / n
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    return cons_from_prim(np.ones(n), 0.0, p).reshape(3, 1, n).copy()
 
 
 def random_smooth_state(system: int, nx: int, ny: int, seed: int) -> np.ndarray:
