@@ -42,7 +42,26 @@ typedef enum {
     WENOZN_ETIMEOUT = 5      /* device status bit: a bounded device-side wait gave up        */
 } wenozn_status;
 
-typedef enum { WENOZN_BC_PERIODIC = 0, WENOZN_BC_OUTFLOW = 1 } wenozn_bc;
+/* Boundary conditions: periodic (Sec. 4.2); outflow, the zero-order extrapolation of the
+ * transmissive condition (Sec. 4.4); reflective wall (the blast-wave and Rayleigh-Taylor
+ * set-ups of Sec. 4.3.2 / 4.4): ghost cell -1-g (g < 0) or 2n-1-g (g >= n) with the momentum
+ * normal to the wall negated (for advection the mirror image alone). */
+typedef enum { WENOZN_BC_PERIODIC = 0, WENOZN_BC_OUTFLOW = 1, WENOZN_BC_REFLECTIVE = 2 } wenozn_bc;
+
+/* Weight function of the fifth-order reconstruction: WENO-ZN (Eq. (new), the method),
+ * WENO-Z with q = 1 (Eq. (15)), the linear optimal weights c_k, or Jiang-Shu
+ * (alpha_k = c_k / (IS_k + eps)^2, Sec. 2.1; the paper's JS runs use eps = 1e-6). */
+typedef enum {
+    WENOZN_WEIGHTS_ZN = 0, WENOZN_WEIGHTS_Z = 1, WENOZN_WEIGHTS_LINEAR = 2, WENOZN_WEIGHTS_JS = 3
+} wenozn_weights;
+
+/* Flux splitting (Euler; advection always splits with |a|): global Lax-Friedrichs, one
+ * speed per direction (Sec. 4.3, the default); global LF with one speed per characteristic
+ * field, max |u - c|, max |u|, max |u + c|; local LF with the largest |u| + c of each
+ * interface's six stencil cells; Steger-Warming flux-vector splitting (Sec. 4.4). */
+typedef enum {
+    WENOZN_SPLIT_LF = 0, WENOZN_SPLIT_LF_FIELD = 1, WENOZN_SPLIT_LLF = 2, WENOZN_SPLIT_SW = 3
+} wenozn_split;
 
 typedef enum {
     WENOZN_ADVECTION_1D = 0, /* u_t + a u_x = 0 (Sec. 4.2), nvar = 1 */
@@ -52,11 +71,14 @@ typedef enum {
 
 /* Problem description.  The numerical constants default to the paper's choices:
  * gamma = 1.4 (Sec. 4.3), eps = 1e-40 in Eq. (new) (the value that reproduces the Sec. 4.1
- * table), A = 10 in Eq. (function), cfl = 0.5 (Sec. 4).  `flags` must be 0. */
+ * table), A = 10 in Eq. (function), cfl = 0.5 (Sec. 4), WENO-ZN weights, global LF
+ * splitting.  `flags` must be 0. */
 typedef struct {
     int32_t system;          /* wenozn_system                                  */
     int32_t nx, ny;          /* interior cells, 1 .. 2^30 each, nx*ny <= 2^34; ny = 1 in 1D */
     int32_t bc_x, bc_y;      /* wenozn_bc per direction (bc_y ignored in 1D)   */
+    int32_t weights;         /* wenozn_weights                                 */
+    int32_t split;           /* wenozn_split                                   */
     int32_t flags;           /* reserved, 0                                    */
     double dx, dy;           /* uniform spacing (> 0; dy ignored in 1D)        */
     double gamma;            /* ratio of specific heats (Euler)                */
@@ -101,10 +123,17 @@ wenozn_status wenozn_fill_ghosts(const wenozn_problem* p, double* U_padded, void
 wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat, int32_t side,
                                  double eps, double A, void* stream);
 
+/* The same reconstruction with the weight function `weights` (wenozn_weights); A is used by
+ * WENO-ZN only.  EINVAL for an unknown weight function. */
+wenozn_status wenozn_reconstruct_weights(const double* f_padded, int64_t n, double* fhat, int32_t side,
+                                         int32_t weights, double eps, double A, void* stream);
+
 /* Global Lax-Friedrichs speeds (Sec. 4.3 / 4.4): alpha_out[0] = max_ij(|u| + c),
- * alpha_out[1] = max_ij(|v| + c) (2D; 0 otherwise); |a| for advection.
+ * alpha_out[1] = max_ij(|v| + c) (2D; 0 otherwise); |a| for advection.  With the per-field
+ * splitting also alpha_out[2..4] = max |u - c|, max |u|, max |u + c| and alpha_out[5..7] the
+ * same with v (2D; 0 otherwise).
  *   U         : device state [nvar][ny][nx].
- *   alpha_out : device, 2 doubles, overwritten.
+ *   alpha_out : device, 2 doubles (8 with the per-field splitting), overwritten.
  *   status_dev: device int32 status word or NULL; a NaN/Inf, rho <= 0 or p <= 0 ORs
  *               WENOZN_ENONFINITE into it. */
 wenozn_status wenozn_max_wavespeed(const wenozn_problem* p, const double* U, double* alpha_out,
@@ -115,8 +144,9 @@ wenozn_status wenozn_max_wavespeed(const wenozn_problem* p, const double* U, dou
  * characteristic projection (Euler), WENO-ZN reconstruction of both split parts and
  * back-projection, F^ = R (g^+ + g^-), at every interface of that direction.
  *   U     : device state [nvar][ny][nx].
- *   alpha : device, 2 doubles: the LF speed of each direction (as wenozn_max_wavespeed
- *           writes them); ignored for advection, which splits with |a|.
+ *   alpha : device, 2 doubles (8 with the per-field splitting): the LF speeds as
+ *           wenozn_max_wavespeed writes them; ignored for advection, which splits with |a|
+ *           (and by the local-LF and Steger-Warming splittings, which need none).
  *   dir   : 0 = x, Fout[nvar][ny][nx+1] with Fout[k][j][i] at x_{i-1/2} of row j;
  *           1 = y (2D only), Fout[nvar][ny+1][nx] with Fout[k][j][i] at y_{j-1/2}.
  *   Fout  : device, overwritten; must not overlap U. */

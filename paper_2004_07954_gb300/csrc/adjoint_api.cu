@@ -27,6 +27,9 @@ wenozn_status check_vjp(const wenozn_problem* p, void* ws, size_t ws_bytes, Layo
     wenozn_status st = check_problem(p);
     if (st != WENOZN_OK) return st;
     if (p->system == WENOZN_EULER_2D) return WENOZN_EINVAL;     // the adjoint covers the 1D systems
+    // ... of the default scheme (WENO-ZN weights, global LF, periodic or outflow boundaries)
+    if (p->weights != WENOZN_WEIGHTS_ZN || p->split != WENOZN_SPLIT_LF || p->bc_x == WENOZN_BC_REFLECTIVE)
+        return WENOZN_EINVAL;
     if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
     *L = layout_of(*p);
     if (ws_bytes < L->total_vjp) return WENOZN_ENOMEM_WS;
@@ -69,6 +72,8 @@ wenozn_status wenozn_vjp_workspace_size(const wenozn_problem* p, size_t* bytes) 
     wenozn_status st = check_problem(p);
     if (st != WENOZN_OK) return st;
     if (!bytes || p->system == WENOZN_EULER_2D) return WENOZN_EINVAL;
+    if (p->weights != WENOZN_WEIGHTS_ZN || p->split != WENOZN_SPLIT_LF || p->bc_x == WENOZN_BC_REFLECTIVE)
+        return WENOZN_EINVAL;
     *bytes = layout_of(*p).total_vjp;
     return WENOZN_OK;
 }
@@ -119,7 +124,7 @@ wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, doub
     const double* stage_in[2] = {U, u1};
     double* stage_out[2] = {u1, u2};
     for (int stage = 0; stage < 2 && e == cudaSuccess; ++stage) {
-        e = launch_fluxes(*p, stage_in[stage], ctrl->alpha[stage], fx, nullptr, s);
+        e = launch_fluxes(*p, stage_in[stage], ctrl->alpha[stage], nullptr, fx, nullptr, s);
         if (e != cudaSuccess) break;
         UpdateArgs u = update_args(*p, ctrl, fx, nullptr);
         u.mode = stage + 1;

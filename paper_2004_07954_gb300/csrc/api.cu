@@ -19,14 +19,14 @@ cudaError_t rk3_stages(const wenozn_problem& p, const Layout& lay, void* ws, con
     double* fx = reinterpret_cast<double*>(ws_base(ws) + lay.fx);
     double* gy = reinterpret_cast<double*>(ws_base(ws) + lay.gy);
     const bool euler = p.system != WENOZN_ADVECTION_1D;
-    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
+    cudaError_t e = clear_speeds(ctrl, s);
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p.system, U, int64_t(p.nx) * p.ny, p.gamma, p.adv_speed, ctrl->alpha[0],
-                                 &ctrl->status, s);
+                                 &ctrl->status, s, field_slot(p, ctrl, 0));
     const double* stage_in[3] = {U, u1, u2};
     double* stage_out[3] = {u1, u2, U_out};
     for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
-        e = launch_fluxes(p, stage_in[stage], ctrl->alpha[stage], fx, gy, s);
+        e = launch_fluxes(p, stage_in[stage], ctrl->alpha[stage], &ctrl->alpha_f[stage][0][0], fx, gy, s);
         if (e != cudaSuccess) break;
         UpdateArgs u = update_args(p, ctrl, fx, gy);
         u.mode = stage + 1;
@@ -61,6 +61,8 @@ wenozn_status wenozn_problem_init(wenozn_problem* p, int32_t system, int32_t nx,
     p->A = 10.0;
     p->cfl = 0.5;
     p->adv_speed = 1.0;
+    p->weights = WENOZN_WEIGHTS_ZN;
+    p->split = WENOZN_SPLIT_LF;
     return WENOZN_OK;
 }
 
@@ -90,18 +92,28 @@ wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat
                                           static_cast<cudaStream_t>(stream)));
 }
 
+wenozn_status wenozn_reconstruct_weights(const double* f_padded, int64_t n, double* fhat, int32_t side,
+                                         int32_t weights, double eps, double A, void* stream) {
+    if (!f_padded || !fhat || n < 1 || n > (int64_t(1) << 31) - 8) return WENOZN_EINVAL;
+    if (side != 1 && side != -1) return WENOZN_EINVAL;
+    if (weights < 0 || weights > 3) return WENOZN_EINVAL;
+    if (!finite_pos(eps) || !std::isfinite(A) || A < 0.0) return WENOZN_EINVAL;
+    return cuda_status(launch_reconstruct(f_padded, n, fhat, side, eps, A, static_cast<cudaStream_t>(stream),
+                                          weights));
+}
+
 wenozn_status wenozn_max_wavespeed(const wenozn_problem* p, const double* U, double* alpha_out,
                                    int32_t* status_dev, void* stream) {
     wenozn_status st = check_problem(p);
     if (st != WENOZN_OK) return st;
     if (!U || !alpha_out) return WENOZN_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(alpha_out, 0, 2 * sizeof(double), s);
+    const bool per_field = p->split == WENOZN_SPLIT_LF_FIELD && p->system != WENOZN_ADVECTION_1D;
+    cudaError_t e = cudaMemsetAsync(alpha_out, 0, (per_field ? 8 : 2) * sizeof(double), s);
     if (e != cudaSuccess) return WENOZN_ECUDA;
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(alpha_out);
     return cuda_status(launch_max_wavespeed(p->system, U, int64_t(p->nx) * p->ny, p->gamma,
-                                            p->adv_speed,
-                                            reinterpret_cast<unsigned long long*>(alpha_out),
-                                            status_dev, s));
+                                            p->adv_speed, a, status_dev, s, per_field ? a + 2 : nullptr));
 }
 
 wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double* alpha,
@@ -113,11 +125,14 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     FluxArgs fa;
     fa.U = U;
     fa.alpha_bits = reinterpret_cast<const unsigned long long*>(alpha);
+    fa.alpha_f_bits = alpha ? fa.alpha_bits + 2 : nullptr;
+    fa.weights = p->weights;
+    fa.split = p->split;
     fa.nx = p->nx;
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
     fa.A4 = 0.25 * p->A;
-    fa.fast_rcp = zn_fast_rcp(p->eps, p->A);
+    fa.fast_rcp = zn_fast_rcp(p->eps, p->A, p->weights);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;
     fa.Fout = Fout;
@@ -137,11 +152,11 @@ wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, vo
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
     double* fx = reinterpret_cast<double*>(ws_base(ws) + lay.fx);
     double* gy = reinterpret_cast<double*>(ws_base(ws) + lay.gy);
-    cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
+    cudaError_t e = clear_speeds(ctrl, s);
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, int64_t(p->nx) * p->ny, p->gamma, p->adv_speed,
-                                 ctrl->alpha[0], &ctrl->status, s);
-    if (e == cudaSuccess) e = launch_fluxes(*p, U, ctrl->alpha[0], fx, gy, s);
+                                 ctrl->alpha[0], &ctrl->status, s, field_slot(*p, ctrl, 0));
+    if (e == cudaSuccess) e = launch_fluxes(*p, U, ctrl->alpha[0], &ctrl->alpha_f[0][0][0], fx, gy, s);
     if (e == cudaSuccess) {
         UpdateArgs u = update_args(*p, ctrl, fx, gy);
         u.mode = 0;

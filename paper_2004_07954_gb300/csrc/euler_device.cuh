@@ -13,12 +13,14 @@ namespace wz {
 template <int NV>
 struct CellPlanes {
     static constexpr int kPerCell = NV == 1 ? 2 : 2 * NV + (NV == 4 ? 4 : 3);
+    static constexpr int kPerCellGeneric = kPerCell + (NV == 1 ? 0 : 1);   // + |u_n| + c
     double* hp;
     double* hm;
     double* sr;
     double* un;
     double* H;
     double* ut;
+    double* sp;          // generic kernels: the cell's |u_n| + c (local LF)
     int NC;
     __device__ __forceinline__ CellPlanes(double* base, int nc) : NC(nc) {
         hp = base;
@@ -27,6 +29,7 @@ struct CellPlanes {
         un = sr + nc;
         H = un + nc;
         ut = H + nc;
+        sp = base + kPerCell * nc;
     }
 };
 
@@ -66,6 +69,77 @@ __device__ __forceinline__ void split_cell(const double* Uc, double alpha, doubl
         s.hm[k * s.NC + si] = fma(-half_a, Uc[k], hF[k]);
     }
     s.sr[si] = rho * rs;                               // sqrt(rho)
+    s.un[si] = un;
+    s.H[si] = Ep * rr;
+    if (NV == 4) s.ut[si] = ut;
+}
+
+// The cell phase of the generic kernels, by splitting (split: 0 global LF, 1 per-field LF,
+// 2 local LF, 3 Steger-Warming):
+//   0     h+- = (F +- alpha U)/2, as split_cell;
+//   1, 2  hp = F/2, hm = U/2 (split after the projection, per field or per interface), and
+//         the cell's |u_n| + c in the speed plane (oracle operation order);
+//   3     hp = F+, hm = F- of Steger and Warming:
+//         F+- = rho/(2 gamma) (2(g-1) l2 + l1 + l3, 2(g-1) l2 u + l1 (u-c) + l3 (u+c),
+//                              [(2(g-1) l2 + l1 + l3) v,] (g-1) l2 q^2 + l1 ((u-c)^2 + v^2)/2
+//                              + l3 ((u+c)^2 + v^2)/2 + (3-g)(l1 + l3) c^2 / (2(g-1)))
+//         with l = (u-c, u, u+c) and l+- = (l +- |l|)/2, q^2 = u^2 + v^2.
+// Advection ignores the splitting (every variant reduces to alpha = |a| there).
+template <int NV>
+__device__ __forceinline__ void split_cell_gen(const double* Uc, int split, double alpha, double a_adv,
+                                               double gamma, const CellPlanes<NV>& s, int si) {
+    const double gm1 = gamma - 1.0;
+    if (NV == 1 || split == 0) {
+        split_cell<NV>(Uc, alpha, a_adv, gm1, s, si);
+        return;
+    }
+    const double rho = Uc[0], mn = Uc[1], E = Uc[NV - 1];
+    const double mt = NV == 4 ? Uc[2] : 0.0;
+    const double rs = rsqrt(rho);
+    const double rr = rs * rs;
+    const double un = mn * rr;
+    const double ut = mt * rr;
+    const double kin = NV == 4 ? 0.5 * fma(mn, un, mt * ut) : 0.5 * (mn * un);
+    const double p = gm1 * (E - kin);
+    const double Ep = E + p;
+    if (split == 3) {
+        const double c = sqrt(gamma * p * rr);
+        const double l1 = un - c, l3 = un + c;
+        const double lp[3] = {0.5 * (l1 + fabs(l1)), 0.5 * (un + fabs(un)), 0.5 * (l3 + fabs(l3))};
+        const double lm[3] = {0.5 * (l1 - fabs(l1)), 0.5 * (un - fabs(un)), 0.5 * (l3 - fabs(l3))};
+        const double k0 = rho / (2.0 * gamma);
+        const double q2 = NV == 4 ? fma(un, un, ut * ut) : un * un;
+        const double vv = NV == 4 ? ut * ut : 0.0;
+        const double e1 = 0.5 * fma(l1, l1, vv), e3 = 0.5 * fma(l3, l3, vv);     // ((u -+ c)^2 + v^2)/2
+        const double w13 = (3.0 - gamma) * c * c / (2.0 * gm1);
+        const double g2 = 2.0 * gm1;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const double* l = side == 0 ? lp : lm;
+            double* h = side == 0 ? s.hp : s.hm;
+            const double m0 = fma(g2, l[1], l[0] + l[2]);
+            h[si] = k0 * m0;
+            h[s.NC + si] = k0 * fma(g2 * l[1], un, fma(l[0], l1, l[2] * l3));
+            if (NV == 4) h[2 * s.NC + si] = k0 * (m0 * ut);
+            h[(NV - 1) * s.NC + si] = k0 * fma(gm1 * l[1], q2, fma(l[0], e1, fma(l[2], e3, (l[0] + l[2]) * w13)));
+        }
+    } else {
+        const double hun = 0.5 * un;
+        double hF[NV];
+        hF[0] = 0.5 * mn;
+        hF[1] = fma(mn, hun, 0.5 * p);
+        if (NV == 4) hF[2] = mt * hun;
+        hF[NV - 1] = hun * Ep;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            s.hp[k * s.NC + si] = hF[k];
+            s.hm[k * s.NC + si] = 0.5 * Uc[k];
+        }
+        double vx, vy;
+        wave_speeds<NV>(Uc, gamma, vx, vy);
+        s.sp[si] = vx;
+    }
+    s.sr[si] = rho * rs;
     s.un[si] = un;
     s.H[si] = Ep * rr;
     if (NV == 4) s.ut[si] = ut;
@@ -133,6 +207,103 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
     // back-projection F^ = R g^ with the right eigenvectors (columns)
     //   r_{u-c} = (1, u-c, [v,] H-uc), r_u = (1, u, [v,] q^2/2), r_shear = (0, 0, 1, v),
     //   r_{u+c} = (1, u+c, [v,] H+uc)
+    const double uc = u * c;
+    if (NV == 3) {
+        const double d20 = gh[2] - gh[0];
+        Fh[0] = gh[0] + gh[1] + gh[2];
+        Fh[1] = fma(u, Fh[0], c * d20);
+        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, 0.5 * q2 * gh[1]));
+    } else {
+        const double d30 = gh[3] - gh[0];
+        Fh[0] = gh[0] + gh[1] + gh[3];
+        Fh[1] = fma(u, Fh[0], c * d30);
+        Fh[2] = fma(v, Fh[0], gh[2]);
+        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(0.5 * q2, gh[1], v * gh[2])));
+    }
+}
+
+// The interface flux of the generic kernels: weights and splitting chosen at run time.
+// Splits 0 and 3 project the cell split fluxes h+- (5 + 5 stencil points); splits 1 and 2
+// project F/2 and U/2 of the six cells and split each field k with its speed alpha_k:
+// g+- = l_k.(F/2) +- alpha_k l_k.(U/2), alpha_k = alpha_f[kind of field k] (split 1; kinds
+// 0 u-c, 1 u, 2 u+c) or the largest |u_n| + c of the six cells (split 2).
+template <int NV>
+__device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int base, int stride, double gm1,
+                                                   double eps4, double A4, bool fast_rcp, int weights, int split,
+                                                   const double* alpha_f, double* Fh) {
+    const int NC = s.NC;
+    if (NV == 1) {
+        const double p0 = s.hp[base], p1 = s.hp[base + stride], p2 = s.hp[base + 2 * stride];
+        const double p3 = s.hp[base + 3 * stride], p4 = s.hp[base + 4 * stride];
+        const double m0 = s.hm[base + stride], m1 = s.hm[base + 2 * stride], m2 = s.hm[base + 3 * stride];
+        const double m3 = s.hm[base + 4 * stride], m4 = s.hm[base + 5 * stride];
+        Fh[0] = zn_flux_w(p0, p1, p2, p3, p4, eps4, A4, fast_rcp, weights) +
+                zn_flux_w(m4, m3, m2, m1, m0, eps4, A4, fast_rcp, weights);
+        return;
+    }
+    const int cl = base + 2 * stride, cr = base + 3 * stride;
+    const double srl = s.sr[cl], srr = s.sr[cr];
+    const double rsum = rcp_nr(srl + srr);
+    const double wl = srl * rsum, wr = srr * rsum;
+    const double u = fma(wl, s.un[cl], wr * s.un[cr]);
+    const double v = NV == 4 ? fma(wl, s.ut[cl], wr * s.ut[cr]) : 0.0;
+    const double H = fma(wl, s.H[cl], wr * s.H[cr]);
+    const double q2 = NV == 4 ? fma(u, u, v * v) : u * u;
+    const double c2 = gm1 * fma(-0.5, q2, H);
+    const double rc = rsqrt(c2);
+    const double c = c2 * rc;
+    const double b1 = gm1 * (rc * rc);
+    const double b2 = 0.5 * q2 * b1;
+    const double hrc = 0.5 * rc;
+    // left eigenvectors through their shared parts, as in interface_flux
+    auto project = [&](const double* hs, int i, double* g) {
+        const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
+        const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+        const double Z = fma(b2, h0, -(b1 * W));
+        const double B = hrc * fma(u, h0, -h1);
+        g[0] = fma(0.5, Z, B);
+        g[1] = h0 - Z;
+        if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+        g[NV - 1] = fma(0.5, Z, -B);
+    };
+    double gp[5][NV], gm[5][NV];
+    if (split == 0 || split == 3) {
+#pragma unroll
+        for (int st = 0; st < 5; ++st) {
+            project(s.hp, base + st * stride, gp[st]);
+            project(s.hm, base + (st + 1) * stride, gm[st]);
+        }
+    } else {
+        double ak[NV];
+        if (split == 2) {
+            double a = s.sp[base];
+#pragma unroll
+            for (int st = 1; st < 6; ++st) a = fmax(a, s.sp[base + st * stride]);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) ak[k] = a;
+        } else {
+            ak[0] = alpha_f[0];
+            ak[1] = alpha_f[1];
+            if (NV == 4) ak[2] = alpha_f[1];
+            ak[NV - 1] = alpha_f[2];
+        }
+#pragma unroll
+        for (int st = 0; st < 6; ++st) {
+            double gF[NV], gU[NV];
+            project(s.hp, base + st * stride, gF);
+            project(s.hm, base + st * stride, gU);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                if (st <= 4) gp[st][k] = fma(ak[k], gU[k], gF[k]);
+                if (st >= 1) gm[st - 1][k] = fma(-ak[k], gU[k], gF[k]);
+            }
+        }
+    }
+    double gh[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, A4, fast_rcp, weights) +
+                zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, A4, fast_rcp, weights);
     const double uc = u * c;
     if (NV == 3) {
         const double d20 = gh[2] - gh[0];

@@ -1,5 +1,8 @@
 // Interface-flux kernels: global Lax-Friedrichs splitting, Roe-averaged characteristic
 // projection and WENO-ZN reconstruction of both split parts, one thread per interface.
+// The generic instantiations (GEN) take the weight function and the flux splitting at run
+// time (WENO-Z / linear / Jiang-Shu weights; per-field LF, local LF, Steger-Warming); the
+// default scheme keeps its own instantiations.
 //
 // A block owns a tile of TI interfaces along the sweep direction times TA grid lines.  It
 // first computes, once per cell of the tile plus its 3+2 halo cells, the split fluxes
@@ -26,7 +29,7 @@ template <> struct Tile<3, 0, true> { static constexpr int TI = 64, TA = 1, THRE
 template <> struct Tile<4, 0, false> { static constexpr int TI = 128, TA = 4, THREADS = 256; };
 template <> struct Tile<4, 1, false> { static constexpr int TI = 32, TA = 16, THREADS = 256; };
 
-template <int NV, int DIR, bool SMALL>
+template <int NV, int DIR, bool SMALL, bool GEN>
 __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(FluxArgs a) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int kThreads = Tile<NV, DIR, SMALL>::THREADS;
@@ -48,13 +51,17 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
 
     const double alpha = NV == 1 ? fabs(a.adv_speed) : __longlong_as_double((long long)a.alpha_bits[DIR]);
     const double gm1 = a.gamma - 1.0;
+    double alpha_f[3] = {0.0, 0.0, 0.0};           // per-field speeds of this direction
+    if (GEN && NV > 1 && a.split == 1)
+        for (int k = 0; k < 3; ++k) alpha_f[k] = __longlong_as_double((long long)a.alpha_f_bits[DIR * 3 + k]);
 
     // ---- per-cell quantities -------------------------------------------------------
     for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
         const int l = DIR == 0 ? idx / CL : idx % TA;
         const int lc = DIR == 0 ? idx % CL : idx / TA;
         const int line = min(l0 + l, nlines - 1);
-        const int g = ghost_src(j0 - 3 + lc, n, a.bc);
+        const int gi = j0 - 3 + lc;
+        const int g = ghost_src(gi, n, a.bc);
         const int64_t cell = DIR == 0 ? int64_t(line) * a.nx + g : int64_t(g) * a.nx + line;
         // direction frame: (rho, m_n, m_t, E)
         double Uc[NV];
@@ -63,8 +70,10 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
             Uc[1] = a.U[(DIR == 0 ? 1 : 2) * nc + cell];
             if (NV == 4) Uc[2] = a.U[(DIR == 0 ? 2 : 1) * nc + cell];
             Uc[NV - 1] = a.U[(NV - 1) * nc + cell];
+            if (a.bc == 2 && ghost_mirrored(gi, n, a.bc)) Uc[1] = -Uc[1];   // wall mirror image
         }
-        split_cell<NV>(Uc, alpha, a.adv_speed, gm1, sp, sidx(l, lc));
+        if (GEN) split_cell_gen<NV>(Uc, a.split, alpha, a.adv_speed, a.gamma, sp, sidx(l, lc));
+        else split_cell<NV>(Uc, alpha, a.adv_speed, gm1, sp, sidx(l, lc));
     }
     __syncthreads();
 
@@ -76,7 +85,11 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         const int j = j0 + jl, line = l0 + l;
         if (j >= nint || line >= nlines) continue;
         double Fh[NV];
-        interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.A4, a.fast_rcp != 0, Fh);
+        if (GEN)
+            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.A4, a.fast_rcp != 0, a.weights,
+                                   a.split, alpha_f, Fh);
+        else
+            interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.A4, a.fast_rcp != 0, Fh);
         // store, undoing the direction frame
         if (DIR == 0) {
             const int64_t base = int64_t(line) * (a.nx + 1) + j;
@@ -94,11 +107,12 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     }
 }
 
-template <int NV, int DIR, bool SMALL>
+template <int NV, int DIR, bool SMALL, bool GEN>
 cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int NC = (TI + 5) * TA;
-    constexpr size_t smem = size_t(NC) * CellPlanes<NV>::kPerCell * sizeof(double);
+    constexpr size_t smem =
+        size_t(NC) * (GEN ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCell) * sizeof(double);
     // the dynamic shared-memory limit is a per-device function attribute
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;
@@ -106,7 +120,7 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(flux_kernel<NV, DIR, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(flux_kernel<NV, DIR, SMALL, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem));
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
@@ -116,7 +130,7 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     const unsigned along = unsigned((n + 1 + TI - 1) / TI);
     const unsigned across = unsigned((nlines + TA - 1) / TA);
     dim3 grid = DIR == 0 ? dim3(along, across) : dim3(across, along);
-    flux_kernel<NV, DIR, SMALL><<<grid, Tile<NV, DIR, SMALL>::THREADS, smem, s>>>(a);
+    flux_kernel<NV, DIR, SMALL, GEN><<<grid, Tile<NV, DIR, SMALL>::THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -130,17 +144,23 @@ int sm_count_cached() {
     return sms > 0 ? sms : 152;
 }
 
-}  // namespace
-
-cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s) {
+template <bool GEN>
+cudaError_t launch_flux_t(int system, int dir, const FluxArgs& a, cudaStream_t s) {
     if (system != 2) {
         // 1D: short lines take the small tiles so that every SM has work
         const int64_t big_tiles = (int64_t(a.nx) + 512) / 512 * a.ny;
         const bool small = big_tiles < 2 * sm_count_cached();
-        if (system == 0) return small ? launch_one<1, 0, true>(a, s) : launch_one<1, 0, false>(a, s);
-        return small ? launch_one<3, 0, true>(a, s) : launch_one<3, 0, false>(a, s);
+        if (system == 0) return small ? launch_one<1, 0, true, GEN>(a, s) : launch_one<1, 0, false, GEN>(a, s);
+        return small ? launch_one<3, 0, true, GEN>(a, s) : launch_one<3, 0, false, GEN>(a, s);
     }
-    return dir == 0 ? launch_one<4, 0, false>(a, s) : launch_one<4, 1, false>(a, s);
+    return dir == 0 ? launch_one<4, 0, false, GEN>(a, s) : launch_one<4, 1, false, GEN>(a, s);
+}
+
+}  // namespace
+
+cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s) {
+    const bool generic = a.weights != 0 || (system != 0 && a.split != 0);
+    return generic ? launch_flux_t<true>(system, dir, a, s) : launch_flux_t<false>(system, dir, a, s);
 }
 
 }  // namespace wz

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 
@@ -49,12 +50,13 @@ inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 inline wenozn_status check_problem(const wenozn_problem* p) {
     if (!p) return WENOZN_EINVAL;
     if (p->system < 0 || p->system > 2 || p->flags != 0) return WENOZN_EINVAL;
+    if (p->weights < 0 || p->weights > 3 || p->split < 0 || p->split > 3) return WENOZN_EINVAL;
     const bool two_d = p->system == WENOZN_EULER_2D;
     if (p->nx < 1 || p->nx > (1 << 30)) return WENOZN_EINVAL;
     if (two_d ? (p->ny < 1 || p->ny > (1 << 30)) : p->ny != 1) return WENOZN_EINVAL;
     if (int64_t(p->nx) * p->ny > (int64_t(1) << 34)) return WENOZN_EINVAL;
-    if ((p->bc_x != WENOZN_BC_PERIODIC && p->bc_x != WENOZN_BC_OUTFLOW)) return WENOZN_EINVAL;
-    if (two_d && p->bc_y != WENOZN_BC_PERIODIC && p->bc_y != WENOZN_BC_OUTFLOW) return WENOZN_EINVAL;
+    if (p->bc_x < WENOZN_BC_PERIODIC || p->bc_x > WENOZN_BC_REFLECTIVE) return WENOZN_EINVAL;
+    if (two_d && (p->bc_y < WENOZN_BC_PERIODIC || p->bc_y > WENOZN_BC_REFLECTIVE)) return WENOZN_EINVAL;
     if (!finite_pos(p->dx) || (two_d && !finite_pos(p->dy))) return WENOZN_EINVAL;
     if (!finite_pos(p->eps) || !std::isfinite(p->A) || p->A < 0.0 || !finite_pos(p->cfl)) return WENOZN_EINVAL;
     if (p->system == WENOZN_ADVECTION_1D) {
@@ -67,15 +69,19 @@ inline wenozn_status check_problem(const wenozn_problem* p) {
 
 inline wenozn_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WENOZN_OK : WENOZN_ECUDA; }
 
-inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsigned long long* alpha_bits) {
+inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsigned long long* alpha_bits,
+                          const unsigned long long* alpha_f_bits) {
     FluxArgs fa;
     fa.U = U;
     fa.alpha_bits = alpha_bits;
+    fa.alpha_f_bits = alpha_f_bits;
+    fa.weights = p.weights;
+    fa.split = p.split;
     fa.nx = p.nx;
     fa.ny = p.ny;
     fa.eps4 = 4.0 * p.eps;
     fa.A4 = 0.25 * p.A;
-    fa.fast_rcp = zn_fast_rcp(p.eps, p.A);
+    fa.fast_rcp = zn_fast_rcp(p.eps, p.A, p.weights);
     fa.gamma = p.gamma;
     fa.adv_speed = p.adv_speed;
     fa.Fout = nullptr;
@@ -83,10 +89,12 @@ inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsign
     return fa;
 }
 
-// Launches the x (and y) flux kernels for stage input U with LF speeds in `alpha_bits`.
+// Launches the x (and y) flux kernels for stage input U with LF speeds in `alpha_bits`
+// (and the per-field speeds in `alpha_f_bits`, [dir][3], for the per-field splitting).
 inline cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const unsigned long long* alpha_bits,
-                                 double* fx, double* gy, cudaStream_t s) {
-    FluxArgs fa = flux_args(p, U, alpha_bits);
+                                 const unsigned long long* alpha_f_bits, double* fx, double* gy,
+                                 cudaStream_t s) {
+    FluxArgs fa = flux_args(p, U, alpha_bits, alpha_f_bits);
     fa.Fout = fx;
     cudaError_t e = launch_flux(p.system, 0, fa, s);
     if (e != cudaSuccess || p.system != WENOZN_EULER_2D) return e;
@@ -106,6 +114,7 @@ inline UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double*
     u.rdy = p.system == WENOZN_EULER_2D ? 1.0 / p.dy : 0.0;
     u.ctrl = ctrl;
     u.next_slot = -1;
+    u.field_speeds = p.split == WENOZN_SPLIT_LF_FIELD && p.system != WENOZN_ADVECTION_1D ? 1 : 0;
     u.cfl = p.cfl;
     u.dx = p.dx;
     u.dy = p.dy;
@@ -115,5 +124,17 @@ inline UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double*
 }
 
 inline char* ws_base(void* ws) { return static_cast<char*>(ws); }
+
+// Clears every LF-speed slot (global and per-field) of the control block.
+inline cudaError_t clear_speeds(Ctrl* ctrl, cudaStream_t s) {
+    static_assert(offsetof(Ctrl, alpha_f) == sizeof(Ctrl::alpha), "speed slots must be adjacent");
+    return cudaMemsetAsync(ctrl->alpha, 0, sizeof(Ctrl::alpha) + sizeof(Ctrl::alpha_f), s);
+}
+
+// The per-field speed slot to fill for this problem (null unless it splits per field).
+inline unsigned long long* field_slot(const wenozn_problem& p, Ctrl* ctrl, int slot) {
+    return p.split == WENOZN_SPLIT_LF_FIELD && p.system != WENOZN_ADVECTION_1D ? &ctrl->alpha_f[slot][0][0]
+                                                                                : nullptr;
+}
 
 }  // namespace wz

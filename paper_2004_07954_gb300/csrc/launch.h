@@ -15,12 +15,20 @@ struct FluxArgs {
     const double* U;                       // stage input, [nv][ny][nx]
     double* Fout;
     const unsigned long long* alpha_bits;  // LF speeds (x, y) of U as bit patterns; unused for advection
-    int nx, ny, bc;                        // bc of the sweep direction
+    const unsigned long long* alpha_f_bits;  // per-field speeds [dir][3] (split 1 only)
+    int nx, ny, bc;                        // bc of the sweep direction (0 periodic, 1 outflow, 2 reflective)
     int fast_rcp;                          // 1: Newton reciprocal for f^ = num/den (see zn_flux)
+    int weights, split;                    // weight function and flux splitting (wenozn.h enums)
     double eps4, A4, gamma, adv_speed;     // eps4 = 4 eps, A4 = A / 4
 };
-// Whether the WENO-ZN denominator is guaranteed positive and normal (Newton reciprocal).
-inline int zn_fast_rcp(double eps, double A) { return A > 0.0 && eps >= 1e-60 ? 1 : 0; }
+// Whether the reconstruction's common denominator is guaranteed positive and normal, so the
+// Newton reciprocal applies: WENO-ZN needs A > 0 and eps >= 1e-60, WENO-Z and Jiang-Shu
+// eps >= 1e-60, the linear weights always.
+inline int zn_fast_rcp(double eps, double A, int weights = 0) {
+    if (weights == 2) return 1;
+    if (weights != 0) return eps >= 1e-60 ? 1 : 0;
+    return A > 0.0 && eps >= 1e-60 ? 1 : 0;
+}
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s);
 
 // Flux difference, SSP-RK3 stage combination and the next stage's LF speeds.
@@ -35,17 +43,19 @@ struct UpdateArgs {
     int mode;            // 0: out = L; 1, 2, 3: RK3 stages
     Ctrl* ctrl;
     int next_slot;       // alpha slot to accumulate the output's LF speeds into, or -1
+    int field_speeds;    // also accumulate the per-field speeds (per-field LF splitting)
     double dt_fixed, t_remaining, cfl, dx, dy, gamma, adv_speed;
 };
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s);
 
-// Global LF speeds of U folded into dst[0..1] (bit-pattern max; dst must start at 0).
+// Global LF speeds of U folded into dst[0..1] (bit-pattern max; dst must start at 0) and,
+// when dst_f is not null, the per-field speeds into dst_f[dir][3] (|u-c|, |u|, |u+c|).
 cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, double gamma,
                                  double adv_speed, unsigned long long* dst, int32_t* status,
-                                 cudaStream_t s);
+                                 cudaStream_t s, unsigned long long* dst_f = nullptr);
 
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
-                               double eps, double A, cudaStream_t s);
+                               double eps, double A, cudaStream_t s, int weights = 0);
 
 // Batched 1D Euler (see batch_kernels.cu).
 struct BatchArgs {

@@ -83,18 +83,22 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
     double* gy = reinterpret_cast<double*>(b + off_gy);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
+    const bool per_field = p->split == WENOZN_SPLIT_LF_FIELD && p->system != WENOZN_ADVECTION_1D;
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s);
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, int64_t(nx * ny), p->gamma, p->adv_speed, ctrl->alpha[0],
-                                 &ctrl->status, s);
+                                 &ctrl->status, s, per_field ? &ctrl->alpha_f[0][0][0] : nullptr);
     FluxArgs fa;
     fa.U = U;
     fa.alpha_bits = ctrl->alpha[0];
+    fa.alpha_f_bits = &ctrl->alpha_f[0][0][0];
+    fa.weights = p->weights;
+    fa.split = p->split;
     fa.nx = p->nx;
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
     fa.A4 = 0.25 * p->A;
-    fa.fast_rcp = zn_fast_rcp(p->eps, p->A);
+    fa.fast_rcp = zn_fast_rcp(p->eps, p->A, p->weights);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;
     if (e == cudaSuccess) {
@@ -120,6 +124,7 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
         u.out = L;
         u.ctrl = ctrl;
         u.next_slot = -1;
+        u.field_speeds = 0;
         u.gamma = p->gamma;
         u.adv_speed = p->adv_speed;
         e = launch_update(p->system, u, s);

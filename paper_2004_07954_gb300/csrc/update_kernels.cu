@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
     const int64_t sx = int64_t(a.ny) * (a.nx + 1);       // x-flux plane stride
     const int64_t sy = int64_t(a.ny + 1) * a.nx;         // y-flux plane stride
     double mx = 0.0, my = 0.0;
+    double fmx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // per-field speeds, x then y
     bool bad = false;
     for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
         const int64_t j = cell / a.nx, i = cell - j * a.nx;
@@ -76,33 +77,61 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
             if (NV == 1) {
                 bad |= !isfinite(o[0]);
             } else if (a.next_slot >= 0 || a.mode == 3) {
-                double vx, vy;
-                bad |= !wave_speeds<NV>(o, a.gamma, vx, vy);
+                double u, v, c;
+                const bool adm = wave_state<NV>(o, a.gamma, u, v, c);
+                const double vx = __dadd_rn(fabs(u), c), vy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
+                bad |= !(adm && isfinite(vx) && isfinite(vy));
                 mx = fmax(mx, vx);
                 my = fmax(my, vy);
+                if (a.field_speeds) {
+                    double f[3];
+                    field_speeds(u, c, f);
+                    for (int k = 0; k < 3; ++k) fmx[k] = fmax(fmx[k], f[k]);
+                    if (NV == 4) {
+                        field_speeds(v, c, f);
+                        for (int k = 0; k < 3; ++k) fmx[3 + k] = fmax(fmx[3 + k], f[k]);
+                    }
+                }
             }
         }
     }
     if (bad) atomicOr(&a.ctrl->status, kStatusNonFinite);
-    if (NV != 1 && a.next_slot >= 0) block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
+    if (NV != 1 && a.next_slot >= 0) {
+        block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
+        if (a.field_speeds) block_max_n_atomic<6>(fmx, &a.ctrl->alpha_f[a.next_slot][0][0]);
+    }
 }
 
 template <int NV, int T>
 __global__ void __launch_bounds__(T) max_wavespeed_kernel(const double* U, int64_t nc, double gamma,
-                                                          unsigned long long* dst, int32_t* status) {
+                                                          unsigned long long* dst, int32_t* status,
+                                                          unsigned long long* dst_f) {
     double mx = 0.0, my = 0.0;
+    double fmx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
         double s[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) s[k] = U[k * nc + cell];
-        double vx, vy;
-        bad |= !wave_speeds<NV>(s, gamma, vx, vy);
+        double u, v, c;
+        const bool adm = wave_state<NV>(s, gamma, u, v, c);
+        const double vx = __dadd_rn(fabs(u), c), vy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
+        bad |= !(adm && isfinite(vx) && isfinite(vy));
         mx = fmax(mx, vx);
         my = fmax(my, vy);
+        if (dst_f) {
+            double f[3];
+            field_speeds(u, c, f);
+            for (int k = 0; k < 3; ++k) fmx[k] = fmax(fmx[k], f[k]);
+            if (NV == 4) {
+                field_speeds(v, c, f);
+                for (int k = 0; k < 3; ++k) fmx[3 + k] = fmax(fmx[3 + k], f[k]);
+            }
+        }
     }
     if (bad && status) atomicOr(status, kStatusNonFinite);
     block_max2_atomic(mx, my, dst);
+    if (dst_f) block_max_n_atomic<6>(fmx, dst_f);
 }
 
 __global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, unsigned long long* dst) {
@@ -114,12 +143,12 @@ __global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, u
 
 __global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, int64_t n, double* fhat,
                                                                 int side, double eps4, double A4,
-                                                                int fast_rcp) {
+                                                                int fast_rcp, int weights) {
     const int64_t j = blockIdx.x * int64_t(kThreads) + threadIdx.x;
     if (j > n) return;
     const double* s = f + j;
-    fhat[j] = side > 0 ? zn_flux(s[0], s[1], s[2], s[3], s[4], eps4, A4, fast_rcp != 0)
-                       : zn_flux(s[5], s[4], s[3], s[2], s[1], eps4, A4, fast_rcp != 0);
+    fhat[j] = side > 0 ? zn_flux_w(s[0], s[1], s[2], s[3], s[4], eps4, A4, fast_rcp != 0, weights)
+                       : zn_flux_w(s[5], s[4], s[3], s[2], s[1], eps4, A4, fast_rcp != 0, weights);
 }
 
 __global__ void __launch_bounds__(kThreads) rcp_check_kernel(const double* d, int64_t n, double* fast,
@@ -144,7 +173,9 @@ __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int 
         const int64_t row = two_d ? r + 3 : 0;
         double* line = U + (k * py + row) * px;
         const int gi = g < 3 ? g - 3 : nx + (g - 3);          // -3..-1, n..n+2
-        line[gi + 3] = line[ghost_src(gi, nx, bc_x) + 3];
+        const double val = line[ghost_src(gi, nx, bc_x) + 3];
+        // a wall's mirror image carries the opposite x momentum
+        line[gi + 3] = (nv > 1 && k == 1 && ghost_mirrored(gi, nx, bc_x)) ? -val : val;
     } else {
         const int64_t total = int64_t(nv) * px * 6;
         if (t >= total) return;
@@ -152,7 +183,8 @@ __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int 
         const int64_t col = (t / 6) % px, k = t / (6 * int64_t(px));
         double* plane = U + k * py * px;
         const int gj = g < 3 ? g - 3 : ny + (g - 3);
-        plane[int64_t(gj + 3) * px + col] = plane[int64_t(ghost_src(gj, ny, bc_y) + 3) * px + col];
+        const double val = plane[int64_t(ghost_src(gj, ny, bc_y) + 3) * px + col];
+        plane[int64_t(gj + 3) * px + col] = (k == 2 && ghost_mirrored(gj, ny, bc_y)) ? -val : val;
     }
 }
 
@@ -185,12 +217,13 @@ void update_nv(const UpdateArgs& a, int64_t nc, cudaStream_t s) {
 
 template <int NV>
 void max_wavespeed_nv(const double* U, int64_t nc, double gamma, unsigned long long* dst, int32_t* status,
-                      cudaStream_t s) {
+                      unsigned long long* dst_f, cudaStream_t s) {
     const int sms = sm_count();
     if (few_cells(nc, sms))
-        max_wavespeed_kernel<NV, 64><<<grid_for(nc, sms * 16, 64), 64, 0, s>>>(U, nc, gamma, dst, status);
+        max_wavespeed_kernel<NV, 64><<<grid_for(nc, sms * 16, 64), 64, 0, s>>>(U, nc, gamma, dst, status, dst_f);
     else
-        max_wavespeed_kernel<NV, kThreads><<<grid_for(nc, sms * 4), kThreads, 0, s>>>(U, nc, gamma, dst, status);
+        max_wavespeed_kernel<NV, kThreads><<<grid_for(nc, sms * 4), kThreads, 0, s>>>(U, nc, gamma, dst, status,
+                                                                                        dst_f);
 }
 
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
@@ -203,21 +236,21 @@ cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
 
 cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, double gamma,
                                  double adv_speed, unsigned long long* dst, int32_t* status,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, unsigned long long* dst_f) {
     if (system == 0) {
         abs_speed_kernel<<<1, 32, 0, s>>>(adv_speed, dst);
         return cudaGetLastError();
     }
-    if (system == 1) max_wavespeed_nv<3>(U, ncells, gamma, dst, status, s);
-    else max_wavespeed_nv<4>(U, ncells, gamma, dst, status, s);
+    if (system == 1) max_wavespeed_nv<3>(U, ncells, gamma, dst, status, dst_f, s);
+    else max_wavespeed_nv<4>(U, ncells, gamma, dst, status, dst_f, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
-                               double eps, double A, cudaStream_t s) {
+                               double eps, double A, cudaStream_t s, int weights) {
     const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
     reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, 0.25 * A,
-                                                 zn_fast_rcp(eps, A));
+                                                 zn_fast_rcp(eps, A, weights), weights);
     return cudaGetLastError();
 }
 

@@ -123,14 +123,67 @@ __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2,
 }
 
 // ------------------------------------------------------------------------------------
+// The same reconstruction with the weight function chosen at run time (weights: 0 WENO-ZN,
+// Eq. (new); 1 WENO-Z with q = 1, Eq. (15); 2 linear (the optimal weights c_k); 3 Jiang-Shu,
+// c_k / (IS_k + eps)^2, Sec. 2.1).  All four share the scaled indicators b_k = 4 (IS_k + eps)
+// and the common-denominator form f^ = sum a_k q'_k / (a_0 + 6 a_1 + 3 a_2):
+//   WENO-Z:  alpha_k / c_k = 1 + tau5/(IS_k + eps) = (b_k + T)/b_k with T = |b_0 - b_2| = 4 tau5;
+//            times b_0 b_1 b_2: a_k = b_0 b_1 b_2 + T prod_{j != k} b_j;
+//   JS:      alpha_k / c_k = 16 / b_k^2; times (b_0 b_1 b_2)^2 / 16: a_k = (prod_{j != k} b_j)^2;
+//   linear:  a_k = 1.
+// ------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, double c, double d, double e,
+                                                       double eps4, double A4, int weights) {
+    if (weights == 0) return zn_parts(a, b, c, d, e, eps4, A4);
+    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+    const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
+    const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
+    const double k13_3 = 13.0 / 3.0;
+    const double k1_12 = 1.0 / 12.0;
+    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
+    const double q0 = fma(k1_12, s0, fma(0.25, t0, c));
+    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
+    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
+    double a0 = 1.0, a1 = 1.0, a2 = 1.0;
+    if (weights != 2) {
+        const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));
+        const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
+        const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
+        const double b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1;
+        if (weights == 1) {
+            const double T = fabs(b0 - b2);
+            const double b012 = b01 * b2;
+            a0 = fma(T, b12, b012);
+            a1 = fma(T, b02, b012);
+            a2 = fma(T, b01, b012);
+        } else {
+            a0 = b12 * b12;
+            a1 = b02 * b02;
+            a2 = b01 * b01;
+        }
+    }
+    ZnParts r;
+    r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
+    r.den = fma(6.0, a1, fma(3.0, a2, a0));
+    return r;
+}
+
+__host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
+                                                     double eps4, double A4, bool fast_rcp, int weights) {
+    const ZnParts r = zn_parts_w(a, b, c, d, e, eps4, A4, weights);
+    return fast_rcp ? r.num * rcp_nr(r.den) : r.num / r.den;
+}
+
+// ------------------------------------------------------------------------------------
 // Workspace control block (first 256 bytes of the caller's workspace).
 // ------------------------------------------------------------------------------------
 struct Ctrl {
-    unsigned long long alpha[3][2];   // LF speeds per RK stage slot, as IEEE bit patterns
-    double dt;                        // the step the current RK3 step uses
-    int32_t status;                   // OR of (1 << wenozn_status) device-detected bits
+    unsigned long long alpha[3][2];       // LF speeds per RK stage slot, as IEEE bit patterns
+    unsigned long long alpha_f[3][2][3];  // per-field speeds (slot, direction, |u-c|, |u|, |u+c|)
+    double dt;                            // the step the current RK3 step uses
+    int32_t status;                       // OR of (1 << wenozn_status) device-detected bits
     int32_t pad0;
-    double reserved[24];
+    double reserved[6];
 };
 static_assert(sizeof(Ctrl) <= 256, "control block must fit 256 bytes");
 
@@ -140,20 +193,33 @@ constexpr int32_t kStatusNonFinite = 1 << 4;   // (1 << WENOZN_ENONFINITE)
 // contraction (so the global maximum, a pure comparison, is bit-identical to it).
 // Returns false when the state is not admissible (non-finite, rho <= 0 or p <= 0).
 template <int NV>
-__device__ __forceinline__ bool wave_speeds(const double* s, double gamma, double& sx, double& sy) {
+__device__ __forceinline__ bool wave_state(const double* s, double gamma, double& u, double& v, double& c) {
     const double rho = s[0];
-    const double u = __ddiv_rn(s[1], rho);
-    const double v = NV == 4 ? __ddiv_rn(s[2], rho) : 0.0;
+    u = __ddiv_rn(s[1], rho);
+    v = NV == 4 ? __ddiv_rn(s[2], rho) : 0.0;
     const double E = s[NV - 1];
     double kin;
     if (NV == 4) kin = __dmul_rn(__dmul_rn(0.5, rho), __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
     else kin = __dmul_rn(__dmul_rn(__dmul_rn(0.5, rho), u), u);
     const double p = __dmul_rn(__dadd_rn(gamma, -1.0), __dadd_rn(E, -kin));
-    const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+    c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+    return rho > 0.0 && p > 0.0 && isfinite(E);
+}
+
+template <int NV>
+__device__ __forceinline__ bool wave_speeds(const double* s, double gamma, double& sx, double& sy) {
+    double u, v, c;
+    const bool adm = wave_state<NV>(s, gamma, u, v, c);
     sx = __dadd_rn(fabs(u), c);
     sy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
-    const bool ok = rho > 0.0 && p > 0.0 && isfinite(sx) && isfinite(sy) && isfinite(E);
-    return ok;
+    return adm && isfinite(sx) && isfinite(sy);
+}
+
+// Per-field speeds |u-c|, |u|, |u+c| of one direction (the oracle's operation order).
+__device__ __forceinline__ void field_speeds(double u, double c, double* f) {
+    f[0] = fabs(__dadd_rn(u, -c));
+    f[1] = fabs(u);
+    f[2] = fabs(__dadd_rn(u, c));
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -185,13 +251,51 @@ __device__ __forceinline__ void block_max2_atomic(double vx, double vy, unsigned
     }
 }
 
-// Ghost-cell index map: periodic wrap or zero-order extrapolation (outflow).
+// Block-wide maxima of N non-negative values folded into dst[0..N-1] (bit-pattern
+// atomicMax).  Must be called by every thread of the block.
+template <int N>
+__device__ __forceinline__ void block_max_n_atomic(const double* v, unsigned long long* dst) {
+    __shared__ double red[N][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const double m = warp_max(v[k]);
+        if (lane == 0) red[k][w] = m;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const double m = warp_max(lane < nw ? red[k][lane] : 0.0);
+            if (lane == 0) atomicMax(&dst[k], (unsigned long long)__double_as_longlong(m));
+        }
+    }
+    __syncthreads();
+}
+
+// Ghost-cell index map: periodic wrap (bc 0), zero-order extrapolation (outflow, bc 1), or
+// the mirror image across the wall (reflective, bc 2: cell -1-g for g < 0, 2n-1-g for
+// g >= n, repeated for tiny grids, i.e. the grid continued with period 2n and mirrored in
+// every other copy).
 __host__ __device__ __forceinline__ int ghost_src(int g, int n, int bc) {
     if (bc == 0) {
         g %= n;
         return g < 0 ? g + n : g;
     }
+    if (bc == 2) {
+        int m = g % (2 * n);
+        if (m < 0) m += 2 * n;
+        return m < n ? m : 2 * n - 1 - m;
+    }
     return g < 0 ? 0 : (g >= n ? n - 1 : g);
+}
+
+// Whether the reflective ghost g is a mirror image (its normal momentum changes sign).
+__host__ __device__ __forceinline__ bool ghost_mirrored(int g, int n, int bc) {
+    if (bc != 2) return false;
+    int m = g % (2 * n);
+    if (m < 0) m += 2 * n;
+    return m >= n;
 }
 
 }  // namespace wz

@@ -17,7 +17,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libwenozn.so")
 
 WENOZN_OK, WENOZN_EINVAL, WENOZN_ECUDA, WENOZN_ENOMEM_WS, WENOZN_ENONFINITE, WENOZN_ETIMEOUT = range(6)
-WENOZN_BC_PERIODIC, WENOZN_BC_OUTFLOW = 0, 1
+WENOZN_BC_PERIODIC, WENOZN_BC_OUTFLOW, WENOZN_BC_REFLECTIVE = 0, 1, 2
+WENOZN_WEIGHTS_ZN, WENOZN_WEIGHTS_Z, WENOZN_WEIGHTS_LINEAR, WENOZN_WEIGHTS_JS = 0, 1, 2, 3
+WENOZN_SPLIT_LF, WENOZN_SPLIT_LF_FIELD, WENOZN_SPLIT_LLF, WENOZN_SPLIT_SW = 0, 1, 2, 3
 WENOZN_ADVECTION_1D, WENOZN_EULER_1D, WENOZN_EULER_2D = 0, 1, 2
 NVAR = {WENOZN_ADVECTION_1D: 1, WENOZN_EULER_1D: 3, WENOZN_EULER_2D: 4}
 
@@ -30,7 +32,8 @@ class WenoznError(RuntimeError):
 
 class wenozn_problem(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32), ("weights", ctypes.c_int32),
+                ("split", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("eps", ctypes.c_double), ("A", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("adv_speed", ctypes.c_double)]
@@ -60,6 +63,8 @@ _SIGNATURES = {
     "wenozn_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_fill_ghosts": [_P, _VP, _VP],
     "wenozn_reconstruct": [_VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP],
+    "wenozn_reconstruct_weights": [_VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_double, _VP],
     "wenozn_max_wavespeed": [_P, _VP, _VP, _VP, _VP],
     "wenozn_flux": [_P, _VP, _VP, ctypes.c_int32, _VP, _VP],
     "wenozn_rhs": [_P, _VP, _VP, _VP, ctypes.c_size_t, _VP],
@@ -180,6 +185,17 @@ def wenozn_reconstruct(f_padded: torch.Tensor, fhat: torch.Tensor, side: int = 1
     _check("wenozn_reconstruct", lib().wenozn_reconstruct(_dev_ptr(f_padded, "f_padded"), n,
                                                           _dev_ptr(fhat, "fhat"), int(side), float(eps),
                                                           float(A), _stream(stream)))
+
+
+def wenozn_reconstruct_weights(f_padded: torch.Tensor, fhat: torch.Tensor, side: int = 1,
+                               weights: int = WENOZN_WEIGHTS_ZN, eps: float = 1e-40, A: float = 10.0,
+                               stream=None) -> None:
+    n = f_padded.numel() - 6
+    if fhat.numel() != n + 1:
+        raise ValueError("fhat must hold n + 1 values")
+    _check("wenozn_reconstruct_weights", lib().wenozn_reconstruct_weights(
+        _dev_ptr(f_padded, "f_padded"), n, _dev_ptr(fhat, "fhat"), int(side), int(weights), float(eps),
+        float(A), _stream(stream)))
 
 
 def wenozn_max_wavespeed(p: wenozn_problem, U: torch.Tensor, alpha_out: torch.Tensor,

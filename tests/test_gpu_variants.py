@@ -1,0 +1,248 @@
+"""The variant weight functions, flux splittings and the reflective wall on the CUDA path
+(generic kernel instantiations), against the CPU oracle, element by element; the WENO-Z
+column of the critical-point table through the GPU reconstruction; the paper's four-wave
+advection (self-similarity under rescaling) and two-blast-wave problems.
+
+Tolerances as for the default scheme: relative L-infinity <= 1e-12 after one RHS or one RK3
+step, <= 1e-9 at a final time; LF speeds (global and per field) and CFL steps bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2004_07954_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-12
+FINAL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def wz():
+    from paper_2004_07954_gb300 import build, wenozn
+    build.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return wenozn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_linf(got, want):
+    scale = np.abs(want).max()
+    return np.abs(got - want).max() / (scale if scale > 0 else 1.0)
+
+
+def eps_of(weights):
+    return 1e-6 if weights == 3 else 1e-40            # Jiang-Shu with its own eps (Sec. 2.1)
+
+
+def problems(wz, orc, system, nx, ny, dx, dy, bcx, bcy, weights, split):
+    eps = eps_of(weights)
+    p = wz.wenozn_problem_init(system, nx, ny, dx, dy, bc_x=bcx, bc_y=bcy, weights=weights, split=split, eps=eps)
+    P = orc.problem(system, nx, ny, dx=dx, dy=dy, bc_x=bcx, bc_y=bcy, weights=weights, split=split, eps=eps)
+    return p, P
+
+
+# ------------------------------------------------------------------ reconstruction
+@pytest.mark.parametrize("weights", [1, 2, 3])
+@pytest.mark.parametrize("n", [5, 300, 4099])
+def test_reconstruct_weights_random(wz, orc, weights, n):
+    g = np.random.default_rng(n + 11 * weights)
+    for side in (1, -1):
+        for scale in (1.0, 1e-3, 1e4):
+            f = g.normal(size=n + 6) * scale
+            f[g.random(n + 6) < 0.1] += 5 * scale
+            out = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+            wz.wenozn_reconstruct_weights(dev(f), out, side, weights, eps_of(weights))
+            want = orc.reconstruct(f, side, eps=eps_of(weights), kind=weights)
+            assert np.abs(host(out) - want).max() <= STEP_TOL * np.abs(f).max()
+
+
+def test_table3_weno_z_column_on_gpu(wz):
+    """The WENO-Z (q = 1) column of the paper's critical-point table through the CUDA
+    reconstruction: every row whose error lies above FP64 round-off (k = 1: j = 0, 1;
+    k = 2, 3: all eight)."""
+    from conftest import read_golden
+    rows = {1: range(0, 2), 2: range(0, 8), 3: range(0, 8)}
+    checked = 0
+    for k, j, z, _za, _zn in read_golden("table3_critical_point.txt"):
+        k, j = int(k), int(j)
+        if j not in rows[k]:
+            continue
+        dx = 0.025 / 2 ** j
+        xs = dx * np.arange(-3, 4)
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+        wz.wenozn_reconstruct_weights(dev(xs ** k * np.exp(xs)), out, 1, wz.WENOZN_WEIGHTS_Z, 1e-40)
+        fh = host(out)
+        err = abs((fh[1] - fh[0]) / dx - (1.0 if k == 1 else 0.0))
+        assert err == pytest.approx(z, rel=1e-4)
+        checked += 1
+    assert checked == 18
+
+
+# ------------------------------------------------------------------ one RHS / RK3 step
+CASES = [
+    (1, 1100, 1, 0, 1),      # 1D, periodic, short-line tiles, ragged
+    (1, 3000, 1, 2, 1),      # 1D, reflective walls
+    (2, 70, 53, 1, 2),       # 2D, outflow x, reflective y
+    (2, 64, 40, 2, 0),       # 2D, reflective x, periodic y
+]
+
+
+def _state(system, nx, ny, seed):
+    if system == 1:
+        return inputs.euler1d_ic(nx, seed)
+    return inputs.euler2d_ic(nx, ny, seed)
+
+
+@pytest.mark.parametrize("split", [0, 1, 2, 3])
+@pytest.mark.parametrize("weights", [0, 1, 3])
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}d-{c[1]}x{c[2]}-bc{c[3]}{c[4]}" for c in CASES])
+def test_variant_rhs_step_and_speeds(wz, orc, case, weights, split):
+    system, nx, ny, bcx, bcy = case
+    dx = 10.0 / nx if system == 1 else 1.0 / nx
+    p, P = problems(wz, orc, system, nx, ny, dx, 1.0 / ny, bcx, bcy, weights, split)
+    U0 = _state(system, nx, ny, seed=weights + 4 * split)
+    U = dev(U0)
+    # LF speeds (8 values with the per-field splitting) bit for bit
+    a = torch.zeros(8, dtype=torch.float64, device="cuda")
+    wz.wenozn_max_wavespeed(p, U, a)
+    a = host(a)
+    assert a[0] == orc.max_wavespeed(P, U0, 0)
+    if system == 2:
+        assert a[1] == orc.max_wavespeed(P, U0, 1)
+    if split == 1:
+        for k in range(3):
+            assert a[2 + k] == orc.field_speed(P, U0, 0, k)
+            if system == 2:
+                assert a[5 + k] == orc.field_speed(P, U0, 1, k)
+    # one RHS
+    S = wz.Solver(p)
+    L = S.rhs(U)
+    assert rel_linf(host(L), orc.rhs(P, U0)) <= STEP_TOL
+    # one RK3 step (CFL step on the device)
+    dt = S.step(U, return_dt=True)
+    want, dt_o = orc.rk3_step(P, U0)
+    assert dt == dt_o
+    assert rel_linf(host(U), want) <= STEP_TOL
+    assert S.status() == 0
+
+
+@pytest.mark.parametrize("weights", [0, 1, 3])
+def test_advection_variants_and_reflective(wz, orc, weights):
+    """Advection ignores the splitting; the reflective wall mirrors the scalar."""
+    n = 500
+    U0 = inputs.four_wave_ic(n)
+    for bc in (0, 2):
+        p, P = problems(wz, orc, 0, n, 1, 2.0 / n, 1.0, bc, bc, weights, 3)
+        S = wz.Solver(p)
+        assert rel_linf(host(S.rhs(dev(U0))), orc.rhs(P, U0)) <= STEP_TOL
+
+
+@pytest.mark.parametrize("system", [1, 2])
+def test_fill_ghosts_reflective(wz, system):
+    """Ghost cells of a reflective wall: the mirror image with the normal momentum negated."""
+    nx, ny = 9, 7 if system == 2 else 1
+    nv = 3 if system == 1 else 4
+    g = np.random.default_rng(3)
+    p = wz.wenozn_problem_init(system, nx, ny, 0.1, 0.1, bc_x=2, bc_y=2)
+    if system == 1:
+        Up = np.zeros((nv, nx + 6))
+        Up[:, 3:nx + 3] = g.normal(size=(nv, nx))
+        t = dev(Up)
+        wz.wenozn_fill_ghosts(p, t)
+        got = host(t)
+        for m in range(1, 4):
+            sgn = np.array([1.0, -1.0, 1.0])
+            assert np.array_equal(got[:, 3 - m], sgn * Up[:, 2 + m])
+            assert np.array_equal(got[:, nx + 2 + m], sgn * Up[:, nx + 3 - m])
+    else:
+        Up = np.zeros((nv, ny + 6, nx + 6))
+        Up[:, 3:ny + 3, 3:nx + 3] = g.normal(size=(nv, ny, nx))
+        t = dev(Up)
+        wz.wenozn_fill_ghosts(p, t)
+        got = host(t)
+        sx = np.array([1.0, -1.0, 1.0, 1.0]).reshape(4, 1)
+        sy = np.array([1.0, 1.0, -1.0, 1.0]).reshape(4, 1)
+        for m in range(1, 4):
+            assert np.array_equal(got[:, 3:ny + 3, 3 - m], sx * Up[:, 3:ny + 3, 2 + m])
+            assert np.array_equal(got[:, 3 - m, :], sy * got[:, 2 + m, :])   # corners mirrored twice
+            assert np.array_equal(got[:, ny + 2 + m, :], sy * got[:, ny + 3 - m, :])
+
+
+# ------------------------------------------------------------------ final times
+def test_blast_waves_final_time(wz, orc):
+    """Two interacting blast waves (Sec. 4.3.2), N = 400, reflective walls, CFL 0.5 to
+    t = 0.038, default scheme and Steger-Warming splitting."""
+    n = 400
+    U0 = inputs.blast_wave_ic(n)
+    for split in (0, 3):
+        p, P = problems(wz, orc, 1, n, 1, 1.0 / n, 1.0, 2, 2, 0, split)
+        S = wz.Solver(p)
+        t = dev(U0)
+        steps = S.run(t, 0.038)
+        want, steps_o = orc.run(P, U0, 0.038)
+        assert steps == steps_o
+        assert rel_linf(host(t), want) <= FINAL_TOL
+        assert S.status() == 0
+
+
+def test_four_wave_self_similarity(wz, orc):
+    """Sec. 4.2, case 1 (N = 200, periodic, CFL 0.5 to T = 6): the solution for the initial
+    data scaled by 1/A is the A = 1 solution scaled by 1/A, for A = 100 and 0.01, since
+    WENO-ZN combines only quantities of the same dimension (eps = 1e-40 is negligible next
+    to every nonzero indicator); and the A = 1 run matches the oracle."""
+    n = 200
+    runs = {}
+    for A in (1.0, 100.0, 0.01):
+        p = wz.wenozn_problem_init(0, n, 1, 2.0 / n, 1.0, bc_x=0)
+        S = wz.Solver(p)
+        t = dev(inputs.four_wave_ic(n, A))
+        S.run(t, 6.0)
+        runs[A] = host(t)
+    base = runs[1.0]
+    for A in (100.0, 0.01):
+        assert rel_linf(A * runs[A], base) <= 1e-12
+    P = orc.problem(0, n, 1, dx=2.0 / n, bc_x=0)
+    want, _ = orc.run(P, inputs.four_wave_ic(n), 6.0)
+    assert rel_linf(base, want) <= FINAL_TOL
+
+
+@pytest.mark.parametrize("split", [1, 2, 3])
+def test_euler2d_variants_final_time(wz, orc, split):
+    """2D Riemann problem, reflective walls in x, outflow in y, 40 x 32, 25 CFL steps."""
+    nx, ny = 40, 32
+    U0 = inputs.euler2d_ic(nx, ny, 1)
+    p, P = problems(wz, orc, 2, nx, ny, 1.0 / nx, 1.0 / ny, 2, 1, 0, split)
+    S = wz.Solver(p)
+    t = dev(U0)
+    want = U0.copy()
+    for _ in range(25):
+        dt = S.step(t, return_dt=True)
+        want, dt_o = orc.rk3_step(P, want)
+        assert dt == dt_o
+    assert rel_linf(host(t), want) <= FINAL_TOL
+
+
+def test_variant_arguments_rejected(wz):
+    p = wz.wenozn_problem_init(1, 64, 1, 0.1, 1.0, weights=4)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_workspace_size(p)
+    p = wz.wenozn_problem_init(1, 64, 1, 0.1, 1.0, split=5)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_workspace_size(p)
+    p = wz.wenozn_problem_init(1, 64, 1, 0.1, 1.0, bc_x=3)
+    with pytest.raises(wz.WenoznError):
+        wz.wenozn_workspace_size(p)
+    # the adjoint covers the default scheme only
+    for kw in ({"weights": 1}, {"split": 3}, {"bc_x": 2}):
+        p = wz.wenozn_problem_init(1, 64, 1, 0.1, 1.0, **kw)
+        with pytest.raises(wz.WenoznError):
+            wz.wenozn_vjp_workspace_size(p)
