@@ -40,7 +40,7 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "69e1410c0a104936", "n": 4096, "bytes": 964.3e6}
+TRAFFIC_CAPTURE = {"sha256_16": "ae2478cba83ce2c7", "n": 4096, "bytes": 961.6e6}
 
 
 def kernel_source_hash() -> str:
@@ -68,20 +68,35 @@ def parse_args():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-fd-dirs", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
-    ap.add_argument("--only", choices=["batched", "adjoint"], default=None,
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--only", choices=["batched", "adjoint", "variants"], default=None,
                     help="run only this part and print its object (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
 
 
-def algorithmic_flops(nx: int, ny: int) -> dict:
-    """Algorithmic FP64 operations (one per add, mul, div, sqrt) of the scheme as the paper
-    writes it, counted by the oracle's op-counting instantiation (constants below)."""
-    iface, cell, speed, diff = 1098.0, 42.0, 28.0, 20.0      # 2D Euler, per unit
+# Algorithmic FP64 operations (one per add, mul, div, sqrt of the scheme as the paper writes
+# it, comparisons apart) per unit, as the oracle's op-counting instantiation counts them
+# (oracle.opcount_parts; tests/test_opcount.py checks these tables against it):
+# (interface flux, split fluxes and Roe ingredients per cell and sweep, LF-speed evaluation
+# per cell (both directions in 2D, with the per-field speeds where the splitting needs them),
+# flux difference per cell (all directions), RK3 combination per cell and step).
+OPS_2D = {  # (weights, split): per-unit counts, 2D Euler
+    (0, 0): (1090.0, 42.0, 28.0, 20.0, 48.0),     # WENO-ZN, global LF (the default scheme)
+    (0, 1): (1274.0, 22.0, 58.0, 20.0, 48.0),     # per-field LF
+    (0, 2): (1274.0, 22.0, 28.0, 20.0, 48.0),     # local LF
+    (0, 3): (1090.0, 152.0, 28.0, 20.0, 48.0),    # Steger-Warming
+}
+OPS_1D_CELL_UPDATE = 2448.0     # 1D Euler, default scheme, per cell-update (large grid)
+
+
+def algorithmic_flops(nx: int, ny: int, weights: int = 0, split: int = 0) -> dict:
+    """Algorithmic FP64 operations of one 2D RK3 step and of its flux launches."""
+    iface, cell, speed, diff, rk = OPS_2D[(weights, split)]
     x_flux = iface * (nx + 1) * ny + cell * nx * ny
     y_flux = iface * nx * (ny + 1) + cell * nx * ny
     per_stage = x_flux + y_flux + (speed + diff) * nx * ny
-    step = 3 * per_stage + 48.0 * nx * ny
+    step = 3 * per_stage + rk * nx * ny
     return {"x_flux": x_flux, "y_flux": y_flux, "step": step,
             "per_cell_update": step / (nx * ny), "per_interface": iface}
 
@@ -194,7 +209,7 @@ def bench_batched(wenozn, inputs, seed: int, K: int, B: int = 2048) -> dict:
     graph_ms = e0.elapsed_time(e1)
     del g2, solvers, states
     shape = wenozn.wenozn_batch_shape(bt.bp.shape)
-    flops = 2466.0 * cells          # algorithmic flops per cell-update (1D Euler, large grid)
+    flops = OPS_1D_CELL_UPDATE * cells          # algorithmic flops per cell-update
     return {"workload": f"{B} independent 1D Euler problems (seeded Shu-Osher family), sizes log-uniform "
                         f"in [128, 16384], {cells} cells, outflow, per-instance CFL 0.5 step",
             "metric": "cell-updates/s", "value": cells / (ms_step / 1e3), "ms_per_step": ms_step,
@@ -206,6 +221,51 @@ def bench_batched(wenozn, inputs, seed: int, K: int, B: int = 2048) -> dict:
                                       "speedup_vs_eager": round(eager_ms / ms_step, 1),
                                       "speedup_vs_graph": round(graph_ms / ms_step, 2)},
             "device_status": status}
+
+
+VARIANTS = [("weno_z", 1, 0), ("jiang_shu", 3, 0), ("per_field_lf", 0, 1), ("local_lf", 0, 2),
+            ("steger_warming", 0, 3)]
+
+
+def bench_variants(wenozn, inputs, seed: int, n: int = 4096, K: int = 3) -> dict:
+    """The variant weight functions and flux splittings (generic kernels) on the benchmark's
+    2D Euler workload: K RK3 steps after one warm-up step each, CUDA events; the default
+    scheme timed the same way for the ratio.  The FP64 fraction uses the oracle's operation
+    count of each splitting (weight variants: none, since the oracle also evaluates the
+    WENO-ZN quantities for them)."""
+    import torch
+    U0 = torch.from_numpy(inputs.euler2d_ic(n, n, seed)).cuda()
+    out = {"workload": f"2D Euler {n}x{n}, the benchmark's seeded four-quadrant problem, outflow, CFL 0.5",
+           "steps": K}
+    base_ms = None
+    for name, weights, split in [("default", 0, 0)] + VARIANTS:
+        eps = 1e-6 if weights == 3 else 1e-40
+        p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_2D, n, n, 1.0 / n, 1.0 / n, weights=weights,
+                                       split=split, eps=eps)
+        S = wenozn.Solver(p)
+        U = U0.clone()
+        S.step(U)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            S.step(U)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        rec = {"weights": weights, "split": split, "ms_per_step": round(ms, 3),
+               "cell_updates_per_s": n * n / (ms / 1e3), "device_status": S.status()}
+        if (weights, split) in OPS_2D:
+            fl = algorithmic_flops(n, n, weights, split)["step"]
+            rec["fp64_frac"] = round(fl / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)
+        if base_ms is None:
+            base_ms = ms
+        else:
+            rec["time_vs_default"] = round(ms / base_ms, 3)
+        out[name] = rec
+        del S, U
+        torch.cuda.empty_cache()
+    return out
 
 
 def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, fd_dirs: int = 20) -> dict:
@@ -386,6 +446,8 @@ def main():
     if args.only is not None:
         if args.only == "batched":
             part = bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
+        elif args.only == "variants":
+            part = bench_variants(wenozn, inputs, args.seed + rank, args.n)
         else:
             part = bench_adjoint(wenozn, inputs, args.seed + rank, steps=args.adjoint_steps,
                                  fd_dirs=args.adjoint_fd_dirs)
@@ -491,6 +553,7 @@ def main():
            "d2h_bytes_per_step": nbytes, "steps": ke}
 
     batched = None if args.no_batched else bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
+    variants = None if args.no_variants else bench_variants(wenozn, inputs, args.seed + rank, n)
     adjoint = None if args.no_adjoint else bench_adjoint(wenozn, inputs, args.seed + rank,
                                                          steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
 
@@ -508,7 +571,7 @@ def main():
                            "parallelism": f"{world} independent replica(s), one per GPU",
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "variants": variants, "adjoint": adjoint,
                 "gpu_launches": 10 * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -84,7 +84,10 @@ def lib():
                 "oracle_roe_eigen": (None, [_D, _D, ctypes.c_int, ctypes.c_double, _D]),
                 "oracle_normal_flux": (None, [_D, ctypes.c_int, ctypes.c_double, _D]),
                 "oracle_opcount_rhs": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
+                "oracle_opcount_rhs_variant": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, _D]),
                 "oracle_opcount_parts": (None, [ctypes.c_int, _D]),
+                "oracle_opcount_parts_variant": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
                 "oracle_rhs_jvp": (None, [_P, _D, _D, _D, _D]),
                 "oracle_steger_warming": (None, [_D, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]),
                 "oracle_field_speed": (ctypes.c_double, [_P, _D, ctypes.c_int, ctypes.c_int]),
@@ -202,16 +205,17 @@ def normal_flux(U, gamma=1.4) -> np.ndarray:
     return out[: u.shape[0]]
 
 
-def opcount_rhs(system, nx, ny=1) -> dict:
+def opcount_rhs(system, nx, ny=1, weights=W_ZN, split=S_LF) -> dict:
+    """Algorithmic operation counts of one RHS evaluation on an nx x ny periodic grid."""
     out = np.zeros(5)
-    lib().oracle_opcount_rhs(int(system), int(nx), int(ny), _ptr(out))
+    lib().oracle_opcount_rhs_variant(int(system), int(nx), int(ny), int(weights), int(split), _ptr(out))
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), out.tolist()))
 
 
-def opcount_parts(system) -> dict:
+def opcount_parts(system, weights=W_ZN, split=S_LF) -> dict:
     """Algorithmic operations (add+mul+div+sqrt) of the pieces of one RHS evaluation."""
     out = np.zeros(9)
-    lib().oracle_opcount_parts(int(system), _ptr(out))
+    lib().oracle_opcount_parts_variant(int(system), int(weights), int(split), _ptr(out))
     return {"interface": out[0], "cell_per_sweep": out[1], "wavespeed_cell": out[2],
             "difference_cell_per_dir": out[3], "cmp_interface": out[4], "cmp_cell_per_sweep": out[5],
             "cmp_wavespeed_cell": out[6]}

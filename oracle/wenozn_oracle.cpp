@@ -489,23 +489,23 @@ T max_wavespeed(const Problem& P, const T* U, int dir) {
     return best;
 }
 
-// Largest |lambda| of one eigenvalue kind (0: u_n - c, 1: u_n, 2: u_n + c) over the
+// Largest |lambda| of each eigenvalue kind (0: u_n - c, 1: u_n, 2: u_n + c) over the
 // interior: the per-field LF speeds.
 template <class T>
-T max_field_speed(const Problem& P, const T* U, int dir, int kind) {
+void max_field_speeds(const Problem& P, const T* U, int dir, T* best) {
     const int nv = nvar_of(P.system);
     const int64_t nc = int64_t(P.nx) * P.ny;
-    T best = T(0);
+    for (int k = 0; k < 3; ++k) best[k] = T(0);
     for (int64_t c = 0; c < nc; ++c) {
         T s[4];
         for (int k = 0; k < nv; ++k) s[k] = U[k * nc + c];
         if (dir == 1) std::swap(s[1], s[2]);
         Prim<T> w = primitives(s, nv, T(P.gamma));
         const T cs = sound_speed(w, T(P.gamma));
-        const T lam = kind == 0 ? w.un - cs : (kind == 1 ? w.un : w.un + cs);
-        best = tmax(best, tabs(lam));
+        best[0] = tmax(best[0], tabs(w.un - cs));
+        best[1] = tmax(best[1], tabs(w.un));
+        best[2] = tmax(best[2], tabs(w.un + cs));
     }
-    return best;
 }
 
 // The speeds a splitting needs for one stage input: the global LF speeds per direction and,
@@ -517,11 +517,10 @@ Speeds<T> stage_speeds(const Problem& P, const T* U) {
     Speeds<T> a{};
     a.ax = max_wavespeed(P, U, 0);
     a.ay = P.system == SYS_EULER2D ? max_wavespeed(P, U, 1) : T(0);
-    if (P.split == S_LF_FIELD && P.system != SYS_ADV1D)
-        for (int k = 0; k < 3; ++k) {
-            a.fx[k] = max_field_speed(P, U, 0, k);
-            if (P.system == SYS_EULER2D) a.fy[k] = max_field_speed(P, U, 1, k);
-        }
+    if (P.split == S_LF_FIELD && P.system != SYS_ADV1D) {
+        max_field_speeds(P, U, 0, a.fx);
+        if (P.system == SYS_EULER2D) max_field_speeds(P, U, 1, a.fy);
+    }
     return a;
 }
 
@@ -763,10 +762,10 @@ void oracle_normal_flux(const double* U, int nv, double gamma, double* F) {
 // Algorithmic floating-point operations of one RHS evaluation on an nx x ny periodic
 // grid (alpha reduction included), counted by running the oracle on OpCount scalars.
 // out: add mul div sqrt cmp (totals).
-void oracle_opcount_rhs(int system, int nx, int ny, double* out) {
+void oracle_opcount_rhs_variant(int system, int nx, int ny, int weights, int split, double* out) {
     Problem P{};
     P.system = system; P.nx = nx; P.ny = ny; P.bc_x = BC_PERIODIC; P.bc_y = BC_PERIODIC;
-    P.weights = W_ZN; P.dx = 0.1; P.dy = 0.1; P.gamma = 1.4; P.eps = 1e-40; P.A = 10;
+    P.weights = weights; P.split = split; P.dx = 0.1; P.dy = 0.1; P.gamma = 1.4; P.eps = 1e-40; P.A = 10;
     P.cfl = 0.5; P.adv_speed = 1.0;
     const int nv = nvar_of(system);
     const int64_t nc = int64_t(nx) * ny;
@@ -793,15 +792,19 @@ void oracle_opcount_rhs(int system, int nx, int ny, double* out) {
     out[3] = double(g_tally.sqrt_); out[4] = double(g_tally.cmp);
 }
 
+void oracle_opcount_rhs(int system, int nx, int ny, double* out) {
+    oracle_opcount_rhs_variant(system, nx, ny, W_ZN, S_LF, out);
+}
+
 // Algorithmic operations of the pieces of one RHS, counted on OpCount scalars (add+mul+div
 // +sqrt; comparisons apart): out[0] one interface flux, out[1] the per-cell split-flux
 // and Roe ingredients of one sweep (per cell), out[2] one cell's LF-speed evaluation
 // (both directions in 2D), out[3] one cell's flux difference per direction,
 // out[4..8] the comparison counts of the same pieces.
-void oracle_opcount_parts(int system, double* out) {
+void oracle_opcount_parts_variant(int system, int weights, int split, double* out) {
     Problem P{};
     P.system = system; P.nx = 8; P.ny = 1; P.bc_x = BC_PERIODIC; P.bc_y = BC_PERIODIC;
-    P.weights = W_ZN; P.dx = 0.1; P.dy = 0.1; P.gamma = 1.4; P.eps = 1e-40; P.A = 10;
+    P.weights = weights; P.split = split; P.dx = 0.1; P.dy = 0.1; P.gamma = 1.4; P.eps = 1e-40; P.A = 10;
     P.cfl = 0.5; P.adv_speed = 1.0;
     const int nv = nvar_of(system);
     std::vector<OpCount> line(14 * nv);
@@ -820,8 +823,9 @@ void oracle_opcount_parts(int system, double* out) {
     line_cells(P, line.data(), 14, nv, OpCount(2.0), lc);
     out[1] = total(g_tally) / 14.0; out[5] = double(g_tally.cmp) / 14.0;
     OpCount F[4];
+    OpCount af[3] = {OpCount(1.0), OpCount(1.5), OpCount(2.0)};
     g_tally = OpTally();
-    interface_flux(P, lc, nv, 5, F);
+    interface_flux(P, lc, nv, 5, F, af);
     out[0] = total(g_tally); out[4] = double(g_tally.cmp);
     std::vector<OpCount> U(nv * 8);
     for (int k = 0; k < nv; ++k)
@@ -831,6 +835,11 @@ void oracle_opcount_parts(int system, double* out) {
         P.nx = 8;
         max_wavespeed<OpCount>(P, U.data(), 0);
         if (system == SYS_EULER2D) max_wavespeed<OpCount>(P, U.data(), 1);
+        if (split == S_LF_FIELD) {
+            OpCount fs[3];
+            max_field_speeds<OpCount>(P, U.data(), 0, fs);
+            if (system == SYS_EULER2D) max_field_speeds<OpCount>(P, U.data(), 1, fs);
+        }
     }
     out[2] = total(g_tally) / 8.0; out[6] = double(g_tally.cmp) / 8.0;
     // flux difference: -(F_{i+1/2} - F_{i-1/2}) / dx per variable
@@ -848,7 +857,9 @@ void oracle_steger_warming(const double* U, int nv, double gamma, int sign, doub
 
 // Largest |lambda| of eigenvalue kind (0: u_n - c, 1: u_n, 2: u_n + c) over the grid.
 double oracle_field_speed(const Problem* P, const double* U, int dir, int kind) {
-    return max_field_speed<double>(*P, U, dir, kind);
+    double best[3];
+    max_field_speeds<double>(*P, U, dir, best);
+    return best[kind];
 }
 
 // RHS with the LF speeds given: sp = (alpha_x, alpha_y, fx0, fx1, fx2, fy0, fy1, fy2).
@@ -858,6 +869,8 @@ void oracle_rhs_speeds(const Problem* P, const double* U, const double* sp, doub
     for (int k = 0; k < 3; ++k) { a.fx[k] = sp[2 + k]; a.fy[k] = sp[5 + k]; }
     rhs_with_speeds<double>(*P, U, Lout, a);
 }
+
+void oracle_opcount_parts(int system, double* out) { oracle_opcount_parts_variant(system, W_ZN, S_LF, out); }
 
 // Jacobian-vector products of the discrete scheme (forward mode, Dual scalars).
 // rhs: L = rhs(U), dL = J(U) dU (the LF speed differentiated through its argmax cell).
