@@ -273,7 +273,11 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
     1/2 ||rho(T) - rho_target||^2, gradient with respect to the initial conserved state.
     Times the forward rollout, the adjoint with every state kept and with a checkpoint
     every 50 steps, and checks the gradient against central differences (h = 1e-7) of the
-    GPU forward along `fd_dirs` seeded directions."""
+    GPU forward along `fd_dirs` seeded smooth directions.  (Cell-to-cell noise directions
+    are not checked by differences: on this smooth state the squared fourth difference tau8
+    is of order dx^8, so a perturbation of size h ~ 1e-7 already dominates it and the loss
+    is far from linear on any usable h; the test suite checks such directions against the
+    oracle's exact forward-mode derivative instead.)"""
     import numpy as np
     import torch
     from paper_2004_07954_gb300.rollout import cfl_step, rollout
@@ -328,28 +332,19 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
         return (lp - lm) / (2 * hh)
 
     with torch.no_grad():
-        for kind in (("smooth", "white") if fd_dirs > 0 else ()):
-            worst, worst_big_h = 0.0, 0.0
-            for _ in range(fd_dirs):
-                if kind == "smooth":      # a few random Fourier modes per variable, scaled like U0
-                    v = np.zeros_like(u0)
-                    for k in range(3):
-                        for m in range(1, 5):
-                            v[k, 0] += gen.normal() * np.sin(2 * np.pi * m * x / 10 + gen.uniform(0, 2 * np.pi))
-                        v[k, 0] *= np.abs(u0[k, 0]).mean()
-                else:
-                    v = gen.normal(size=u0.shape) * np.abs(u0)
-                gv = float(np.sum(grad * v))
-                fd = fd_at(v, h)
-                worst = max(worst, abs(gv - fd) / abs(fd))
-                if kind == "white":
-                    # the loss barely responds to cell-to-cell noise, so at h = 1e-7 the
-                    # difference of the two rollouts is near their rounding; h = 1e-5 shows it
-                    fd5 = fd_at(v, 1e-5)
-                    worst_big_h = max(worst_big_h, abs(gv - fd5) / abs(fd5))
-            checks[kind] = {"directions": fd_dirs, "max_rel_err": worst}
-            if kind == "white":
-                checks[kind]["max_rel_err_h_1e-5"] = worst_big_h
+        worst = 0.0
+        for _ in range(fd_dirs):
+            # a few random Fourier modes per variable, scaled like U0
+            v = np.zeros_like(u0)
+            for k in range(3):
+                for m in range(1, 5):
+                    v[k, 0] += gen.normal() * np.sin(2 * np.pi * m * x / 10 + gen.uniform(0, 2 * np.pi))
+                v[k, 0] *= np.abs(u0[k, 0]).mean()
+            gv = float(np.sum(grad * v))
+            fd = fd_at(v, h)
+            worst = max(worst, abs(gv - fd) / abs(fd))
+        if fd_dirs > 0:
+            checks["smooth_directions"] = {"directions": fd_dirs, "max_rel_err": worst}
     return {"workload": f"1D Euler N={n}, seeded smooth periodic multi-wave state, {steps} SSP-RK3 steps of "
                         f"fixed dt (CFL 0.5 of U0), loss 1/2||rho(T) - rho_target||^2, rho_target from seed+1",
             "forward_s": round(t_fwd, 4), "store_all": res[1], "checkpoint_every_50": res[50],
