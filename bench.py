@@ -52,6 +52,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Units all ranks processed per second: every rank advances its own replica."""
+    return world * steps * units_per_rank_step / (ms_max / 1e3)
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,13 +498,9 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     status = S.status()
-    value = world * args.steps * n * n / (ms / 1e3)
+    value = job_throughput(n * n, args.steps, world, ms)
 
     # ---- dominant kernels, timed live on the launching stream ------------------------
     alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -560,13 +572,9 @@ def main():
     e2e_run(ke, e0)
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ems], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+    ems = max_over_ranks(e0.elapsed_time(e1), world)
     nbytes = U.numel() * U.element_size()
-    e2e = {"value": world * ke * n * n / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    e2e = {"value": job_throughput(n * n, ke, world, ems), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "steps": ke,
            "copies": "pinned host <-> device on one stream per direction, overlapped with the previous/next step"}
 

@@ -211,6 +211,13 @@ const double* wenozn_workspace_dt(const void* ws);
  * non-zero, resets it. */
 wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, void* stream);
 
+/* Synchronises `stream` and returns in *device_status the device status bits (as
+ * wenozn_workspace_status reports them) raised in the control block that the most recent
+ * stepping call on `stream` used (wenozn_rhs, wenozn_rhs_noalloc, wenozn_rk3_step,
+ * wenozn_rk3_step_keep, wenozn_rhs_vjp, wenozn_rk3_step_vjp, wenozn_batch_rk3_step), then
+ * clears them; 0 when nothing ran on the stream.  That workspace must still be allocated. */
+wenozn_status wenozn_last_error(void* stream, int32_t* device_status);
+
 /* ---------------------------------------------------------------------------------------
  * Discrete adjoint of the 1D systems (advection and 1D Euler; 2D returns WENOZN_EINVAL).
  * Vector-Jacobian products of the scheme as implemented, with these conventions at its

@@ -90,6 +90,7 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
     VjpArgs v = vjp_args(*p, L, ws);
+    note_status(stream, &ctrl->status);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) {
         v.U = U;
@@ -118,6 +119,7 @@ wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, doub
     const bool euler = p->system != WENOZN_ADVECTION_1D;
 
     // recompute the stage inputs U1, U2 of the forward step (same kernels, fixed dt)
+    note_status(stream, &ctrl->status);
     cudaError_t e = cudaMemsetAsync(ctrl->alpha, 0, sizeof(ctrl->alpha), s);
     if (e == cudaSuccess)
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);

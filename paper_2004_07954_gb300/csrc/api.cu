@@ -2,11 +2,27 @@
 // the RHS evaluation and the SSP-RK3 step.  Declarations and contracts: include/wenozn.h.
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "host_common.h"
 
 using namespace wz;
 
+
+namespace wz {
+
+namespace {
+std::mutex g_status_mu;
+std::unordered_map<void*, int32_t*> g_status_of_stream;   // stream -> device status word
+}  // namespace
+
+void note_status(void* stream, int32_t* status_dev) {
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    g_status_of_stream[stream] = status_dev;
+}
+
+}  // namespace wz
 
 namespace {
 
@@ -163,6 +179,7 @@ wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, vo
         u.out = L;
         e = launch_update(p->system, u, s);
     }
+    note_status(stream, &ctrl->status);
     return cuda_status(e);
 }
 
@@ -178,6 +195,7 @@ wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, dou
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
     double* u1 = reinterpret_cast<double*>(ws_base(ws) + lay.u1);
     double* u2 = reinterpret_cast<double*>(ws_base(ws) + lay.u2);
+    note_status(stream, &ctrl->status);
     if (rk3_stages(*p, lay, ws, U, U, u1, u2, dt, t_remaining, s) != cudaSuccess) return WENOZN_ECUDA;
     if (dt_out) {
         cudaError_t e = cudaMemcpyAsync(dt_out, &ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -199,6 +217,7 @@ wenozn_status wenozn_rk3_step_keep(const wenozn_problem* p, const double* U, dou
     if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    note_status(stream, &ctrl->status);
     cudaError_t e = rk3_stages(*p, lay, ws, U, U_next, U1, U2, dt, 0.0, s);
     // the three stages' x speeds: alpha[s][0], s = 0, 1, 2 (a stride of two words)
     if (e == cudaSuccess)
@@ -221,6 +240,25 @@ wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, 
     if (e == cudaSuccess && clear) e = cudaMemsetAsync(&ctrl->status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return WENOZN_ECUDA;
     *status = host;
+    return WENOZN_OK;
+}
+
+wenozn_status wenozn_last_error(void* stream, int32_t* device_status) {
+    if (!device_status) return WENOZN_EINVAL;
+    int32_t* dev = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_status_mu);
+        auto it = g_status_of_stream.find(stream);
+        if (it != g_status_of_stream.end()) dev = it->second;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t host = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && dev) e = cudaMemcpyAsync(&host, dev, sizeof host, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dev) e = cudaMemsetAsync(dev, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return WENOZN_ECUDA;
+    *device_status = host;
     return WENOZN_OK;
 }
 

@@ -211,7 +211,9 @@ wenozn_status wenozn_batch_rk3_step(const wenozn_batch_params* bp, const int64_t
     const BatchLayout L = batch_layout(bp->nbatch, cells);
     if (ws_bytes < L.total) return WENOZN_ENOMEM_WS;
     const int shape = bp->shape < 0 ? default_shape() : bp->shape;
-    cudaError_t e = step_launches(bp, ptrs_of(ws, L), cells, U, shape, static_cast<cudaStream_t>(stream));
+    const Ptrs bptr = ptrs_of(ws, L);
+    note_status(stream, &bptr.ctrl->status);
+    cudaError_t e = step_launches(bp, bptr, cells, U, shape, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? WENOZN_OK : WENOZN_ECUDA;
 }
 

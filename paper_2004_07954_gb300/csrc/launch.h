@@ -104,6 +104,10 @@ int vjp_partial_count(int n);
 size_t vjp_contrib_doubles(int nv, int n);
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
 
+// Remembers the device status word the most recent stepping call on `stream` wrote to
+// (read back by wenozn_last_error).
+void note_status(void* stream, int32_t* status_dev);
+
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,

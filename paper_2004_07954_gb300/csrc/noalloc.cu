@@ -129,5 +129,6 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
         u.adv_speed = p->adv_speed;
         e = launch_update(p->system, u, s);
     }
+    note_status(stream, &ctrl->status);
     return e == cudaSuccess ? WENOZN_OK : WENOZN_ECUDA;
 }

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "wenozn_rk3_step": [_P, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                         _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
+    "wenozn_last_error": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
     "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
@@ -249,6 +250,13 @@ def wenozn_rk3_step(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, dt: fl
                                  ws.numel() * ws.element_size(), _stream(stream))
     _check("wenozn_rk3_step", code)
     return out.value if return_dt else None
+
+
+def wenozn_last_error(stream=None) -> int:
+    """Device status bits raised by the most recent stepping call on `stream` (cleared)."""
+    st = ctypes.c_int32(0)
+    _check("wenozn_last_error", lib().wenozn_last_error(_stream(stream), ctypes.byref(st)))
+    return st.value
 
 
 def wenozn_workspace_status(ws: torch.Tensor, clear: bool = False, stream=None) -> int:

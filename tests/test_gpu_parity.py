@@ -356,6 +356,11 @@ def test_nonfinite_status(wz):
     U[0, 0, 10] = -1.0
     S.step(dev(U), dt=1e-4)
     assert S.status() & (1 << wz.WENOZN_ENONFINITE)
+    # the same bits through the per-stream query, which clears them
+    assert wz.wenozn_last_error() & (1 << wz.WENOZN_ENONFINITE)
+    assert wz.wenozn_last_error() == 0 and S.status() == 0
+    S.step(dev(inputs.euler1d_ic(n, seed=0)), dt=1e-4)
+    assert wz.wenozn_last_error() == 0
 
 
 def test_invalid_arguments_gpu(wz):
