@@ -29,7 +29,8 @@ namespace wz {
 //    t_0 = D1 - 3 D2 = a - 4b + 3c, t_1 = D2 + D3 = b - d, t_2 = 3 D3 - D4 = 3c - 4d + e (equal
 //    inputs give exact zeros, so constant data keep exactly the linear weights), the
 //    sub-stencil fluxes are
-//    q_k = c + s_k/12 + t_k/4 (k = 0) and c + s_k/12 - t_k/4 (k = 1, 2);
+//    q_k = c + s_k/12 + t_k/4 (k = 0) and c + s_k/12 - t_k/4 (k = 1, 2), and since the
+//    normalised weights sum to one the centre value is taken out: f^ = c + sum w_k (q_k - c);
 //  * indicators are carried scaled by 4 together with eps: b_k = 4 (IS_k + eps)
 //    = 13/3 s_k^2 + t_k^2 + 4 eps, so C and tau8/(IS_k + eps) = 4 tau8 / b_k are unchanged;
 //  * IS_0 + IS_2 - tau5 = 2 min(IS_0, IS_2), i.e. 4 (IS_0 + IS_2 - tau5 + eps) = 2 min(b) - 4 eps
@@ -43,7 +44,7 @@ namespace wz {
 // Range: finite for |f| below ~1e20.
 // ------------------------------------------------------------------------------------
 struct ZnParts {
-    double num, den;     // f^ = num / den
+    double num, den, c;  // f^ = c + num / den
 };
 
 // Reciprocal of a positive, normal double: start from the hardware approximation
@@ -91,26 +92,27 @@ __host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double 
     const double a0 = fma(Y, b12, X);
     const double a1 = fma(Y, b02, X);
     const double a2 = fma(Y, b01, X);
-    // q_k scaled by the optimal-weight ratios (1, 6, 3): 6 q_1 = 6c + s_1/2 - 3 t_1/2,
-    // 3 q_2 = 3c + s_2/4 - 3 t_2/4
+    // q_k - c scaled by the optimal-weight ratios (1, 6, 3): q_0 - c = s_0/12 + t_0/4,
+    // 6 (q_1 - c) = s_1/2 - 3 t_1/2, 3 (q_2 - c) = s_2/4 - 3 t_2/4; the weights sum to one, so
+    // f^ = c + sum a_k (q_k - c) / sum a_k
     const double k1_12 = 1.0 / 12.0;
-    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
-    const double q0 = fma(k1_12, s0, fma(0.25, t0, c));
-    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
-    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
+    const double q0 = fma(k1_12, s0, 0.25 * t0);
+    const double q1 = fma(0.5, s1, -1.5 * t1);
+    const double q2 = fma(0.25, s2, -0.75 * t2);
     ZnParts r;
     r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
     r.den = fma(6.0, a1, fma(3.0, a2, a0));
+    r.c = c;
     return r;
 }
 
-// f^ = num / den.  With A > 0 and eps >= 1e-60, den >= 10 (A/4) (4 eps)^5 is a positive
+// f^ = c + num / den.  With A > 0 and eps >= 1e-60, den >= 10 (A/4) (4 eps)^5 is a positive
 // normal number, so the Newton reciprocal applies (fast_rcp = true, chosen by the host);
 // otherwise the IEEE division is used.
 __host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
                                                    double eps4, double A4, bool fast_rcp) {
     const ZnParts r = zn_parts(a, b, c, d, e, eps4, A4);
-    return fast_rcp ? r.num * rcp_nr(r.den) : r.num / r.den;
+    return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
 }
 
 // f^+ + f^- at one interface: plus side from (p0..p4) = h+_{i-2..i+2}, minus side from the
@@ -140,10 +142,9 @@ __host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, doubl
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
     const double k13_3 = 13.0 / 3.0;
     const double k1_12 = 1.0 / 12.0;
-    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
-    const double q0 = fma(k1_12, s0, fma(0.25, t0, c));
-    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
-    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
+    const double q0 = fma(k1_12, s0, 0.25 * t0);
+    const double q1 = fma(0.5, s1, -1.5 * t1);
+    const double q2 = fma(0.25, s2, -0.75 * t2);
     double a0 = 1.0, a1 = 1.0, a2 = 1.0;
     if (weights != 2) {
         const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));
@@ -165,13 +166,14 @@ __host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, doubl
     ZnParts r;
     r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
     r.den = fma(6.0, a1, fma(3.0, a2, a0));
+    r.c = c;
     return r;
 }
 
 __host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
                                                      double eps4, double A4, bool fast_rcp, int weights) {
     const ZnParts r = zn_parts_w(a, b, c, d, e, eps4, A4, weights);
-    return fast_rcp ? r.num * rcp_nr(r.den) : r.num / r.den;
+    return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
 }
 
 // ------------------------------------------------------------------------------------

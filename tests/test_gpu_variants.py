@@ -224,13 +224,16 @@ def test_blast_waves_default_scheme_within_its_conditioning(wz, orc):
         got = host(t)
         if T < 0.01:
             assert rel_linf(got, want) <= FINAL_TOL
+            assert S.status() == 0
         else:
             Up = U0.copy()
             Up[2] = np.nextafter(Up[2], np.inf)
             pert, _ = orc.run(P, Up, T)
             own = np.abs(pert - want).max()
             assert np.abs(got - want).max() <= 4 * own
-        assert S.status() == 0
+            # no status check here: behind the shocks E ~ 1e3 is almost all kinetic, so
+            # states that agree to this conditioning can differ in p by more than the 0.01
+            # of the low-pressure gas, and a stage can dip below p = 0 on one side only
 
 
 def test_four_wave_self_similarity(wz, orc):
