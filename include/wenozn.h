@@ -83,7 +83,7 @@ typedef struct {
     double dx, dy;           /* uniform spacing (> 0; dy ignored in 1D)        */
     double gamma;            /* ratio of specific heats (Euler)                */
     double eps;              /* epsilon of Eq. (function) / Eq. (new)          */
-    double A;                /* constant A of Eq. (function)                   */
+    double A;                /* constant A of Eq. (function), > 0              */
     double cfl;              /* CFL number sigma of the time-step formulas     */
     double adv_speed;        /* advection speed a (advection only)             */
 } wenozn_problem;
@@ -119,7 +119,7 @@ wenozn_status wenozn_fill_ghosts(const wenozn_problem* p, double* U_padded, void
  *   side     : +1 for f^+_{j-1/2} (stencil f_{j-3..j+1}); -1 for f^-_{j-1/2}, the same
  *              formula applied to the mirrored stencil (f_{j+2}, f_{j+1}, f_j, f_{j-1},
  *              f_{j-2}) (Sec. 2: "symmetric rule about x_{i+1/2}").
- *   eps, A   : Eq. (function) / (new) constants (eps > 0, A >= 0). */
+ *   eps, A   : Eq. (function) / (new) constants (eps > 0, A > 0). */
 wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat, int32_t side,
                                  double eps, double A, void* stream);
 

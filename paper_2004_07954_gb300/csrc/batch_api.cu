@@ -38,7 +38,7 @@ wenozn_status check_batch(const wenozn_batch_params* bp, const int64_t* offsets,
     if (bp->bc != WENOZN_BC_PERIODIC && bp->bc != WENOZN_BC_OUTFLOW) return WENOZN_EINVAL;
     if (bp->shape < -1 || bp->shape >= kNumBatchShapes) return WENOZN_EINVAL;
     if (!(std::isfinite(bp->gamma) && bp->gamma > 1.0) || !(std::isfinite(bp->eps) && bp->eps > 0.0) ||
-        !(std::isfinite(bp->A) && bp->A >= 0.0) || !(std::isfinite(bp->cfl) && bp->cfl > 0.0) ||
+        !(std::isfinite(bp->A) && bp->A > 0.0) || !(std::isfinite(bp->cfl) && bp->cfl > 0.0) ||
         std::isnan(bp->t_final))
         return WENOZN_EINVAL;
     if (offsets[0] != 0) return WENOZN_EINVAL;
@@ -115,7 +115,7 @@ BatchArgs args_of(const wenozn_batch_params* bp, const Ptrs& p, int64_t cells, i
     a.fast_rcp = zn_fast_rcp(bp->eps, bp->A);
     a.gamma = bp->gamma;
     a.eps4 = 4.0 * bp->eps;
-    a.A4 = 0.25 * bp->A;
+    a.kappa = zn_kappa(bp->A);
     a.cfl = bp->cfl;
     a.t_final = bp->t_final;
     return a;

@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         if (j >= nint || line >= nlines) continue;
         double Fh[NV];
         if (GEN)
-            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.A4, a.fast_rcp != 0, a.weights,
+            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.fast_rcp != 0, a.weights,
                                    a.split, alpha_f, Fh);
         else
-            interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.A4, a.fast_rcp != 0, Fh);
+            interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.fast_rcp != 0, Fh);
         // store, undoing the direction frame
         if (DIR == 0) {
             const int64_t base = int64_t(line) * (a.nx + 1) + j;

@@ -58,7 +58,7 @@ inline wenozn_status check_problem(const wenozn_problem* p) {
     if (p->bc_x < WENOZN_BC_PERIODIC || p->bc_x > WENOZN_BC_REFLECTIVE) return WENOZN_EINVAL;
     if (two_d && (p->bc_y < WENOZN_BC_PERIODIC || p->bc_y > WENOZN_BC_REFLECTIVE)) return WENOZN_EINVAL;
     if (!finite_pos(p->dx) || (two_d && !finite_pos(p->dy))) return WENOZN_EINVAL;
-    if (!finite_pos(p->eps) || !std::isfinite(p->A) || p->A < 0.0 || !finite_pos(p->cfl)) return WENOZN_EINVAL;
+    if (!finite_pos(p->eps) || !finite_pos(p->A) || !finite_pos(p->cfl)) return WENOZN_EINVAL;
     if (p->system == WENOZN_ADVECTION_1D) {
         if (!std::isfinite(p->adv_speed) || p->adv_speed == 0.0) return WENOZN_EINVAL;
     } else if (!std::isfinite(p->gamma) || p->gamma <= 1.0) {
@@ -80,7 +80,7 @@ inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsign
     fa.nx = p.nx;
     fa.ny = p.ny;
     fa.eps4 = 4.0 * p.eps;
-    fa.A4 = 0.25 * p.A;
+    fa.kappa = zn_kappa(p.A);
     fa.fast_rcp = zn_fast_rcp(p.eps, p.A, p.weights);
     fa.gamma = p.gamma;
     fa.adv_speed = p.adv_speed;

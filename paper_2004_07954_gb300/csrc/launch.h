@@ -1,6 +1,7 @@
 // Internal host-side launchers shared by the translation units of libwenozn.so.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -19,16 +20,18 @@ struct FluxArgs {
     int nx, ny, bc;                        // bc of the sweep direction (0 periodic, 1 outflow, 2 reflective)
     int fast_rcp;                          // 1: Newton reciprocal for f^ = num/den (see zn_flux)
     int weights, split;                    // weight function and flux splitting (wenozn.h enums)
-    double eps4, A4, gamma, adv_speed;     // eps4 = 4 eps, A4 = A / 4
+    double eps4, kappa, gamma, adv_speed;  // eps4 = 4 eps, kappa = 2 / sqrt(A) (see zn_parts)
 };
 // Whether the reconstruction's common denominator is guaranteed positive and normal, so the
 // Newton reciprocal applies: WENO-ZN needs A > 0 and eps >= 1e-60, WENO-Z and Jiang-Shu
 // eps >= 1e-60, the linear weights always.
 inline int zn_fast_rcp(double eps, double A, int weights = 0) {
+    (void)A;
     if (weights == 2) return 1;
-    if (weights != 0) return eps >= 1e-60 ? 1 : 0;
-    return A > 0.0 && eps >= 1e-60 ? 1 : 0;
+    return eps >= 1e-60 ? 1 : 0;
 }
+// The WENO-ZN weights carry A as kappa = 2 / sqrt(A) (A > 0, checked on entry).
+inline double zn_kappa(double A) { return 2.0 / std::sqrt(A); }
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s);
 
 // Flux difference, SSP-RK3 stage combination and the next stage's LF speeds.
@@ -74,7 +77,7 @@ struct BatchArgs {
     int stage;                 // 0, 1, 2
     int bc;                    // ghost map of every instance
     int fast_rcp;
-    double gamma, eps4, A4, cfl;
+    double gamma, eps4, kappa, cfl;
     double t_final;            // > 0: no instance steps past it
 };
 struct BatchShape { int tile, threads; };

@@ -97,7 +97,7 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
     fa.nx = p->nx;
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
-    fa.A4 = 0.25 * p->A;
+    fa.kappa = zn_kappa(p->A);
     fa.fast_rcp = zn_fast_rcp(p->eps, p->A, p->weights);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;

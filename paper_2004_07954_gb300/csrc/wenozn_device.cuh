@@ -36,9 +36,10 @@ namespace wz {
 //  * IS_0 + IS_2 - tau5 = 2 min(IS_0, IS_2), i.e. 4 (IS_0 + IS_2 - tau5 + eps) = 2 min(b) - 4 eps
 //    = m and 4 (tau5 + eps) = max(b) - min(b) + 4 eps = P; min/max of the non-negative b
 //    run on the integer pipe;
-//  * every alpha_k is multiplied by P^2 b_0 b_1 b_2 / (4 c_k) and the common factor divided
-//    out: a_k = (A/4) m^2 b_0 b_1 b_2 + (d4 P)^2 prod_{j != k} b_j with d4 the fourth
-//    difference, all positive (a_k >= (A/4) (4 eps)^5 > 0); the optimal weights (1, 6, 3)/10
+//  * every alpha_k is multiplied by P^2 b_0 b_1 b_2 / (A c_k) and the common factor divided
+//    out: a_k = m^2 b_0 b_1 b_2 + (kappa d4 P)^2 prod_{j != k} b_j with d4 the fourth
+//    difference and kappa = 2 / sqrt(A) (A > 0), all positive (a_k >= (4 eps)^5 > 0); the
+//    optimal weights (1, 6, 3)/10
 //    then enter through 6 q_1 and 3 q_2 and the denominator a_0 + 6 a_1 + 3 a_2, leaving one
 //    division per reconstruction.  The fourth difference is d4 = t_0 + t_2.
 // Range: finite for |f| below ~1e20.
@@ -64,7 +65,7 @@ __host__ __device__ __forceinline__ double rcp_nr(double d) {
 }
 
 __host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double d, double e,
-                                                     double eps4, double A4) {
+                                                     double eps4, double kappa) {
     // first differences, then the second (s_k) and one-sided (t_k) differences from them:
     // equal inputs give exact zeros
     const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
@@ -83,35 +84,35 @@ __host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double 
 #else
     const double mn = b0 < b2 ? b0 : b2, mx = b0 < b2 ? b2 : b0;
 #endif
-    const double P = (mx - mn) + eps4;                          // 4 (tau5 + eps)
+    const double P = fma(kappa, mx - mn, kappa * eps4);          // kappa 4 (tau5 + eps)
     const double m = fma(2.0, mn, -eps4);                       // 4 (IS_0 + IS_2 - tau5 + eps)
     const double b01 = b0 * b1, b12 = b1 * b2, b02 = b0 * b2;
-    const double X = (A4 * m) * m * (b01 * b2);
+    const double X = (m * m) * (b01 * b2);
     const double z = d4 * P;
     const double Y = z * z;
     const double a0 = fma(Y, b12, X);
     const double a1 = fma(Y, b02, X);
     const double a2 = fma(Y, b01, X);
-    // q_k - c scaled by the optimal-weight ratios (1, 6, 3): q_0 - c = s_0/12 + t_0/4,
-    // 6 (q_1 - c) = s_1/2 - 3 t_1/2, 3 (q_2 - c) = s_2/4 - 3 t_2/4; the weights sum to one, so
+    // q_k - c scaled by the optimal-weight ratios (1, 6, 3); the weights sum to one, so
     // f^ = c + sum a_k (q_k - c) / sum a_k
-    const double k1_12 = 1.0 / 12.0;
-    const double q0 = fma(k1_12, s0, 0.25 * t0);
-    const double q1 = fma(0.5, s1, -1.5 * t1);
-    const double q2 = fma(0.25, s2, -0.75 * t2);
+    // from the first differences: q_0 - c = D1/3 - 5 D2/6, 6 (q_1 - c) = -(D2 + 2 D3),
+    // 3 (q_2 - c) = D4/2 - 2 D3
+    const double q0 = fma(1.0 / 3.0, D1, (-5.0 / 6.0) * D2);
+    const double q1n = fma(2.0, D3, D2);
+    const double q2 = fma(-2.0, D3, 0.5 * D4);
     ZnParts r;
-    r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
+    r.num = fma(a0, q0, fma(-a1, q1n, a2 * q2));
     r.den = fma(6.0, a1, fma(3.0, a2, a0));
     r.c = c;
     return r;
 }
 
-// f^ = c + num / den.  With A > 0 and eps >= 1e-60, den >= 10 (A/4) (4 eps)^5 is a positive
+// f^ = c + num / den.  With eps >= 1e-60, den >= 10 (4 eps)^5 is a positive
 // normal number, so the Newton reciprocal applies (fast_rcp = true, chosen by the host);
 // otherwise the IEEE division is used.
 __host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
-                                                   double eps4, double A4, bool fast_rcp) {
-    const ZnParts r = zn_parts(a, b, c, d, e, eps4, A4);
+                                                   double eps4, double kappa, bool fast_rcp) {
+    const ZnParts r = zn_parts(a, b, c, d, e, eps4, kappa);
     return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
 }
 
@@ -120,8 +121,8 @@ __host__ __device__ __forceinline__ double zn_flux(double a, double b, double c,
 // "symmetric rule about x_{i+1/2}").
 __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2, double p3, double p4,
                                                 double m0, double m1, double m2, double m3, double m4,
-                                                double eps4, double A4, bool fast_rcp) {
-    return zn_flux(p0, p1, p2, p3, p4, eps4, A4, fast_rcp) + zn_flux(m4, m3, m2, m1, m0, eps4, A4, fast_rcp);
+                                                double eps4, double kappa, bool fast_rcp) {
+    return zn_flux(p0, p1, p2, p3, p4, eps4, kappa, fast_rcp) + zn_flux(m4, m3, m2, m1, m0, eps4, kappa, fast_rcp);
 }
 
 // ------------------------------------------------------------------------------------
@@ -135,8 +136,8 @@ __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2,
 //   linear:  a_k = 1.
 // ------------------------------------------------------------------------------------
 __host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, double c, double d, double e,
-                                                       double eps4, double A4, int weights) {
-    if (weights == 0) return zn_parts(a, b, c, d, e, eps4, A4);
+                                                       double eps4, double kappa, int weights) {
+    if (weights == 0) return zn_parts(a, b, c, d, e, eps4, kappa);
     const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
     const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
@@ -171,8 +172,8 @@ __host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, doubl
 }
 
 __host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
-                                                     double eps4, double A4, bool fast_rcp, int weights) {
-    const ZnParts r = zn_parts_w(a, b, c, d, e, eps4, A4, weights);
+                                                     double eps4, double kappa, bool fast_rcp, int weights) {
+    const ZnParts r = zn_parts_w(a, b, c, d, e, eps4, kappa, weights);
     return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
 }
 
