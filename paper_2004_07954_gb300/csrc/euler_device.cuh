@@ -175,6 +175,7 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
     const double b1 = gm1 * (rc * rc);                 // (gamma - 1) / c^2
     const double b2 = 0.5 * q2 * b1;
     const double hrc = 0.5 * rc;
+    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2;
     // Projection onto the left eigenvectors of the Roe state (rows, direction frame)
     //   l_{u-c} = ( (b2 + u/c)/2, -(b1 u + 1/c)/2, -b1 v/2, b1/2 )
     //   l_u     = ( 1 - b2, b1 u, b1 v, -b1 )
@@ -186,12 +187,12 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
     auto project = [&](const double* hs, int i, double* g) {
         const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
         const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
-        const double Z = fma(b2, h0, -(b1 * W));
-        const double B = hrc * fma(u, h0, -h1);
-        g[0] = fma(0.5, Z, B);
-        g[1] = h0 - Z;
+        const double Zh = fma(hb2, h0, -(hb1 * W));          // Z / 2
+        const double Bi = fma(u, h0, -h1);                   // 2 c B
+        g[0] = fma(hrc, Bi, Zh);
+        g[1] = fma(-2.0, Zh, h0);
         if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
-        g[NV - 1] = fma(0.5, Z, -B);
+        g[NV - 1] = fma(-hrc, Bi, Zh);
     };
     double gp[5][NV], gm[5][NV];
 #pragma unroll
@@ -255,16 +256,17 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
     const double b1 = gm1 * (rc * rc);
     const double b2 = 0.5 * q2 * b1;
     const double hrc = 0.5 * rc;
+    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2;
     // left eigenvectors through their shared parts, as in interface_flux
     auto project = [&](const double* hs, int i, double* g) {
         const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
         const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
-        const double Z = fma(b2, h0, -(b1 * W));
-        const double B = hrc * fma(u, h0, -h1);
-        g[0] = fma(0.5, Z, B);
-        g[1] = h0 - Z;
+        const double Zh = fma(hb2, h0, -(hb1 * W));          // Z / 2
+        const double Bi = fma(u, h0, -h1);                   // 2 c B
+        g[0] = fma(hrc, Bi, Zh);
+        g[1] = fma(-2.0, Zh, h0);
         if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
-        g[NV - 1] = fma(0.5, Z, -B);
+        g[NV - 1] = fma(-hrc, Bi, Zh);
     };
     double gp[5][NV], gm[5][NV];
     if (split == 0 || split == 3) {
