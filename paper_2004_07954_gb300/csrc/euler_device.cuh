@@ -53,14 +53,15 @@ __device__ __forceinline__ void split_cell(const double* Uc, double alpha, doubl
     const double rr = rs * rs;                         // 1 / rho
     const double un = mn * rr;
     const double ut = mt * rr;
-    const double kin = NV == 4 ? 0.5 * fma(mn, un, mt * ut) : 0.5 * (mn * un);
-    const double p = gm1 * (E - kin);
-    const double Ep = E + p;
+    // p/2 = (gamma-1)(E - (m_n u_n + m_t u_t)/2)/2
+    const double mq = NV == 4 ? fma(mn, un, mt * ut) : mn * un;
+    const double hp2 = fma(-0.25 * gm1, mq, (0.5 * gm1) * E);
+    const double Ep = fma(2.0, hp2, E);
     // half the physical flux, F/2 = (m_n, m_n u_n + p, m_t u_n, u_n (E + p)) / 2
     const double hun = 0.5 * un;
     double hF[NV];
     hF[0] = 0.5 * mn;
-    hF[1] = fma(mn, hun, 0.5 * p);
+    hF[1] = fma(mn, hun, hp2);
     if (NV == 4) hF[2] = mt * hun;
     hF[NV - 1] = hun * Ep;
 #pragma unroll
@@ -172,10 +173,10 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
     const double c2 = gm1 * fma(-0.5, q2, H);
     const double rc = rsqrt(c2);
     const double c = c2 * rc;
-    const double b1 = gm1 * (rc * rc);                 // (gamma - 1) / c^2
-    const double b2 = 0.5 * q2 * b1;
     const double hrc = 0.5 * rc;
-    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2;
+    const double hq2 = 0.5 * q2;
+    const double hb1 = (0.5 * gm1) * (rc * rc);        // b1 / 2, b1 = (gamma - 1) / c^2
+    const double hb2 = hq2 * hb1;                      // b2 / 2, b2 = q^2 b1 / 2
     // Projection onto the left eigenvectors of the Roe state (rows, direction frame)
     //   l_{u-c} = ( (b2 + u/c)/2, -(b1 u + 1/c)/2, -b1 v/2, b1/2 )
     //   l_u     = ( 1 - b2, b1 u, b1 v, -b1 )
@@ -213,13 +214,13 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
         const double d20 = gh[2] - gh[0];
         Fh[0] = gh[0] + gh[1] + gh[2];
         Fh[1] = fma(u, Fh[0], c * d20);
-        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, 0.5 * q2 * gh[1]));
+        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, hq2 * gh[1]));
     } else {
         const double d30 = gh[3] - gh[0];
         Fh[0] = gh[0] + gh[1] + gh[3];
         Fh[1] = fma(u, Fh[0], c * d30);
         Fh[2] = fma(v, Fh[0], gh[2]);
-        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(0.5 * q2, gh[1], v * gh[2])));
+        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(hq2, gh[1], v * gh[2])));
     }
 }
 
@@ -253,10 +254,10 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
     const double c2 = gm1 * fma(-0.5, q2, H);
     const double rc = rsqrt(c2);
     const double c = c2 * rc;
-    const double b1 = gm1 * (rc * rc);
-    const double b2 = 0.5 * q2 * b1;
     const double hrc = 0.5 * rc;
-    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2;
+    const double hq2 = 0.5 * q2;
+    const double hb1 = (0.5 * gm1) * (rc * rc);        // b1 / 2, b1 = (gamma - 1) / c^2
+    const double hb2 = hq2 * hb1;                      // b2 / 2, b2 = q^2 b1 / 2
     // left eigenvectors through their shared parts, as in interface_flux
     auto project = [&](const double* hs, int i, double* g) {
         const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
@@ -311,13 +312,13 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
         const double d20 = gh[2] - gh[0];
         Fh[0] = gh[0] + gh[1] + gh[2];
         Fh[1] = fma(u, Fh[0], c * d20);
-        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, 0.5 * q2 * gh[1]));
+        Fh[2] = fma(H, gh[0] + gh[2], fma(uc, d20, hq2 * gh[1]));
     } else {
         const double d30 = gh[3] - gh[0];
         Fh[0] = gh[0] + gh[1] + gh[3];
         Fh[1] = fma(u, Fh[0], c * d30);
         Fh[2] = fma(v, Fh[0], gh[2]);
-        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(0.5 * q2, gh[1], v * gh[2])));
+        Fh[3] = fma(H, gh[0] + gh[3], fma(uc, d30, fma(hq2, gh[1], v * gh[2])));
     }
 }
 
