@@ -191,6 +191,14 @@ wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const double* U, doubl
 wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, double t_remaining,
                               double* dt_out, void* ws, size_t ws_bytes, void* stream);
 
+/* nsteps SSP-RK3 steps of U in place, each with the fixed step dt > 0 or, for dt <= 0, its
+ * CFL step; the same results as nsteps calls of wenozn_rk3_step, bit for bit.  The LF speeds
+ * of each new state come from the last stage's update (which evaluates them anyway), so the
+ * sequence needs one reduction at the start and no memset; it does not synchronise and can
+ * be captured in a CUDA graph. */
+wenozn_status wenozn_rk3_run(const wenozn_problem* p, double* U, int64_t nsteps, double dt, void* ws,
+                             size_t ws_bytes, void* stream);
+
 /* One SSP-RK3 step with the fixed step dt > 0, out of place, keeping what its reverse
  * (wenozn_rk3_step_vjp_stages) needs:
  *   U       : device, [nvar][ny][nx], the state U^n (read only);
@@ -213,7 +221,7 @@ wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, 
 
 /* Synchronises `stream` and returns in *device_status the device status bits (as
  * wenozn_workspace_status reports them) raised in the control block that the most recent
- * stepping call on `stream` used (wenozn_rhs, wenozn_rhs_noalloc, wenozn_rk3_step,
+ * stepping call on `stream` used (wenozn_rhs, wenozn_rhs_noalloc, wenozn_rk3_step, wenozn_rk3_run,
  * wenozn_rk3_step_keep, wenozn_rhs_vjp, wenozn_rk3_step_vjp, wenozn_batch_rk3_step), then
  * clears them; 0 when nothing ran on the stream.  That workspace must still be allocated. */
 wenozn_status wenozn_last_error(void* stream, int32_t* device_status);

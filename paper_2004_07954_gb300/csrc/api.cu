@@ -205,6 +205,48 @@ wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, dou
     return WENOZN_OK;
 }
 
+wenozn_status wenozn_rk3_run(const wenozn_problem* p, double* U, int64_t nsteps, double dt, void* ws,
+                             size_t ws_bytes, void* stream) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!U || !ws || nsteps < 1 || std::isnan(dt) || std::isinf(dt)) return WENOZN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    const Layout lay = layout_of(*p);
+    if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    double* u1 = reinterpret_cast<double*>(ws_base(ws) + lay.u1);
+    double* u2 = reinterpret_cast<double*>(ws_base(ws) + lay.u2);
+    double* fx = reinterpret_cast<double*>(ws_base(ws) + lay.fx);
+    double* gy = reinterpret_cast<double*>(ws_base(ws) + lay.gy);
+    const bool euler = p->system != WENOZN_ADVECTION_1D;
+    note_status(stream, &ctrl->status);
+    // the speeds of U^n once; afterwards each step's last stage leaves those of U^{n+1} in
+    // slot 0.  Stage s reads slot s, accumulates slot s+1 (mod 3) and clears slot s+2.
+    cudaError_t e = clear_speeds(ctrl, s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p->system, U, int64_t(p->nx) * p->ny, p->gamma, p->adv_speed, ctrl->alpha[0],
+                                 &ctrl->status, s, field_slot(*p, ctrl, 0));
+    const double* stage_in[3] = {U, u1, u2};
+    double* stage_out[3] = {u1, u2, U};
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+            e = launch_fluxes(*p, stage_in[stage], ctrl->alpha[stage], &ctrl->alpha_f[stage][0][0], fx, gy, s);
+            if (e != cudaSuccess) break;
+            UpdateArgs u = update_args(*p, ctrl, fx, gy);
+            u.mode = stage + 1;
+            u.Us = stage_in[stage];
+            u.Un = U;
+            u.out = stage_out[stage];
+            u.next_slot = euler ? (stage + 1) % 3 : -1;
+            u.clear_slot = euler ? (stage + 2) % 3 : -1;
+            u.dt_fixed = dt;
+            e = launch_update(p->system, u, s);
+        }
+    }
+    return cuda_status(e);
+}
+
 wenozn_status wenozn_rk3_step_keep(const wenozn_problem* p, const double* U, double* U_next, double dt,
                                    double* U1, double* U2, double* alphas, void* ws, size_t ws_bytes,
                                    void* stream) {

@@ -114,6 +114,7 @@ inline UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double*
     u.rdy = p.system == WENOZN_EULER_2D ? 1.0 / p.dy : 0.0;
     u.ctrl = ctrl;
     u.next_slot = -1;
+    u.clear_slot = -1;
     u.field_speeds = p.split == WENOZN_SPLIT_LF_FIELD && p.system != WENOZN_ADVECTION_1D ? 1 : 0;
     u.cfl = p.cfl;
     u.dx = p.dx;

@@ -96,6 +96,11 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
         }
     }
     if (bad) atomicOr(&a.ctrl->status, kStatusNonFinite);
+    if (a.clear_slot >= 0 && blockIdx.x == 0 && threadIdx.x < 8) {
+        unsigned long long* z = threadIdx.x < 2 ? &a.ctrl->alpha[a.clear_slot][threadIdx.x]
+                                                : &a.ctrl->alpha_f[a.clear_slot][0][threadIdx.x - 2];
+        *z = 0ull;
+    }
     if (NV != 1 && a.next_slot >= 0) {
         block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
         if (a.field_speeds) block_max_n_atomic<6>(fmx, &a.ctrl->alpha_f[a.next_slot][0][0]);

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_run": [_P, _VP, ctypes.c_int64, ctypes.c_double, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_keep": [_P, _VP, _VP, ctypes.c_double, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp_stages": [_P, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_stages": [_VP, _P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -309,6 +310,12 @@ def wenozn_rk3_step_vjp(p: wenozn_problem, U: torch.Tensor, dt: float, lam: torc
                                                             _stream(stream)))
 
 
+def wenozn_rk3_run(p: wenozn_problem, U: torch.Tensor, nsteps: int, ws: torch.Tensor, dt: float = 0.0,
+                   stream=None) -> None:
+    _check("wenozn_rk3_run", lib().wenozn_rk3_run(ctypes.byref(p), _dev_ptr(U, "U"), int(nsteps), float(dt),
+                                                  _ws_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
 def wenozn_rk3_step_keep(p: wenozn_problem, U: torch.Tensor, U_next: torch.Tensor, dt: float, U1: torch.Tensor,
                          U2: torch.Tensor, alphas: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
     _check("wenozn_rk3_step_keep", lib().wenozn_rk3_step_keep(
@@ -354,6 +361,10 @@ class Solver:
 
     def step(self, U: torch.Tensor, dt: float = 0.0, t_remaining: float = 0.0, return_dt=False, stream=None):
         return wenozn_rk3_step(self.p, U, self.ws, dt, t_remaining, return_dt, stream)
+
+    def steps(self, U: torch.Tensor, n: int, dt: float = 0.0, stream=None) -> None:
+        """n RK3 steps in one asynchronous call (no clipping at a final time)."""
+        wenozn_rk3_run(self.p, U, n, self.ws, dt, stream)
 
     def run(self, U: torch.Tensor, T: float, dt: float = 0.0, stream=None) -> int:
         """Advance to time T (CFL steps clipped at T, or fixed steps); returns steps."""

@@ -186,6 +186,24 @@ def test_rk3_step_parity(wz, orc, system, nx, ny, bc):
     assert rel_linf(host(t), want) <= STEP_TOL
 
 
+@pytest.mark.parametrize("system,nx,ny,split", [(2, 70, 53, 0), (1, 777, 1, 0), (0, 300, 1, 0), (2, 40, 33, 1),
+                                                 (1, 500, 1, 1)])
+def test_rk3_run_equals_repeated_steps(wz, system, nx, ny, split):
+    """The chained steps (LF speeds of each new state from the last stage, rotating slots)
+    give the results of single steps bit for bit, with CFL and with fixed steps."""
+    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / max(ny, 1), split=split)
+    U0 = (inputs.euler2d_ic(nx, ny, 2) if system == 2 else
+          inputs.euler1d_ic(nx, 2) if system == 1 else inputs.advection_ic(nx, "sin"))
+    for dt in (0.0, 1e-4):
+        S = wz.Solver(p)
+        a, b = dev(U0), dev(U0)
+        for _ in range(7):
+            S.step(a, dt=dt)
+        S.steps(b, 7, dt=dt)
+        assert torch.equal(a, b)
+        assert S.status() == 0
+
+
 def test_rk3_fixed_and_clipped_dt(wz, orc):
     n = 300
     U = inputs.euler1d_ic(n, seed=2)
