@@ -18,7 +18,7 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     v.rdx = 1.0 / p.dx;
     v.gamma = p.gamma;
     v.eps4 = 4.0 * p.eps;
-    v.A4 = 0.25 * p.A;
+    v.kappa = zn_kappa(p.A);
     v.adv_speed = p.adv_speed;
     return v;
 }

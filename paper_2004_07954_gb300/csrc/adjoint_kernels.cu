@@ -19,11 +19,12 @@ namespace {
 
 // Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), writes dW/df * Wb to
 // fb[0..4] and returns W(f).
-__host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double A4, int fast,
+__host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double kappa, int fast,
                                                   double* fb) {
     const double a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
-    // first differences, then the second (s_k) and one-sided (t_k) differences from them:
-    // equal inputs give exact zeros
+    // the forward of zn_parts: first differences, second (s_k) and one-sided (t_k)
+    // differences, scaled indicators b_k, weights a_k = m^2 b0 b1 b2 + (kappa d4 P)^2 prod_{j!=k} b_j,
+    // W = c + N / D with the sub-stencil fluxes q_k - c from the first differences
     const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
     const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
@@ -42,60 +43,53 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
 #endif
     const double mn = i0 < i2 ? b0 : b2, mx = i0 < i2 ? b2 : b0;
     const double sg = i0 > i2 ? 1.0 : (i0 < i2 ? -1.0 : 0.0);
-    const double P = (mx - mn) + eps4;
+    const double P = fma(kappa, mx - mn, kappa * eps4);
     const double m = fma(2.0, mn, -eps4);
     const double b12 = b1 * b2, b02 = b0 * b2, b01 = b0 * b1, b012 = b01 * b2;
-    const double Am = A4 * m;
-    const double K = Am * m;
-    const double X = K * b012;
+    const double m2 = m * m;
+    const double X = m2 * b012;
     const double z = d4 * P;
     const double Y = z * z;
     const double a0 = fma(Y, b12, X), a1 = fma(Y, b02, X), a2 = fma(Y, b01, X);
-    const double c3 = fma(2.0, c, c), c6 = fma(5.0, c, c);
-    const double q0 = fma(1.0 / 12.0, s0, fma(0.25, t0, c));
-    const double q1 = fma(0.5, s1, fma(-1.5, t1, c6));
-    const double q2 = fma(0.25, s2, fma(-0.75, t2, c3));
-    const double N = fma(a0, q0, fma(a1, q1, a2 * q2));
+    const double q0 = fma(1.0 / 3.0, D1, (-5.0 / 6.0) * D2);      // q_0 - c
+    const double q1n = fma(2.0, D3, D2);                             // -6 (q_1 - c)
+    const double q2 = fma(-2.0, D3, 0.5 * D4);                       // 3 (q_2 - c)
+    const double N = fma(a0, q0, fma(-a1, q1n, a2 * q2));
     const double D = fma(6.0, a1, fma(3.0, a2, a0));
     const double rD = fast ? rcp_nr(D) : 1.0 / D;
-    const double W = N * rD;
+    const double R = N * rD;
     // reverse
-    const double Nb = Wb * rD, Db = -Nb * W;
-    const double a0b = fma(Nb, q0, Db), a1b = fma(Nb, q1, 6.0 * Db), a2b = fma(Nb, q2, 3.0 * Db);
-    const double q0b = Nb * a0, q1b = Nb * a1, q2b = Nb * a2;
+    const double Nb = Wb * rD, Db = -Nb * R;
+    const double a0b = fma(Nb, q0, Db), a1b = fma(-Nb, q1n, 6.0 * Db), a2b = fma(Nb, q2, 3.0 * Db);
+    const double q0b = Nb * a0, q1nb = -Nb * a1, q2b = Nb * a2;
     const double Xb = (a0b + a1b) + a2b;
     const double Yb = fma(a0b, b12, fma(a1b, b02, a2b * b01));
-    const double XK = Xb * K;
+    const double XK = Xb * m2;                       // X = m^2 b0 b1 b2
     double b0b = fma(Y, fma(a1b, b2, a2b * b1), XK * b12);
     const double b1b = fma(Y, fma(a0b, b2, a2b * b0), XK * b02);
     double b2b = fma(Y, fma(a0b, b1, a1b * b0), XK * b01);
-    const double mb = (Xb * b012) * (Am + Am);      // X = A4 m^2 b0 b1 b2
+    const double mb = (Xb * b012) * (m + m);
     const double zb = (z + z) * Yb;
     const double d4b = zb * P, Pb = zb * d4;
-    // P = tau + eps4, m = b0 + b2 - tau - eps4, tau = |b0 - b2|
-    const double taub = Pb - mb;
+    // P = kappa (tau + eps4), m = b0 + b2 - tau - eps4, tau = |b0 - b2|
+    const double taub = fma(kappa, Pb, -mb);
     b0b = fma(sg, taub, b0b + mb);
     b2b = fma(-sg, taub, b2b + mb);
-    // b_k = (13/3) s_k^2 + t_k^2 + eps4; q_k; d4 = t0 + t2
-    const double s0b = fma(1.0 / 12.0, q0b, (b0b + b0b) * ks0);
-    const double s1b = fma(0.5, q1b, (b1b + b1b) * ks1);
-    const double s2b = fma(0.25, q2b, (b2b + b2b) * ks2);
-    const double t0b = fma(0.25, q0b, fma(b0b + b0b, t0, d4b));
-    const double t1b = fma(-1.5, q1b, (b1b + b1b) * t1);
-    const double t2b = fma(-0.75, q2b, fma(b2b + b2b, t2, d4b));
-    const double cb = fma(3.0, q2b, fma(6.0, q1b, q0b));
+    // b_k = (13/3) s_k^2 + t_k^2 + eps4; d4 = t0 + t2
+    const double s0b = (b0b + b0b) * ks0, s1b = (b1b + b1b) * ks1, s2b = (b2b + b2b) * ks2;
+    const double t0b = fma(b0b + b0b, t0, d4b), t1b = (b1b + b1b) * t1, t2b = fma(b2b + b2b, t2, d4b);
     // back through the differences: s_k = D_{k+1} - D_{k+2}, t0 = D1 - 3 D2, t1 = D2 + D3,
-    // t2 = 3 D3 - D4, D_k = f_{k-1} - f_k
-    const double D1b = s0b + t0b;
-    const double D2b = fma(-3.0, t0b, (s1b - s0b) + t1b);
-    const double D3b = fma(3.0, t2b, (s2b - s1b) + t1b);
-    const double D4b = -(s2b + t2b);
+    // t2 = 3 D3 - D4, the q's above, D_k = f_{k-1} - f_k; W depends on c also directly
+    const double D1b = fma(1.0 / 3.0, q0b, s0b + t0b);
+    const double D2b = fma(-5.0 / 6.0, q0b, fma(-3.0, t0b, (s1b - s0b) + t1b) + q1nb);
+    const double D3b = fma(2.0, q1nb, fma(-2.0, q2b, fma(3.0, t2b, (s2b - s1b) + t1b)));
+    const double D4b = fma(0.5, q2b, -(s2b + t2b));
     fb[0] = D1b;
     fb[1] = D2b - D1b;
-    fb[2] = (D3b - D2b) + cb;
+    fb[2] = (D3b - D2b) + Wb;
     fb[3] = D4b - D3b;
     fb[4] = -D4b;
-    return W;
+    return c + R;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -206,8 +200,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
             fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
         }
-        const double gh = zn_vjp(fp, ghb, a.eps4, a.A4, a.fast_rcp, fpb) +
-                          zn_vjp(fm, ghb, a.eps4, a.A4, a.fast_rcp, fmb);
+        const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, a.fast_rcp, fpb) +
+                          zn_vjp(fm, ghb, a.eps4, a.kappa, a.fast_rcp, fmb);
         double Lb[3] = {0, 0, 0};
         const double Lk[3] = {L0, L1, L2};
 #pragma unroll
@@ -313,8 +307,8 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
         fp[s] = hp[i + s];
         fm[4 - s] = hm[i + s + 1];
     }
-    zn_vjp(fp, Fb, a.eps4, a.A4, a.fast_rcp, fpb);
-    zn_vjp(fm, Fb, a.eps4, a.A4, a.fast_rcp, fmb);
+    zn_vjp(fp, Fb, a.eps4, a.kappa, a.fast_rcp, fpb);
+    zn_vjp(fm, Fb, a.eps4, a.kappa, a.fast_rcp, fmb);
     for (int s = 0; s < 6; ++s) {
         const double hpb = s <= 4 ? fpb[s] : 0.0, hmb = s >= 1 ? fmb[5 - s] : 0.0;
         a.C[(2 * s) * P + j] = 0.5 * (hpb + hmb);

@@ -102,7 +102,7 @@ struct VjpArgs {
     const double* X3;
     double c1, c2, c3, d;
     int n, bc, fast_rcp, nblocks;          // nblocks = vjp_partial_count(n)
-    double rdx, gamma, eps4, A4, adv_speed;
+    double rdx, gamma, eps4, kappa, adv_speed;
 };
 int vjp_partial_count(int n);
 size_t vjp_contrib_doubles(int nv, int n);
