@@ -262,6 +262,24 @@ wenozn_status wenozn_rk3_step_vjp_stages(const wenozn_problem* p, const double* 
                                          const double* U2, const double* alphas, double dt, double* lam,
                                          void* ws, size_t ws_bytes, void* stream);
 
+/* A segment of nsteps fixed steps dt > 0 that keeps what its reverse needs, in one call:
+ *   X      : device, [nsteps+1][nvar][nx]; X[0] holds U^0 on entry, X[k] receives U^k;
+ *   S1, S2 : device, [nsteps][nvar][nx], the stage inputs U^(1), U^(2) of every step;
+ *   alphas : device, 3 nsteps + 1 doubles: alphas[3k+s] the LF speed of the stage-s input of
+ *            step k, alphas[3 nsteps] that of U^nsteps (accumulated in place, no reduction
+ *            kernel per step).
+ * Results equal those of nsteps calls of wenozn_rk3_step_keep bit for bit.  1D systems,
+ * default scheme (as the adjoint); ws is a wenozn_vjp_workspace_size workspace. */
+wenozn_status wenozn_rk3_run_keep(const wenozn_problem* p, double* X, double* S1, double* S2, double* alphas,
+                                  int64_t nsteps, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/* The reverse of that segment: lam (device, [nvar][nx]) holds the cotangent of U^nsteps on
+ * entry and that of U^0 on exit; the nsteps reverse steps of wenozn_rk3_step_vjp_stages run
+ * from the last to the first in one call. */
+wenozn_status wenozn_rk3_vjp_run(const wenozn_problem* p, const double* X, const double* S1, const double* S2,
+                                 const double* alphas, int64_t nsteps, double dt, double* lam, void* ws,
+                                 size_t ws_bytes, void* stream);
+
 /* Device addresses, inside the workspace, of the stage inputs U^(1), U^(2) of the last
  * wenozn_rk3_step on it and of its LF speeds (3 doubles with a stride of 2: U^n, U^(1),
  * U^(2) at alphas[0], alphas[2], alphas[4]).  Valid until the next call on the workspace. */

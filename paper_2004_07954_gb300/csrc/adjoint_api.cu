@@ -166,4 +166,58 @@ wenozn_status wenozn_workspace_stages(void* ws, const wenozn_problem* p, const d
     return WENOZN_OK;
 }
 
+wenozn_status wenozn_rk3_run_keep(const wenozn_problem* p, double* X, double* S1, double* S2, double* alphas,
+                                  int64_t nsteps, double dt, void* ws, size_t ws_bytes, void* stream) {
+    Layout L;
+    wenozn_status st = check_vjp(p, ws, ws_bytes, &L);
+    if (st != WENOZN_OK) return st;
+    if (!X || !S1 || !S2 || !alphas || nsteps < 1 || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + L.ctrl);
+    double* fx = reinterpret_cast<double*>(ws_base(ws) + L.fx);
+    const int64_t ns = int64_t(nvar_of(p->system)) * p->nx;          // one state
+    unsigned long long* A = reinterpret_cast<unsigned long long*>(alphas);
+    note_status(stream, &ctrl->status);
+    // every speed accumulates into its own zeroed entry: A[k][s] for the stage-s input of step k
+    cudaError_t e = cudaMemsetAsync(alphas, 0, size_t(3 * nsteps + 1) * sizeof(double), s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p->system, X, p->nx, p->gamma, p->adv_speed, A, &ctrl->status, s);
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        double* Xk = X + k * ns;
+        const double* in[3] = {Xk, S1 + k * ns, S2 + k * ns};
+        double* out[3] = {S1 + k * ns, S2 + k * ns, Xk + ns};
+        for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+            e = launch_fluxes(*p, in[stage], A + 3 * k + stage, nullptr, fx, nullptr, s);
+            if (e != cudaSuccess) break;
+            UpdateArgs u = update_args(*p, ctrl, fx, nullptr);
+            u.mode = stage + 1;
+            u.Us = in[stage];
+            u.Un = Xk;
+            u.out = out[stage];
+            u.alpha_next = p->system != WENOZN_ADVECTION_1D ? A + 3 * k + stage + 1 : nullptr;
+            u.dt_fixed = dt;
+            e = launch_update(p->system, u, s);
+        }
+    }
+    return cuda_status(e);
+}
+
+wenozn_status wenozn_rk3_vjp_run(const wenozn_problem* p, const double* X, const double* S1, const double* S2,
+                                 const double* alphas, int64_t nsteps, double dt, double* lam, void* ws,
+                                 size_t ws_bytes, void* stream) {
+    Layout L;
+    wenozn_status st = check_vjp(p, ws, ws_bytes, &L);
+    if (st != WENOZN_OK) return st;
+    if (!X || !S1 || !S2 || !alphas || !lam || nsteps < 1 || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
+    const int64_t ns = int64_t(nvar_of(p->system)) * p->nx;
+    const unsigned long long* A = reinterpret_cast<const unsigned long long*>(alphas);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int64_t k = nsteps - 1; k >= 0; --k) {
+        st = reverse_stages(*p, L, ws, X + k * ns, S1 + k * ns, S2 + k * ns, A + 3 * k, A + 3 * k + 1,
+                            A + 3 * k + 2, dt, lam, s);
+        if (st != WENOZN_OK) return st;
+    }
+    return WENOZN_OK;
+}
+
 }  // extern "C"

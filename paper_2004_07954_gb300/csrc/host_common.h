@@ -115,6 +115,7 @@ inline UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double*
     u.ctrl = ctrl;
     u.next_slot = -1;
     u.clear_slot = -1;
+    u.alpha_next = nullptr;
     u.field_speeds = p.split == WENOZN_SPLIT_LF_FIELD && p.system != WENOZN_ADVECTION_1D ? 1 : 0;
     u.cfl = p.cfl;
     u.dx = p.dx;

@@ -48,6 +48,7 @@ struct UpdateArgs {
     int next_slot;       // alpha slot to accumulate the output's LF speeds into, or -1
     int field_speeds;    // also accumulate the per-field speeds (per-field LF splitting)
     int clear_slot;      // alpha slot to zero (a later stage accumulates into it), or -1
+    unsigned long long* alpha_next;   // if set: accumulate the output's LF speed here instead of a slot
     double dt_fixed, t_remaining, cfl, dx, dy, gamma, adv_speed;
 };
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s);

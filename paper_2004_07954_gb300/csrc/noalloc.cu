@@ -125,6 +125,7 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
         u.ctrl = ctrl;
         u.next_slot = -1;
         u.clear_slot = -1;
+        u.alpha_next = nullptr;
         u.field_speeds = 0;
         u.gamma = p->gamma;
         u.adv_speed = p->adv_speed;

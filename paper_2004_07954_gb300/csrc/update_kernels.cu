@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
         if (a.mode != 0) {
             if (NV == 1) {
                 bad |= !isfinite(o[0]);
-            } else if (a.next_slot >= 0 || a.mode == 3) {
+            } else if (a.next_slot >= 0 || a.alpha_next || a.mode == 3) {
                 double u, v, c;
                 const bool adm = wave_state<NV>(o, a.gamma, u, v, c);
                 const double vx = __dadd_rn(fabs(u), c), vy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
                                                 : &a.ctrl->alpha_f[a.clear_slot][0][threadIdx.x - 2];
         *z = 0ull;
     }
-    if (NV != 1 && a.next_slot >= 0) {
+    if (NV != 1 && a.alpha_next) {
+        block_max2_atomic(mx, my, a.alpha_next, NV != 4);
+    } else if (NV != 1 && a.next_slot >= 0) {
         block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
         if (a.field_speeds) block_max_n_atomic<6>(fmx, &a.ctrl->alpha_f[a.next_slot][0][0]);
     }

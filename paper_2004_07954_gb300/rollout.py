@@ -2,16 +2,15 @@
 
 `rollout(U0, p, dt, steps)` advances U0 by `steps` RK3 steps of the fixed size dt with the
 library's forward kernels and is differentiable with respect to U0: its backward pass runs
-the hand-written adjoint kernels (wenozn_rk3_step_vjp) step by step in reverse.  Forward
+the hand-written adjoint kernels (wenozn_rk3_vjp_run) over the steps in reverse.  Forward
 states are kept every `checkpoint_every` steps; the backward pass recomputes the states of
-one segment from its checkpoint (with its stage inputs) and walks it backwards, so memory
-holds steps/checkpoint_every + 3 checkpoint_every states; checkpoint_every = 1 keeps every
-step's three stage inputs and LF speeds and recomputes nothing.  The time step is an input, not a function of U0 (the adjoint's
+one segment from its checkpoint (with its stage inputs, one library call) and walks it
+backwards (one call), so memory holds steps/checkpoint_every + 3 checkpoint_every states;
+checkpoint_every = 1 keeps every step's three stage inputs and LF speeds and recomputes
+nothing.  The time step is an input, not a function of U0 (the adjoint's
 convention); choose it from the initial state, e.g. with `cfl_step`.
 """
 from __future__ import annotations
-
-import math
 
 import torch
 
@@ -21,51 +20,45 @@ from . import wenozn as W
 class WenoZNRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U0, p, dt, steps, checkpoint_every, ws):
-        U = U0.detach().clone().contiguous()
         every = max(1, int(checkpoint_every))
         ctx.p, ctx.dt, ctx.steps, ctx.every, ctx.ws = p, dt, steps, every, ws
         if every == 1:
             # keep every step's stage inputs and LF speeds: the reverse pass recomputes nothing
-            ctx.stages = _run_keep_stages(p, ws, U, dt, steps)
-        else:
-            checkpoints = [U.clone()]
-            for k in range(steps):
-                W.wenozn_rk3_step(p, U, ws, dt=dt)
-                if (k + 1) % every == 0 and k + 1 < steps:
-                    checkpoints.append(U.clone())
-            ctx.checkpoints = checkpoints
+            ctx.keep = _segment_keep(p, ws, U0.detach().contiguous(), dt, steps)
+            return ctx.keep[0][steps].clone()
+        U = U0.detach().clone().contiguous()
+        checkpoints = []
+        for k0 in range(0, steps, every):
+            checkpoints.append(U.clone())
+            W.wenozn_rk3_run(p, U, min(every, steps - k0), ws, dt)
+        ctx.checkpoints = checkpoints
         return U
 
     @staticmethod
     def backward(ctx, gU):
         lam = gU.detach().clone().contiguous()
-        p, dt, ws, every = ctx.p, ctx.dt, ctx.ws, ctx.every
+        p, dt, ws, every, steps = ctx.p, ctx.dt, ctx.ws, ctx.every, ctx.steps
         if every == 1:
-            S0, S1, S2, A = ctx.stages
-            for k in reversed(range(ctx.steps)):
-                W.wenozn_rk3_step_vjp_stages(p, S0[k], S1[k], S2[k], A[k], dt, lam, ws)
+            X, S1, S2, A = ctx.keep
+            W.wenozn_rk3_vjp_run(p, X, S1, S2, A, steps, dt, lam, ws)
             return lam, None, None, None, None, None
-        nseg = math.ceil(ctx.steps / every)
-        for seg in reversed(range(nseg)):
-            k0, k1 = seg * every, min(ctx.steps, (seg + 1) * every)
-            U = ctx.checkpoints[seg].clone()
-            S0, S1, S2, A = _run_keep_stages(p, ws, U, dt, k1 - k0)
-            for k in reversed(range(k1 - k0)):
-                W.wenozn_rk3_step_vjp_stages(p, S0[k], S1[k], S2[k], A[k], dt, lam, ws)
+        for seg in reversed(range(len(ctx.checkpoints))):
+            m = min(every, steps - seg * every)
+            X, S1, S2, A = _segment_keep(p, ws, ctx.checkpoints[seg], dt, m)
+            W.wenozn_rk3_vjp_run(p, X, S1, S2, A, m, dt, lam, ws)
         return lam, None, None, None, None, None
 
 
-def _run_keep_stages(p, ws, U, dt, steps):
-    """Advances U in place by `steps` steps, returning every step's stage inputs
-    (U^n, U^(1), U^(2)) and LF speeds, written there by the out-of-place step."""
+def _segment_keep(p, ws, U, dt, steps):
+    """`steps` steps from U (unchanged) in one call, keeping every state X[0..steps], the
+    stage inputs S1, S2 of every step and the LF speeds of every stage input."""
     X = torch.empty((steps + 1,) + tuple(U.shape), dtype=U.dtype, device=U.device)
-    S1, S2 = torch.empty_like(X[:steps]), torch.empty_like(X[:steps])
-    A = torch.empty((steps, 3), dtype=U.dtype, device=U.device)
+    S1 = torch.empty((steps,) + tuple(U.shape), dtype=U.dtype, device=U.device)
+    S2 = torch.empty_like(S1)
+    A = torch.empty(3 * steps + 1, dtype=U.dtype, device=U.device)
     X[0].copy_(U)
-    for k in range(steps):
-        W.wenozn_rk3_step_keep(p, X[k], X[k + 1], dt, S1[k], S2[k], A[k], ws)
-    U.copy_(X[steps])
-    return X[:steps], S1, S2, A
+    W.wenozn_rk3_run_keep(p, X, S1, S2, A, steps, dt, ws)
+    return X, S1, S2, A
 
 
 def rollout(U0: torch.Tensor, p: W.wenozn_problem, dt: float, steps: int, checkpoint_every: int = 1,

@@ -79,6 +79,8 @@ _SIGNATURES = {
     "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_run": [_P, _VP, ctypes.c_int64, ctypes.c_double, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_keep": [_P, _VP, _VP, ctypes.c_double, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_run_keep": [_P, _VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_double, _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_vjp_run": [_P, _VP, _VP, _VP, _VP, ctypes.c_int64, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp_stages": [_P, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_stages": [_VP, _P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                 ctypes.POINTER(ctypes.c_void_p)],
@@ -321,6 +323,22 @@ def wenozn_rk3_step_keep(p: wenozn_problem, U: torch.Tensor, U_next: torch.Tenso
     _check("wenozn_rk3_step_keep", lib().wenozn_rk3_step_keep(
         ctypes.byref(p), _dev_ptr(U, "U"), _dev_ptr(U_next, "U_next"), float(dt), _dev_ptr(U1, "U1"),
         _dev_ptr(U2, "U2"), _dev_ptr(alphas, "alphas"), _ws_ptr(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
+
+
+def wenozn_rk3_run_keep(p: wenozn_problem, X: torch.Tensor, S1: torch.Tensor, S2: torch.Tensor,
+                        alphas: torch.Tensor, nsteps: int, dt: float, ws: torch.Tensor, stream=None) -> None:
+    _check("wenozn_rk3_run_keep", lib().wenozn_rk3_run_keep(
+        ctypes.byref(p), _dev_ptr(X, "X"), _dev_ptr(S1, "S1"), _dev_ptr(S2, "S2"), _dev_ptr(alphas, "alphas"),
+        int(nsteps), float(dt), _ws_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def wenozn_rk3_vjp_run(p: wenozn_problem, X: torch.Tensor, S1: torch.Tensor, S2: torch.Tensor,
+                       alphas: torch.Tensor, nsteps: int, dt: float, lam: torch.Tensor, ws: torch.Tensor,
+                       stream=None) -> None:
+    _check("wenozn_rk3_vjp_run", lib().wenozn_rk3_vjp_run(
+        ctypes.byref(p), _dev_ptr(X, "X"), _dev_ptr(S1, "S1"), _dev_ptr(S2, "S2"), _dev_ptr(alphas, "alphas"),
+        int(nsteps), float(dt), _dev_ptr(lam, "lam"), _ws_ptr(ws), ws.numel() * ws.element_size(),
         _stream(stream)))
 
 

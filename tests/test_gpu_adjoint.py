@@ -134,6 +134,37 @@ def test_rk3_step_keep_matches_in_place_step(wz, system, bc):
         wz.wenozn_rk3_step_keep(p, U, U, dt, S1, S2, A, ws)
 
 
+def test_chained_keep_and_reverse_equal_the_single_steps(wz):
+    """wenozn_rk3_run_keep / wenozn_rk3_vjp_run against wenozn_rk3_step_keep /
+    wenozn_rk3_step_vjp_stages step by step, bit for bit."""
+    n, m = 640, 9
+    p = wz.wenozn_problem_init(1, n, 1, 10.0 / n, 1.0, bc_x=0)
+    U0 = dev(inputs.adjoint_ic(n, seed=16))
+    dt = 0.3 * p.dx
+    ws = wz.vjp_workspace(p)
+    X = torch.empty((m + 1,) + tuple(U0.shape), dtype=torch.float64, device="cuda")
+    S1, S2 = torch.empty_like(X[:m]), torch.empty_like(X[:m])
+    A = torch.empty(3 * m + 1, dtype=torch.float64, device="cuda")
+    X[0].copy_(U0)
+    wz.wenozn_rk3_run_keep(p, X, S1, S2, A, m, dt, ws)
+    U = U0.clone()
+    T1, T2 = torch.empty_like(U), torch.empty_like(U)
+    Ak = torch.empty(3, dtype=torch.float64, device="cuda")
+    for k in range(m):
+        Un = torch.empty_like(U)
+        wz.wenozn_rk3_step_keep(p, U, Un, dt, T1, T2, Ak, ws)
+        assert torch.equal(X[k], U) and torch.equal(S1[k], T1) and torch.equal(S2[k], T2)
+        assert torch.equal(A[3 * k:3 * k + 3], Ak)
+        U = Un
+    assert torch.equal(X[m], U)
+    lam0 = dev(np.random.default_rng(8).normal(size=tuple(U0.shape)))
+    l1, l2 = lam0.clone(), lam0.clone()
+    wz.wenozn_rk3_vjp_run(p, X, S1, S2, A, m, dt, l1, ws)
+    for k in reversed(range(m)):
+        wz.wenozn_rk3_step_vjp_stages(p, X[k], S1[k], S2[k], A[3 * k:3 * k + 3], dt, l2, ws)
+    assert torch.equal(l1, l2)
+
+
 def _loss_grad(wz, p, U0, dt, steps, target, every=1):
     from paper_2004_07954_gb300.rollout import rollout
     U = dev(U0).requires_grad_(True)
