@@ -41,11 +41,12 @@ wenozn_status check_vjp(const wenozn_problem* p, void* ws, size_t ws_bytes, Layo
 wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws, const double* U0,
                              const double* U1, const double* U2, const unsigned long long* a0,
                              const unsigned long long* a1, const unsigned long long* a2, double dt,
-                             double* lam, cudaStream_t s) {
+                             double* lam, cudaStream_t s, bool clear_ctl = true) {
     double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
     double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
     VjpArgs v = vjp_args(p, L, ws);
-    cudaError_t e = cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s);
+    // the control word is zero after every gather; clear it before a sequence starts
+    cudaError_t e = clear_ctl ? cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s) : cudaSuccess;
     if (e != cudaSuccess) return WENOZN_ECUDA;
     // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
     v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
@@ -214,7 +215,7 @@ wenozn_status wenozn_rk3_vjp_run(const wenozn_problem* p, const double* X, const
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int64_t k = nsteps - 1; k >= 0; --k) {
         st = reverse_stages(*p, L, ws, X + k * ns, S1 + k * ns, S2 + k * ns, A + 3 * k, A + 3 * k + 1,
-                            A + 3 * k + 2, dt, lam, s);
+                            A + 3 * k + 2, dt, lam, s, k == nsteps - 1);
         if (st != WENOZN_OK) return st;
     }
     return WENOZN_OK;

@@ -11,6 +11,8 @@
 // order and applies the cell's own derivatives once, so the result is deterministic.  alpha
 // is differentiated through its argmax cell (the lowest index on ties); d|x|/dx is taken as
 // 0 at x = 0.
+#include <atomic>
+
 #include "launch.h"
 
 namespace wz {
@@ -125,6 +127,7 @@ struct EulerSmem {
 
 __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
     __shared__ EulerSmem sm;
+    pdl_wait();
     const int n = a.n, j0 = blockIdx.x * kTI, tid = threadIdx.x;
     const int64_t P = int64_t(n) + 1;
     const double gm1 = a.gamma - 1.0;
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
 
 __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
     __shared__ double hp[kCells], hm[kCells];
+    pdl_wait();
     const int n = a.n, j0 = blockIdx.x * kTI, i = threadIdx.x, j = j0 + i;
     const int64_t P = int64_t(n) + 1;
     const double alpha = fabs(a.adv_speed);
@@ -325,6 +329,7 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
 template <int NV>
 __global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
     constexpr int Q = 2 * NV;
+    pdl_wait();
     const int n = a.n;
     const int64_t P = int64_t(n) + 1;
     const int i = blockIdx.x * kGather + threadIdx.x;
@@ -434,20 +439,55 @@ __global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
 
 }  // namespace
 
+// The Euler interface kernel is FP64-bound and as fast as its busiest SM: the block
+// scheduler balances it over empty SMs (at most two blocks per SM at the sizes where it
+// matters), but launched early beside the previous gather its blocks would pile up on the
+// SMs the gather leaves free.  An unused dynamic shared-memory reservation caps it at two
+// blocks per SM, so the early (programmatic) launch keeps the balanced placement.  The
+// reservation is sized per device, once.
+static cudaError_t euler_interface_pad(size_t* pad) {
+    static std::atomic<unsigned long long> configured{0};
+    static size_t pads[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        int per_sm = 0, reserved = 0;
+        e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess) return e;
+        const long budget = long(per_sm) / 2 - long(reserved) - long(sizeof(EulerSmem)) - 1024;
+        size_t pd = budget > 0 ? size_t(budget) : 0;
+        if (pd > 0) {
+            e = cudaFuncSetAttribute(vjp_interface_euler, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pd));
+            if (e != cudaSuccess) return e;
+        }
+        pads[dev & 63] = pd;
+        configured.fetch_or(bit);
+    }
+    *pad = pads[dev & 63];
+    return cudaSuccess;
+}
+
 int vjp_partial_count(int n) { return (n + 1 + kTI - 1) / kTI; }
 
 size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12 : 42); }
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
     const unsigned gi = unsigned(vjp_partial_count(a.n)), gc = unsigned((a.n + kGather - 1) / kGather);
+    cudaError_t e;
     if (system == 0) {
-        vjp_interface_advection<<<gi, kTI, 0, s>>>(a);
-        vjp_gather_kernel<1><<<gc, kGather, 0, s>>>(a);
+        e = launch_pdl(vjp_interface_advection, dim3(gi), dim3(kTI), 0, s, a);
     } else {
-        vjp_interface_euler<<<gi, 3 * kTI, 0, s>>>(a);
-        vjp_gather_kernel<3><<<gc, kGather, 0, s>>>(a);
+        size_t pad = 0;
+        e = euler_interface_pad(&pad);
+        if (e == cudaSuccess) e = launch_pdl(vjp_interface_euler, dim3(gi), dim3(3 * kTI), pad, s, a);
     }
-    return cudaGetLastError();
+    if (e == cudaSuccess)
+        e = system == 0 ? launch_pdl(vjp_gather_kernel<1>, dim3(gc), dim3(kGather), 0, s, a)
+                        : launch_pdl(vjp_gather_kernel<3>, dim3(gc), dim3(kGather), 0, s, a);
+    return e;
 }
 
 }  // namespace wz

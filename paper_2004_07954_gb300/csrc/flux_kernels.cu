@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     constexpr int NC = CL * TA;           // cells per tile
     extern __shared__ double smem[];
     const CellPlanes<NV> sp(smem, NC);
+    pdl_wait();
 
     const int n = DIR == 0 ? a.nx : a.ny;           // cells along the sweep
     const int nlines = DIR == 0 ? a.ny : a.nx;
@@ -130,8 +131,7 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     const unsigned along = unsigned((n + 1 + TI - 1) / TI);
     const unsigned across = unsigned((nlines + TA - 1) / TA);
     dim3 grid = DIR == 0 ? dim3(along, across) : dim3(across, along);
-    flux_kernel<NV, DIR, SMALL, GEN><<<grid, Tile<NV, DIR, SMALL>::THREADS, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(flux_kernel<NV, DIR, SMALL, GEN>, grid, dim3(Tile<NV, DIR, SMALL>::THREADS), smem, s, a);
 }
 
 int sm_count_cached() {

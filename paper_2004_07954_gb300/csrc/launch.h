@@ -9,6 +9,25 @@
 
 namespace wz {
 
+// Launches a kernel that begins with pdl_wait() with programmatic stream serialization
+// allowed, so that it can be scheduled while the previous kernel in the stream finishes
+// (a memset or copy before it is waited for as usual).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Numerical fluxes at every interface of one sweep direction.
 //   dir 0 (x): Fout[nv][ny][nx+1], Fout[.][j][i] at x_{i-1/2} of row j.
 //   dir 1 (y): Fout[nv][ny+1][nx], Fout[.][j][i] at y_{j-1/2} of column i.

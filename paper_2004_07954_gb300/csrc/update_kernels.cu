@@ -38,6 +38,7 @@ __device__ __forceinline__ double step_dt(const UpdateArgs& a, int system) {
 
 template <int NV, int T>
 __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
+    pdl_wait();
     const int system = NV == 1 ? 0 : (NV == 3 ? 1 : 2);
     double dt = 0.0;
     if (a.mode == 1) {
@@ -218,8 +219,8 @@ bool few_cells(int64_t nc, int sms) { return nc < int64_t(sms) * 2 * kThreads; }
 template <int NV>
 void update_nv(const UpdateArgs& a, int64_t nc, cudaStream_t s) {
     const int sms = sm_count();
-    if (few_cells(nc, sms)) update_kernel<NV, 64><<<grid_for(nc, sms * 32, 64), 64, 0, s>>>(a);
-    else update_kernel<NV, kThreads><<<grid_for(nc, sms * 8), kThreads, 0, s>>>(a);
+    if (few_cells(nc, sms)) launch_pdl(update_kernel<NV, 64>, dim3(grid_for(nc, sms * 32, 64)), dim3(64), 0, s, a);
+    else launch_pdl(update_kernel<NV, kThreads>, dim3(grid_for(nc, sms * 8)), dim3(kThreads), 0, s, a);
 }
 
 template <int NV>

@@ -276,6 +276,17 @@ __device__ __forceinline__ void block_max_n_atomic(const double* v, unsigned lon
     __syncthreads();
 }
 
+// Programmatic dependent launch: kernels launched with launch_pdl may start while the
+// previous kernel in the stream finishes.  Each of them first waits here for that kernel's
+// completion (and memory), before touching anything, then lets its own dependents be
+// scheduled.  Without a programmatic dependency both instructions return at once.
+__device__ __forceinline__ void pdl_wait() {
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 // Ghost-cell index map: periodic wrap (bc 0), zero-order extrapolation (outflow, bc 1), or
 // the mirror image across the wall (reflective, bc 2: cell -1-g for g < 0, 2n-1-g for
 // g >= n, repeated for tiny grids, i.e. the grid continued with period 2n and mirrored in
