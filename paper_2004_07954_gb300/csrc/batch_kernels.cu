@@ -15,6 +15,7 @@
 // time t[B].  Instances that reached t_final take dt = 0 and are skipped.
 #include "euler_device.cuh"
 #include "launch.h"
+#include "speed_screen.cuh"
 
 namespace wz {
 
@@ -30,9 +31,17 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
     const CellPlanes<NV> sp(smem, CL);
     double* sF = smem + CL * CellPlanes<NV>::kPerCell;        // [3][TI]
     __shared__ int s_inst;
+    __shared__ float s_est[TI];                                // screened speed estimates
+    __shared__ float s_red[THREADS / 32];
 
     const int ntiles = a.tile_off[a.B];
     const double gm1 = a.gamma - 1.0;
+    const float gg1 = __double2float_rn(a.gamma * gm1);
+    // the last state this thread evaluated exactly and its speed: a bit-identical state
+    // (constant regions) reuses it
+    double cs[NV];
+    double csx = 0.0;
+    bool cached = false;
     const int slot = a.stage, next = (a.stage + 1) % 3, clear = (a.stage + 2) % 3;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -98,6 +107,7 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
         const double rdx = 1.0 / dxb;
         double mx = 0.0, unused = 0.0;
         bool bad = false;
+        float emax = 0.0f;
         for (int c = threadIdx.x; c < ncell; c += THREADS) {
             const int64_t gc = o + c0 + c;
             double r[NV];
@@ -110,9 +120,35 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
                 else r[k] = fma(1.0 / 3.0, a.Un[k * a.total + gc], (2.0 / 3.0) * ups);
                 a.out[k * a.total + gc] = r[k];
             }
-            double sx, sy;
-            bad |= !wave_speeds<NV>(r, a.gamma, sx, sy);
-            mx = fmax(mx, sx);
+            // the next stage's LF speed: estimate every cell, evaluate exactly only the cells
+            // the tile-wide screen cannot rule out (-1 marks a cell without a bound)
+            const SpeedEstimate est = estimate_speeds<NV>(r, gg1);
+            s_est[c] = est.ok ? est.sx : -1.0f;
+            emax = fmaxf(emax, est.sx);
+        }
+        emax = warp_max_f(emax);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = emax;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; ++w) emax = fmaxf(emax, s_red[w]);
+        for (int c = threadIdx.x; c < ncell; c += THREADS) {
+            const float e = s_est[c];
+            if (e >= 0.0f && e < emax * kScreenKeep) continue;
+            const int64_t gc = o + c0 + c;
+            double r[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) r[k] = a.out[k * a.total + gc];      // this thread's own writes
+            bool same = cached;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) same = same && __double_as_longlong(r[k]) == __double_as_longlong(cs[k]);
+            if (!same) {
+                double sy;
+                bad |= !wave_speeds<NV>(r, a.gamma, csx, sy);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) cs[k] = r[k];
+                cached = true;
+            }
+            mx = fmax(mx, csx);
         }
         if (bad) atomicOr(a.status, kStatusNonFinite);
         block_max2_atomic(mx, unused, &a.alpha[next * a.B + b], true);

@@ -2,6 +2,7 @@
 // speeds folded in), the standalone LF-speed reduction, the single-line reconstruction and
 // the ghost-cell fill.
 #include "launch.h"
+#include "speed_screen.cuh"
 
 namespace wz {
 
@@ -37,7 +38,7 @@ __device__ __forceinline__ double step_dt(const UpdateArgs& a, int system) {
 }
 
 template <int NV, int T>
-__global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
+__global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs a) {
     pdl_wait();
     const int system = NV == 1 ? 0 : (NV == 3 ? 1 : 2);
     double dt = 0.0;
@@ -53,12 +54,38 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
     double mx = 0.0, my = 0.0;
     double fmx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // per-field speeds, x then y
     bool bad = false;
-    for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
-        const int64_t j = cell / a.nx, i = cell - j * a.nx;
-        const int64_t fx = j * (a.nx + 1) + i;
+    // the next stage's LF speeds: exact evaluation only where the screen cannot rule a cell out
+    const bool speeds = NV != 1 && a.mode != 0 && (a.next_slot >= 0 || a.alpha_next || a.mode == 3);
+    // (64-thread blocks, used for small grids, hold two warps: one of them nearly always
+    // holds the block's candidate, so they skip the screen)
+    const bool screen = T >= 128 && speeds && !a.field_speeds;
+    const float gg1 = __double2float_rn(a.gamma * (a.gamma - 1.0));
+    ScreenMax<T> smax;
+    // the last state this thread evaluated exactly and its speeds: a bit-identical state
+    // (constant regions) reuses them
+    double cs[NV];
+    double cvx = 0.0, cvy = 0.0;
+    bool cached = false;
+    // batches of T consecutive cells, the same count for every thread of the block; the row
+    // j of the cell advances incrementally (one division per thread)
+    const int64_t stride = int64_t(gridDim.x) * T;
+    const int64_t dj = stride / a.nx, di = stride - dj * a.nx;
+    int64_t j = (blockIdx.x * int64_t(T) + threadIdx.x) / a.nx;
+    int64_t i = blockIdx.x * int64_t(T) + threadIdx.x - j * a.nx;
+    for (int64_t base = blockIdx.x * int64_t(T); base < nc; base += stride) {
+        const int64_t cell = base + threadIdx.x;
+        const bool valid = cell < nc;
+        const int64_t fx = cell + j;                      // j * (nx + 1) + i
+        i += di;
+        j += dj;
+        if (i >= a.nx) {
+            i -= a.nx;
+            ++j;
+        }
         double o[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
+            if (!valid) break;
             // Eq. (2): L = -(F^_{i+1/2} - F^_{i-1/2})/dx [- (G^_{j+1/2} - G^_{j-1/2})/dy]
             double L = -((a.Fx[k * sx + fx + 1] - a.Fx[k * sx + fx]) * a.rdx);
             if (NV == 4) L = fma(-(a.Gy[k * sy + cell + a.nx] - a.Gy[k * sy + cell]), a.rdy, L);
@@ -74,25 +101,41 @@ __global__ void __launch_bounds__(T) update_kernel(UpdateArgs a) {
             a.out[k * nc + cell] = r;
             o[k] = r;
         }
-        if (a.mode != 0) {
-            if (NV == 1) {
-                bad |= !isfinite(o[0]);
-            } else if (a.next_slot >= 0 || a.alpha_next || a.mode == 3) {
-                double u, v, c;
-                const bool adm = wave_state<NV>(o, a.gamma, u, v, c);
-                const double vx = __dadd_rn(fabs(u), c), vy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
-                bad |= !(adm && isfinite(vx) && isfinite(vy));
-                mx = fmax(mx, vx);
-                my = fmax(my, vy);
-                if (a.field_speeds) {
-                    double f[3];
-                    field_speeds(u, c, f);
-                    for (int k = 0; k < 3; ++k) fmx[k] = fmax(fmx[k], f[k]);
-                    if (NV == 4) {
-                        field_speeds(v, c, f);
-                        for (int k = 0; k < 3; ++k) fmx[3 + k] = fmax(fmx[3 + k], f[k]);
+        if (NV == 1) {
+            if (a.mode != 0 && valid) bad |= !isfinite(o[0]);
+        } else if (speeds) {
+            bool exact = valid;
+            if (screen) {
+                const SpeedEstimate est = valid ? estimate_speeds<NV>(o, gg1) : SpeedEstimate{0.0f, 0.0f, true};
+                smax.add(est.sx, est.sy);
+                exact = valid && (!est.ok || est.sx >= smax.mx * kScreenKeep ||
+                                  (NV == 4 && est.sy >= smax.my * kScreenKeep));
+            }
+            if (exact) {
+                bool same = screen && cached;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) same = same && __double_as_longlong(o[k]) == __double_as_longlong(cs[k]);
+                if (!same) {
+                    double u, v, c;
+                    const bool adm = wave_state<NV>(o, a.gamma, u, v, c);
+                    cvx = __dadd_rn(fabs(u), c);
+                    cvy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
+                    bad |= !(adm && isfinite(cvx) && isfinite(cvy));
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) cs[k] = o[k];
+                    cached = true;
+                    if (a.field_speeds) {
+                        double f[3];
+                        field_speeds(u, c, f);
+                        for (int k = 0; k < 3; ++k) fmx[k] = fmax(fmx[k], f[k]);
+                        if (NV == 4) {
+                            field_speeds(v, c, f);
+                            for (int k = 0; k < 3; ++k) fmx[3 + k] = fmax(fmx[3 + k], f[k]);
+                        }
                     }
                 }
+                mx = fmax(mx, cvx);
+                my = fmax(my, cvy);
             }
         }
     }
@@ -117,16 +160,40 @@ __global__ void __launch_bounds__(T) max_wavespeed_kernel(const double* U, int64
     double mx = 0.0, my = 0.0;
     double fmx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     bool bad = false;
-    for (int64_t cell = blockIdx.x * int64_t(T) + threadIdx.x; cell < nc; cell += int64_t(gridDim.x) * T) {
+    // the same screen as the update kernel's (exact evaluation only where it cannot rule a
+    // cell out, bit-identical states reuse the last exact speeds)
+    const bool screen = T >= 128 && dst_f == nullptr;
+    const float gg1 = __double2float_rn(gamma * (gamma - 1.0));
+    ScreenMax<T> smax;
+    double cs[NV];
+    bool cached = false;
+    for (int64_t base = blockIdx.x * int64_t(T); base < nc; base += int64_t(gridDim.x) * T) {
+        const int64_t cell = base + threadIdx.x;
+        const bool valid = cell < nc;
         double s[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) s[k] = U[k * nc + cell];
+        for (int k = 0; k < NV; ++k) s[k] = valid ? U[k * nc + cell] : 0.0;
+        bool exact = valid;
+        if (screen) {
+            const SpeedEstimate est = valid ? estimate_speeds<NV>(s, gg1) : SpeedEstimate{0.0f, 0.0f, true};
+            smax.add(est.sx, est.sy);
+            exact = valid && (!est.ok || est.sx >= smax.mx * kScreenKeep ||
+                              (NV == 4 && est.sy >= smax.my * kScreenKeep));
+        }
+        if (!exact) continue;
+        bool same = screen && cached;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) same = same && __double_as_longlong(s[k]) == __double_as_longlong(cs[k]);
+        if (same) continue;
         double u, v, c;
         const bool adm = wave_state<NV>(s, gamma, u, v, c);
         const double vx = __dadd_rn(fabs(u), c), vy = NV == 4 ? __dadd_rn(fabs(v), c) : 0.0;
         bad |= !(adm && isfinite(vx) && isfinite(vy));
         mx = fmax(mx, vx);
         my = fmax(my, vy);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) cs[k] = s[k];
+        cached = true;
         if (dst_f) {
             double f[3];
             field_speeds(u, c, f);
@@ -216,22 +283,33 @@ int sm_count() {
 // they run 64-thread blocks instead, so that the work spreads over all SMs.
 bool few_cells(int64_t nc, int sms) { return nc < int64_t(sms) * 2 * kThreads; }
 
+// Blocks of `kern` resident on one SM at once: the grid-stride kernels launch exactly that
+// many per SM, so that every SM gets the same number of cells (no partial last wave).
+template <typename... KArgs>
+int resident_blocks(void (*kern)(KArgs...), int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
 template <int NV>
 void update_nv(const UpdateArgs& a, int64_t nc, cudaStream_t s) {
     const int sms = sm_count();
+    static const int occ = resident_blocks(update_kernel<NV, kThreads>, kThreads);
     if (few_cells(nc, sms)) launch_pdl(update_kernel<NV, 64>, dim3(grid_for(nc, sms * 32, 64)), dim3(64), 0, s, a);
-    else launch_pdl(update_kernel<NV, kThreads>, dim3(grid_for(nc, sms * 8)), dim3(kThreads), 0, s, a);
+    else launch_pdl(update_kernel<NV, kThreads>, dim3(grid_for(nc, sms * occ)), dim3(kThreads), 0, s, a);
 }
 
 template <int NV>
 void max_wavespeed_nv(const double* U, int64_t nc, double gamma, unsigned long long* dst, int32_t* status,
                       unsigned long long* dst_f, cudaStream_t s) {
     const int sms = sm_count();
+    static const int occ = resident_blocks(max_wavespeed_kernel<NV, kThreads>, kThreads);
     if (few_cells(nc, sms))
         max_wavespeed_kernel<NV, 64><<<grid_for(nc, sms * 16, 64), 64, 0, s>>>(U, nc, gamma, dst, status, dst_f);
     else
-        max_wavespeed_kernel<NV, kThreads><<<grid_for(nc, sms * 4), kThreads, 0, s>>>(U, nc, gamma, dst, status,
-                                                                                        dst_f);
+        max_wavespeed_kernel<NV, kThreads><<<grid_for(nc, sms * occ), kThreads, 0, s>>>(U, nc, gamma, dst, status,
+                                                                                          dst_f);
 }
 
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
