@@ -40,7 +40,17 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "990cc3a5e9814de6", "n": 4096, "bytes": 962.2e6}
+TRAFFIC_CAPTURE = {"sha256_16": "990cc3a5e9814de6", "n": 4096, "bytes": 962.2e6,
+                   "fp64_pipe": {"x": 0.886, "y": 0.887}}   # ncu FP64-pipe busy, same capture
+
+
+def hbm_peak() -> tuple:
+    """Measured HBM copy bandwidth of the GB300s (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def kernel_source_hash() -> str:
@@ -85,7 +95,8 @@ def parse_args():
     ap.add_argument("--adjoint-fd-dirs", type=int, default=20)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "variants"], default=None,
+    ap.add_argument("--no-euler1d", action="store_true")
+    ap.add_argument("--only", choices=["batched", "adjoint", "variants", "euler1d"], default=None,
                     help="run only this part and print its object (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
@@ -104,6 +115,7 @@ OPS_2D = {  # (weights, split): per-unit counts, 2D Euler
     (0, 3): (1090.0, 152.0, 28.0, 20.0, 48.0),    # Steger-Warming
 }
 OPS_1D_CELL_UPDATE = 2448.0     # 1D Euler, default scheme, per cell-update (large grid)
+OPS_1D = (755.0, 32.0, 11.0, 6.0)   # 1D Euler: interface, cell per sweep, LF speed, difference
 
 
 def algorithmic_flops(nx: int, ny: int, weights: int = 0, split: int = 0) -> dict:
@@ -236,6 +248,47 @@ def bench_batched(wenozn, inputs, seed: int, K: int, B: int = 2048) -> dict:
                                       "graph_ms_per_step": round(graph_ms, 2),
                                       "speedup_vs_eager": round(eager_ms / ms_step, 1),
                                       "speedup_vs_graph": round(graph_ms / ms_step, 2)},
+            "device_status": status}
+
+
+def bench_euler1d(wenozn, inputs, seed: int, n: int = 1 << 20, K: int = 100) -> dict:
+    """Single 1D Euler problem of n cells (the seeded Shu-Osher family, outflow, CFL 0.5):
+    K chained RK3 steps in one call after 3 warm-up steps, CUDA events; the x-flux kernel
+    timed alone for its FP64 fraction (algorithmic flops of the oracle's count)."""
+    import torch
+    U0 = inputs.euler1d_ic(n, seed)
+    p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_1D, n, 1, 10.0 / n, 1.0)
+    U = torch.from_numpy(U0).cuda()
+    S = wenozn.Solver(p)
+    S.steps(U, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S.steps(U, K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / K
+    status = S.status()
+    alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
+    wenozn.wenozn_max_wavespeed(p, U, alpha)
+    buf = torch.empty(wenozn.flux_shape(p, 0), dtype=torch.float64, device="cuda")
+    wenozn.wenozn_flux(p, U, alpha, 0, buf)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        wenozn.wenozn_flux(p, U, alpha, 0, buf)
+    e1.record()
+    torch.cuda.synchronize()
+    flux_ms = e0.elapsed_time(e1) / reps
+    iface, cell, _, _ = OPS_1D
+    flux_flops = iface * (n + 1) + cell * n
+    return {"workload": f"1D Euler, {n} cells, seeded Shu-Osher family (seed {seed}), outflow, CFL 0.5, "
+                        f"{K} chained SSP-RK3 steps",
+            "metric": "cell-updates/s", "value": n / (ms_step / 1e3), "ms_per_step": round(ms_step, 4),
+            "fp64_frac": round(OPS_1D_CELL_UPDATE * n / (ms_step / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+            "flux_kernel": {"kernel": "flux_kernel<3,0> (512-interface tiles)", "ms": round(flux_ms, 4),
+                            "frac": round(flux_flops / (flux_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "device_status": status}
 
 
@@ -388,9 +441,22 @@ def cpu_baseline(n_full: int, seed: int, target_s: float, steps: int = 1) -> dic
     for _ in range(steps):
         U, _ = O.rk3_step(P, U)
     el = time.perf_counter() - t0
+    # the same oracle on one core, one step on a 512 x 512 sample
+    m1 = min(512, n_full)
+    U1 = inputs.euler2d_ic(m1, m1, seed)
+    P1 = O.problem(O.EULER2D, m1, m1, dx=1.0 / m1, dy=1.0 / m1)
+    O.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.rk3_step(P1, U1)
+        el1 = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(cores)
     return {"value": steps * m * m / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} SSP-RK3 step(s) of the same seeded four-quadrant 2D Euler problem on a "
-                      f"{m}x{m} grid (plain FP64 C++ oracle, OpenMP over grid lines), {el:.1f} s"}
+                      f"{m}x{m} grid (plain FP64 C++ oracle, OpenMP over grid lines), {el:.1f} s",
+            "single_core": {"value": m1 * m1 / el1, "cores": 1,
+                            "sample": f"1 SSP-RK3 step on a {m1}x{m1} grid, {el1:.2f} s"}}
 
 
 def run_reference(args, rank: int):
@@ -457,6 +523,8 @@ def main():
             part = bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
         elif args.only == "variants":
             part = bench_variants(wenozn, inputs, args.seed + rank, args.n)
+        elif args.only == "euler1d":
+            part = bench_euler1d(wenozn, inputs, args.seed + rank)
         else:
             part = bench_adjoint(wenozn, inputs, args.seed + rank, steps=args.adjoint_steps,
                                  fd_dirs=args.adjoint_fd_dirs)
@@ -517,8 +585,9 @@ def main():
     del fx, fy
     fl = algorithmic_flops(n, n)
     achieved = fl["x_flux"] / (kern[0] / 1e3) / 1e9
-    traffic = TRAFFIC_CAPTURE["bytes"] if (kernel_source_hash() == TRAFFIC_CAPTURE["sha256_16"]
-                                           and n == TRAFFIC_CAPTURE["n"]) else None
+    captured = kernel_source_hash() == TRAFFIC_CAPTURE["sha256_16"] and n == TRAFFIC_CAPTURE["n"]
+    traffic = TRAFFIC_CAPTURE["bytes"] if captured else None
+    hbm_gbs, hbm_src = hbm_peak()
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
                 "kernel": "flux_kernel<4,0> (x-direction interface fluxes)",
@@ -526,7 +595,12 @@ def main():
                 "kernel_ms": {"x_flux": round(kern[0], 3), "y_flux": round(kern[1], 3)},
                 "y_flux_frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
                 "step_frac": round(fl["step"] * world * args.steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS / world, 4),
-                "algorithmic_flops_per_cell_update": round(fl["per_cell_update"], 1)}
+                "algorithmic_flops_per_cell_update": round(fl["per_cell_update"], 1),
+                # ncu counters of the same kernels (null once the kernel sources changed)
+                "fp64_pipe_ncu": TRAFFIC_CAPTURE["fp64_pipe"] if captured else None,
+                "dram": None if traffic is None else {
+                    "gbs": round(traffic / (kern[0] / 1e3) / 1e9, 1), "peak_gbs": hbm_gbs,
+                    "frac": round(traffic / (kern[0] / 1e3) / 1e9 / hbm_gbs, 5), "peak_source": hbm_src}}
 
     # ---- end to end: host buffers, copies inside the timed region --------------------
     # Every step copies its input from pinned host memory and its result back.  The copies
@@ -575,6 +649,7 @@ def main():
            "copies": "pinned host <-> device on one stream per direction, overlapped with the previous/next step"}
 
     batched = None if args.no_batched else bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
+    euler1d = None if args.no_euler1d else bench_euler1d(wenozn, inputs, args.seed + rank)
     variants = None if args.no_variants else bench_variants(wenozn, inputs, args.seed + rank, n)
     adjoint = None if args.no_adjoint else bench_adjoint(wenozn, inputs, args.seed + rank,
                                                          steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
@@ -593,7 +668,7 @@ def main():
                            "parallelism": f"{world} independent replica(s), one per GPU",
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "variants": variants, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "variants": variants, "adjoint": adjoint,
                 "gpu_launches": 9 * args.steps + 1, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -27,6 +27,8 @@ def test_1d_cell_update(orc):
     parts = orc.opcount_parts(1)
     per_stage = parts["interface"] + parts["cell_per_sweep"] + parts["wavespeed_cell"] + parts["difference_cell_per_dir"]
     assert 3 * per_stage + 36.0 == bench.OPS_1D_CELL_UPDATE
+    assert (parts["interface"], parts["cell_per_sweep"], parts["wavespeed_cell"],
+            parts["difference_cell_per_dir"]) == bench.OPS_1D
     n = 16
     assert _total(orc.opcount_rhs(1, n)) == (parts["interface"] * (n + 1) + parts["cell_per_sweep"] * (n + 6)
                                             + (parts["wavespeed_cell"] + parts["difference_cell_per_dir"]) * n)
