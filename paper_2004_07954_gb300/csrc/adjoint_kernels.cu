@@ -321,38 +321,83 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
 }
 
 // Per cell i: sum the contributions of the stencil positions that map to it (ghost cells
-// included, fixed order), apply J_F^T to the flux part, add alpha times the LF part and the
-// Roe part, and write out_i = c1 X1_i + c2 X2_i + c3 X3_i + d (J^T lambda)_i.  For Euler the
-// block holding the argmax cell of the LF speed also sums the interface kernel's partials of
-// the LF-speed cotangent (fixed order), adds its term d(|u| + c)/dU there (|x|' = 0 at 0) and
-// clears the argmax word.
-template <int NV>
-__global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
-    constexpr int Q = 2 * NV;
+// included, fixed order), apply the cell's own derivatives once and write
+// out_i = c1 X1_i + c2 X2_i + c3 X3_i + d (J^T lambda)_i.  Advection: f = a u, so the flux
+// part takes the factor a and the LF part |a|.
+__global__ void __launch_bounds__(kGather) vjp_gather_advection(VjpArgs a) {
     pdl_wait();
     const int n = a.n;
     const int64_t P = int64_t(n) + 1;
     const int i = blockIdx.x * kGather + threadIdx.x;
-    double Ub[NV];
+    if (i >= n) return;
+    double Fs = 0.0, Ds = 0.0;
+    if (i >= 3 && i <= n - 4) {
+        // interior: the cell is stencil position s of interface i + 3 - s only
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const int64_t j = i + 3 - s;
+            Fs += a.C[(s * 2) * P + j];
+            Ds += a.C[(s * 2 + 1) * P + j];
+        }
+    } else {
+        int gs[16], ng = 0;             // stencil cells g (in -3 .. n+2) that map to i
+        if (n <= 8) {
+            for (int g = -3; g <= n + 2; ++g)
+                if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
+        } else if (a.bc == 0) {
+            for (int g = i - n; g <= i + n; g += n)
+                if (g >= -3 && g <= n + 2) gs[ng++] = g;
+        } else {
+            gs[ng++] = i;
+            if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
+            if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
+        }
+        for (int q = 0; q < ng; ++q) {
+            const int g = gs[q];
+            for (int s = 0; s < 6; ++s) {
+                const int j = g + 3 - s;         // interface whose stencil position s is g
+                if (j < 0 || j > n) continue;
+                Fs += a.C[(s * 2) * P + j];
+                Ds += a.C[(s * 2 + 1) * P + j];
+            }
+        }
+    }
+    double v = a.d * fma(a.adv_speed, Fs, fabs(a.adv_speed) * Ds);
+    if (a.X1) v = fma(a.c1, a.X1[i], v);
+    if (a.X2) v = fma(a.c2, a.X2[i], v);
+    if (a.X3) v = fma(a.c3, a.X3[i], v);
+    a.out[i] = v;
+}
+
+// Euler: one warp per conserved component, so that the three threads of a cell each sum
+// their own component's contributions (fixed order, as above), exchange the flux parts
+// through shared memory and apply their row of J_F^T (F = (m, m u + p, u (E + p))); three
+// times the warps of one thread per cell, which the FP64 latency of the sums needs at small
+// n.  The block holding the argmax cell of the LF speed also sums the interface kernel's
+// partials of the LF-speed cotangent (fixed order), adds its term d(|u| + c)/dU there
+// (|x|' = 0 at 0) and clears the argmax word.
+constexpr int kGatherCells = 32;
+
+__global__ void __launch_bounds__(3 * kGatherCells) vjp_gather_euler(VjpArgs a) {
+    constexpr int Q = 6;
+    __shared__ double sF[3][kGatherCells];
+    pdl_wait();
+    const int n = a.n;
+    const int64_t P = int64_t(n) + 1;
+    const int m = threadIdx.x / kGatherCells, lane = threadIdx.x % kGatherCells;
+    const int i = blockIdx.x * kGatherCells + lane;
+    double Fs = 0.0, Ds = 0.0, Rs = 0.0;
     if (i < n) {
-        double Fs[NV], Ds[NV], Rs[NV];
-        for (int m = 0; m < NV; ++m) Fs[m] = Ds[m] = Rs[m] = 0.0;
         if (i >= 3 && i <= n - 4) {
-            // interior: the cell is stencil position s of interface i + 3 - s only
 #pragma unroll
             for (int s = 0; s < 6; ++s) {
                 const int64_t j = i + 3 - s;
-#pragma unroll
-                for (int m = 0; m < NV; ++m) {
-                    Fs[m] += a.C[(s * Q + m) * P + j];
-                    Ds[m] += a.C[(s * Q + NV + m) * P + j];
-                }
+                Fs += a.C[(s * Q + m) * P + j];
+                Ds += a.C[(s * Q + 3 + m) * P + j];
             }
-            if (NV == 3)
-#pragma unroll
-                for (int m = 0; m < NV; ++m) Rs[m] = a.C[(kRoe + 3 + m) * P + i] + a.C[(kRoe + m) * P + i + 1];
+            Rs = a.C[(kRoe + 3 + m) * P + i] + a.C[(kRoe + m) * P + i + 1];
         } else {
-            int gs[16], ng = 0;             // stencil cells g (in -3 .. n+2) that map to i
+            int gs[16], ng = 0;
             if (n <= 8) {
                 for (int g = -3; g <= n + 2; ++g)
                     if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
@@ -367,74 +412,72 @@ __global__ void __launch_bounds__(kGather) vjp_gather_kernel(VjpArgs a) {
             for (int q = 0; q < ng; ++q) {
                 const int g = gs[q];
                 for (int s = 0; s < 6; ++s) {
-                    const int j = g + 3 - s;         // interface whose stencil position s is g
+                    const int j = g + 3 - s;
                     if (j < 0 || j > n) continue;
-                    for (int m = 0; m < NV; ++m) {
-                        Fs[m] += a.C[(s * Q + m) * P + j];
-                        Ds[m] += a.C[(s * Q + NV + m) * P + j];
-                    }
-                    if (NV == 3 && (s == 2 || s == 3))
-                        for (int m = 0; m < NV; ++m) Rs[m] += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
+                    Fs += a.C[(s * Q + m) * P + j];
+                    Ds += a.C[(s * Q + 3 + m) * P + j];
+                    if (s == 2 || s == 3) Rs += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
                 }
             }
         }
-        if (NV == 1) {
-            Ub[0] = fma(a.adv_speed, Fs[0], fabs(a.adv_speed) * Ds[0]);
-        } else {
-            const double alpha = __longlong_as_double((long long)a.alpha_bits[0]);
-            const double gm1 = a.gamma - 1.0;
-            const double rho = a.U[i], mom = a.U[n + i], E = a.U[2 * int64_t(n) + i];
-            const double r = 1.0 / rho, u = mom * r;
-            const double p = gm1 * (E - 0.5 * mom * u);
-            const double Ep = E + p;
-            // F = (mom, mom u + p, u (E + p)), u = mom/rho, p = (gamma-1)(E - mom u/2)
-            const double pb = fma(Fs[2], u, Fs[1]);
-            double mb = fma(Fs[1], u, Fs[0]) - gm1 * 0.5 * u * pb;
-            const double Eb = fma(Fs[2], u, gm1 * pb);
-            const double ub = fma(Fs[1], mom, Fs[2] * Ep) - gm1 * 0.5 * mom * pb;
-            mb = fma(ub, r, mb);
-            const double rb = -ub * u * r;
-            Ub[0] = fma(alpha, Ds[0], rb) + Rs[0];
-            Ub[1] = fma(alpha, Ds[1], mb) + Rs[1];
-            Ub[2] = fma(alpha, Ds[2], Eb) + Rs[2];
-        }
     }
-    if (NV == 3) {
-        const unsigned key = a.ctl[0];
-        const int im = key ? int(~key) : -1;
-        if (im >= 0 && im / kGather == int(blockIdx.x)) {     // uniform over the block
-            __shared__ double red[kGather / 32];
-            double v = 0.0;
-            for (int b = threadIdx.x; b < a.nblocks; b += kGather) v += a.partial[b];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-            __syncthreads();
-            if (i == im) {
-                double abar = 0.0;
-                for (int w = 0; w < kGather / 32; ++w) abar += red[w];
-                const double rho = a.U[i], mom = a.U[n + i], E = a.U[2 * int64_t(n) + i];
-                const double u = mom / rho;
-                const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
-                const double c = sqrt(a.gamma * p / rho);
-                const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
-                const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
-                Ub[0] += abar * (sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho));
-                Ub[1] += abar * (sg / rho - kk * gm1 * u);
-                Ub[2] += abar * (kk * gm1);
-                a.ctl[0] = 0u;
-            }
+    sF[m][lane] = Fs;
+    __syncthreads();
+    double Ub = 0.0;
+    double rho = 1.0, mom = 0.0, E = 0.0;
+    if (i < n) {
+        const double F0 = sF[0][lane], F1 = sF[1][lane], F2 = sF[2][lane];
+        const double alpha = __longlong_as_double((long long)a.alpha_bits[0]);
+        const double gm1 = a.gamma - 1.0;
+        rho = a.U[i];
+        mom = a.U[n + i];
+        E = a.U[2 * int64_t(n) + i];
+        const double r = 1.0 / rho, u = mom * r;
+        const double p = gm1 * (E - 0.5 * mom * u);
+        const double Ep = E + p;
+        // F = (mom, mom u + p, u (E + p)), u = mom/rho, p = (gamma-1)(E - mom u/2)
+        const double pb = fma(F2, u, F1);
+        double part;
+        if (m == 2) {
+            part = fma(F2, u, gm1 * pb);                                   // E bar
+        } else {
+            const double ub = fma(F1, mom, F2 * Ep) - gm1 * 0.5 * mom * pb;
+            if (m == 1) part = fma(ub, r, fma(F1, u, F0) - gm1 * 0.5 * u * pb);   // m bar
+            else part = -ub * u * r;                                       // rho bar
         }
+        Ub = fma(alpha, Ds, part) + Rs;
+    }
+    const unsigned key = a.ctl[0];
+    const int im = key ? int(~key) : -1;
+    if (im >= 0 && im / kGatherCells == int(blockIdx.x)) {     // uniform over the block
+        __shared__ double red[3];
+        double v = 0.0;
+        for (int b = threadIdx.x; b < a.nblocks; b += 3 * kGatherCells) v += a.partial[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[m] = v;
+        __syncthreads();
+        if (i == im) {
+            const double abar = red[0] + red[1] + red[2];
+            const double u = mom / rho;
+            const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
+            const double c = sqrt(a.gamma * p / rho);
+            const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
+            const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
+            if (m == 0) Ub += abar * (sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho));
+            else if (m == 1) Ub += abar * (sg / rho - kk * gm1 * u);
+            else Ub += abar * (kk * gm1);
+        }
+        __syncthreads();
+        if (i == im && m == 0) a.ctl[0] = 0u;
     }
     if (i >= n) return;
-    for (int m = 0; m < NV; ++m) {
-        const int64_t idx = int64_t(m) * n + i;
-        double v = a.d * Ub[m];
-        if (a.X1) v = fma(a.c1, a.X1[idx], v);
-        if (a.X2) v = fma(a.c2, a.X2[idx], v);
-        if (a.X3) v = fma(a.c3, a.X3[idx], v);
-        a.out[idx] = v;
-    }
+    const int64_t idx = int64_t(m) * n + i;
+    double v = a.d * Ub;
+    if (a.X1) v = fma(a.c1, a.X1[idx], v);
+    if (a.X2) v = fma(a.c2, a.X2[idx], v);
+    if (a.X3) v = fma(a.c3, a.X3[idx], v);
+    a.out[idx] = v;
 }
 
 }  // namespace
@@ -476,6 +519,7 @@ size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
     const unsigned gi = unsigned(vjp_partial_count(a.n)), gc = unsigned((a.n + kGather - 1) / kGather);
+    const unsigned ge = unsigned((a.n + kGatherCells - 1) / kGatherCells);
     cudaError_t e;
     if (system == 0) {
         e = launch_pdl(vjp_interface_advection, dim3(gi), dim3(kTI), 0, s, a);
@@ -485,8 +529,8 @@ cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = launch_pdl(vjp_interface_euler, dim3(gi), dim3(3 * kTI), pad, s, a);
     }
     if (e == cudaSuccess)
-        e = system == 0 ? launch_pdl(vjp_gather_kernel<1>, dim3(gc), dim3(kGather), 0, s, a)
-                        : launch_pdl(vjp_gather_kernel<3>, dim3(gc), dim3(kGather), 0, s, a);
+        e = system == 0 ? launch_pdl(vjp_gather_advection, dim3(gc), dim3(kGather), 0, s, a)
+                        : launch_pdl(vjp_gather_euler, dim3(ge), dim3(3 * kGatherCells), 0, s, a);
     return e;
 }
 
