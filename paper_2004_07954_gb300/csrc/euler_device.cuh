@@ -79,7 +79,7 @@ __device__ __forceinline__ void split_cell(const double* Uc, double alpha, doubl
 // 2 local LF, 3 Steger-Warming):
 //   0     h+- = (F +- alpha U)/2, as split_cell;
 //   1, 2  hp = F/2, hm = U/2 (split after the projection, per field or per interface), and
-//         the cell's |u_n| + c in the speed plane (oracle operation order);
+//         for 2 the cell's |u_n| + c in the speed plane;
 //   3     hp = F+, hm = F- of Steger and Warming:
 //         F+- = rho/(2 gamma) (2(g-1) l2 + l1 + l3, 2(g-1) l2 u + l1 (u-c) + l3 (u+c),
 //                              [(2(g-1) l2 + l1 + l3) v,] (g-1) l2 q^2 + l1 ((u-c)^2 + v^2)/2
@@ -136,9 +136,9 @@ __device__ __forceinline__ void split_cell_gen(const double* Uc, int split, doub
             s.hp[k * s.NC + si] = hF[k];
             s.hm[k * s.NC + si] = 0.5 * Uc[k];
         }
-        double vx, vy;
-        wave_speeds<NV>(Uc, gamma, vx, vy);
-        s.sp[si] = vx;
+        // local LF: the cell's |u_n| + c (the interface takes the largest of its six cells;
+        // the per-field splitting reads global speeds instead)
+        if (split == 2) s.sp[si] = fabs(un) + sqrt(gamma * p * rr);
     }
     s.sr[si] = rho * rs;
     s.un[si] = un;
