@@ -585,6 +585,8 @@ def main():
     del fx, fy
     fl = algorithmic_flops(n, n)
     achieved = fl["x_flux"] / (kern[0] / 1e3) / 1e9
+    # the FP64 rate pure FMA register arithmetic reaches on this GPU, beside the nominal peak
+    probe = max(wenozn.wenozn_fp64_fma_rate(1 << 17, stream) for _ in range(3))
     captured = kernel_source_hash() == TRAFFIC_CAPTURE["sha256_16"] and n == TRAFFIC_CAPTURE["n"]
     traffic = TRAFFIC_CAPTURE["bytes"] if captured else None
     hbm_gbs, hbm_src = hbm_peak()
@@ -596,6 +598,10 @@ def main():
                 "y_flux_frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
                 "step_frac": round(fl["step"] * world * args.steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS / world, 4),
                 "algorithmic_flops_per_cell_update": round(fl["per_cell_update"], 1),
+                "fp64_fma_probe": {"gflops": round(probe, 1), "of_peak": round(probe / FP64_PEAK_GFLOPS, 4),
+                                   "frac_of_probe": round(achieved / probe, 4),
+                                   "what": "pure FP64 FMA register arithmetic, 2 blocks x 256 threads per SM "
+                                           "(wenozn_fp64_fma_rate), measured in this run"},
                 # ncu counters of the same kernels (null once the kernel sources changed)
                 "fp64_pipe_ncu": TRAFFIC_CAPTURE["fp64_pipe"] if captured else None,
                 "dram": None if traffic is None else {

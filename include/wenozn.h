@@ -353,6 +353,15 @@ wenozn_status wenozn_batch_state(void* ws, int32_t nbatch, const int64_t* offset
 wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, double* ieee,
                                       void* stream);
 
+/* Measurement: the FP64 FMA rate this GPU sustains on pure register arithmetic (two blocks
+ * of 256 threads per SM, four independent FMA chains per thread, fmas_per_thread FMAs each,
+ * no memory traffic), timed with CUDA events on `stream` after one warm-up launch; the
+ * call synchronizes `stream`.  Writes GFLOP/s (2 flops per FMA) to the host double
+ * *gflops.  It is the achievable ceiling beside the nominal peak (2 FP64 FMA lanes per SM
+ * per clock) against which the FP64-bound kernels of Sec. 2 and Sec. 4 are measured.
+ * EINVAL unless 4 <= fmas_per_thread <= 2^32 and gflops is non-NULL. */
+wenozn_status wenozn_fp64_fma_rate(int64_t fmas_per_thread, double* gflops, void* stream);
+
 /* Static description of a status code. */
 const char* wenozn_status_string(wenozn_status s);
 

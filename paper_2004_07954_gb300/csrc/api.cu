@@ -310,6 +310,11 @@ wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, 
     return cuda_status(launch_rcp_check(d, n, fast, ieee, static_cast<cudaStream_t>(stream)));
 }
 
+wenozn_status wenozn_fp64_fma_rate(int64_t fmas_per_thread, double* gflops, void* stream) {
+    if (!gflops || fmas_per_thread < 4 || fmas_per_thread > (int64_t(1) << 32)) return WENOZN_EINVAL;
+    return cuda_status(measure_fma_rate(fmas_per_thread, gflops, static_cast<cudaStream_t>(stream)));
+}
+
 const char* wenozn_status_string(wenozn_status s) {
     switch (s) {
         case WENOZN_OK: return "ok";

@@ -132,6 +132,9 @@ cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
 // (read back by wenozn_last_error).
 void note_status(void* stream, int32_t* status_dev);
 
+// Times sm_count x 2 blocks of 256 threads, each thread fmas_per_thread independent FP64
+// FMAs (four chains), after one warm-up launch; writes the achieved GFLOP/s (2 per FMA).
+cudaError_t measure_fma_rate(int64_t fmas_per_thread, double* gflops, cudaStream_t s);
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,

@@ -263,6 +263,24 @@ __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int 
     }
 }
 
+// FP64 FMA rate probe: four independent FMA chains per thread and no memory traffic in the
+// loop; every thread stores its sum through a pointer argument (into a static buffer for up
+// to kProbeBlocks blocks).  Measured on GB300: a conditional store, or a store to the
+// device symbol itself, made the same loop run at 0.84 of this rate.
+constexpr int kProbeBlocks = 512;
+__device__ double g_fma_out[kProbeBlocks * kThreads];
+
+__global__ void __launch_bounds__(kThreads) fma_probe_kernel(double* out, int iters, double a, double b) {
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+    for (int it = 0; it < iters; ++it) {
+        x0 = fma(x0, a, b);
+        x1 = fma(x1, a, b);
+        x2 = fma(x2, a, b);
+        x3 = fma(x3, a, b);
+    }
+    out[blockIdx.x * kThreads + threadIdx.x] = (x0 + x1) + (x2 + x3);
+}
+
 unsigned grid_for(int64_t items, int cap, int threads = kThreads) {
     int64_t b = (items + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -338,6 +356,32 @@ cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, 
     reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A),
                                                  zn_fast_rcp(eps, A, weights), weights);
     return cudaGetLastError();
+}
+
+cudaError_t measure_fma_rate(int64_t fmas_per_thread, double* gflops, cudaStream_t s) {
+    const int grid = 2 * sm_count() < kProbeBlocks ? 2 * sm_count() : kProbeBlocks;
+    const int iters = int(fmas_per_thread / 4);
+    double* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&out), g_fma_out);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        fma_probe_kernel<<<grid, kThreads, 0, s>>>(out, iters, 0.999999, 1e-7);     // warm-up
+        e = cudaEventRecord(e0, s);
+    }
+    if (e == cudaSuccess) {
+        fma_probe_kernel<<<grid, kThreads, 0, s>>>(out, iters, 0.999999, 1e-7);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess) *gflops = ms > 0.0f ? 2.0 * 4.0 * double(iters) * grid * kThreads / (ms * 1e6) : 0.0;
+    return e;
 }
 
 cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s) {

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
     "wenozn_last_error": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
+    "wenozn_fp64_fma_rate": [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _VP],
     "wenozn_vjp_workspace_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "wenozn_rhs_vjp": [_P, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_rk3_step_vjp": [_P, _VP, ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP],
@@ -276,6 +277,13 @@ def wenozn_check_reciprocal(d: torch.Tensor, stream=None):
                                                                     _dev_ptr(fast, "fast"), _dev_ptr(ieee, "ieee"),
                                                                     _stream(stream)))
     return fast, ieee
+
+
+def wenozn_fp64_fma_rate(fmas_per_thread: int = 1 << 17, stream=None) -> float:
+    """GFLOP/s of pure FP64 FMA register arithmetic on this GPU (synchronizes the stream)."""
+    g = ctypes.c_double(0.0)
+    _check("wenozn_fp64_fma_rate", lib().wenozn_fp64_fma_rate(int(fmas_per_thread), ctypes.byref(g), _stream(stream)))
+    return g.value
 
 
 def wenozn_workspace_dt(ws: torch.Tensor) -> torch.Tensor:

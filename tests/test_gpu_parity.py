@@ -104,6 +104,16 @@ def test_newton_reciprocal_within_one_ulp(wz):
     assert np.all(np.abs(f - i) <= ulp)
 
 
+def test_fp64_fma_rate(wz):
+    """The FP64 FMA probe reports a rate between half and all of the nominal peak
+    (2 FMA lanes per SM per clock, 152 SMs, 2070 MHz) and rejects bad arguments."""
+    g = wz.wenozn_fp64_fma_rate(1 << 15)
+    assert 0.5 * 1258.6 < g < 1.02 * 1258.6
+    for bad in (0, 3, (1 << 32) + 1):
+        with pytest.raises(wz.WenoznError):
+            wz.wenozn_fp64_fma_rate(bad)
+
+
 # ------------------------------------------------------------------ ghosts and LF speeds
 @pytest.mark.parametrize("bc", [0, 1])
 def test_fill_ghosts(wz, orc, bc):
