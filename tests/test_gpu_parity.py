@@ -350,6 +350,34 @@ def test_full_size_tiled_periodic(wz, orc, system, n_big, n_tile):
     assert S.status() == 0
 
 
+def test_benchmark_workload_full_grid(wz, orc):
+    """The benchmark's own workload (2D Euler 4096^2, the seeded four-quadrant problem with
+    seed 0, outflow), through the chained call the benchmark times: every cell of one RK3 step
+    against the oracle's step of the same data, the CFL step bit for bit; and the CFL step of
+    a two-step chain's second step, which comes from the update kernel's screened LF speeds,
+    against the oracle's for the GPU's state after the first step."""
+    n = 4096
+    U0 = inputs.euler2d_ic(n, n, seed=0)
+    p = gpu_problem(wz, 2, n, n, dx=1.0 / n, dy=1.0 / n, bc=1)
+    P = orc_problem(orc, p)
+    one, two = wz.Solver(p), wz.Solver(p)
+    t1, t2 = dev(U0), dev(U0)
+    one.steps(t1, 1)
+    two.steps(t2, 2)
+    torch.cuda.synchronize()
+    dt1 = wz.wenozn_workspace_dt(one.ws).item()
+    dt2 = wz.wenozn_workspace_dt(two.ws).item()
+    assert one.status() == 0 and two.status() == 0
+    del t2, two
+    want, dt_o = orc.rk3_step(P, U0)
+    del U0
+    assert dt1 == dt_o
+    got = host(t1)
+    assert rel_linf(got, want) <= STEP_TOL
+    del want
+    assert dt2 == orc.cfl_dt(P, got)
+
+
 # ------------------------------------------------------------------ invariants on the GPU
 def test_conservation_periodic_gpu(wz):
     n = 256
