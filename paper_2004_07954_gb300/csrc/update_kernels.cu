@@ -48,6 +48,11 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
     } else if (a.mode > 1) {
         dt = a.ctrl->dt;
     }
+    // the stage as base - kx dF - ky dG, with the RK weight of the update and dt/dx, dt/dy
+    // folded into kx, ky: stage 1 U1 = U + dt L; 2: 3/4 U^n + 1/4 (U_s + dt L); 3: 1/3 U^n
+    // + 2/3 (U_s + dt L), where L = -dF/dx - dG/dy (Eq. (2))
+    const double wk = a.mode == 1 ? 1.0 : (a.mode == 2 ? 0.25 : 2.0 / 3.0);
+    const double kx = wk * dt * a.rdx, ky = wk * dt * a.rdy;
     const int64_t nc = int64_t(a.nx) * a.ny;
     const int64_t sx = int64_t(a.ny) * (a.nx + 1);       // x-flux plane stride
     const int64_t sy = int64_t(a.ny + 1) * a.nx;         // y-flux plane stride
@@ -87,16 +92,19 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
         for (int k = 0; k < NV; ++k) {
             if (!valid) break;
             // Eq. (2): L = -(F^_{i+1/2} - F^_{i-1/2})/dx [- (G^_{j+1/2} - G^_{j-1/2})/dy]
-            double L = -((a.Fx[k * sx + fx + 1] - a.Fx[k * sx + fx]) * a.rdx);
-            if (NV == 4) L = fma(-(a.Gy[k * sy + cell + a.nx] - a.Gy[k * sy + cell]), a.rdy, L);
+            const double dF = a.Fx[k * sx + fx + 1] - a.Fx[k * sx + fx];
+            const double dG = NV == 4 ? a.Gy[k * sy + cell + a.nx] - a.Gy[k * sy + cell] : 0.0;
             double r;
             if (a.mode == 0) {
-                r = L;
+                r = -(dF * a.rdx);
+                if (NV == 4) r = fma(-dG, a.rdy, r);
             } else {
-                const double ups = fma(dt, L, a.Us[k * nc + cell]);
-                if (a.mode == 1) r = ups;
-                else if (a.mode == 2) r = fma(0.75, a.Un[k * nc + cell], 0.25 * ups);
-                else r = fma(1.0 / 3.0, a.Un[k * nc + cell], (2.0 / 3.0) * ups);
+                const double us = a.Us[k * nc + cell];
+                double base = us;
+                if (a.mode == 2) base = fma(0.75, a.Un[k * nc + cell], 0.25 * us);
+                else if (a.mode == 3) base = fma(1.0 / 3.0, a.Un[k * nc + cell], (2.0 / 3.0) * us);
+                r = fma(-kx, dF, base);
+                if (NV == 4) r = fma(-ky, dG, r);
             }
             a.out[k * nc + cell] = r;
             o[k] = r;
