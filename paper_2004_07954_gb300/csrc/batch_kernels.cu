@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
             for (int k = 0; k < NV; ++k) sF[k * TI + jl] = Fh[k];
         }
         __syncthreads();
-        const double rdx = 1.0 / dxb;
+        // the stage as base - kx dF with the RK weight and dt/dx folded into kx (Eq. (2))
+        const double kx = (a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt / dxb;
         double mx = 0.0, unused = 0.0;
         bool bad = false;
         float emax = 0.0f;
@@ -113,11 +114,12 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
             double r[NV];
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                const double L = -((sF[k * TI + c + 1] - sF[k * TI + c]) * rdx);   // Eq. (2)
-                const double ups = fma(dt, L, a.Us[k * a.total + gc]);
-                if (a.stage == 0) r[k] = ups;
-                else if (a.stage == 1) r[k] = fma(0.75, a.Un[k * a.total + gc], 0.25 * ups);
-                else r[k] = fma(1.0 / 3.0, a.Un[k * a.total + gc], (2.0 / 3.0) * ups);
+                const double dF = sF[k * TI + c + 1] - sF[k * TI + c];
+                const double us = a.Us[k * a.total + gc];
+                double base = us;
+                if (a.stage == 1) base = fma(0.75, a.Un[k * a.total + gc], 0.25 * us);
+                else if (a.stage == 2) base = fma(1.0 / 3.0, a.Un[k * a.total + gc], (2.0 / 3.0) * us);
+                r[k] = fma(-kx, dF, base);
                 a.out[k * a.total + gc] = r[k];
             }
             // the next stage's LF speed: estimate every cell, evaluate exactly only the cells
