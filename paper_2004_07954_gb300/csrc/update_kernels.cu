@@ -1,6 +1,6 @@
 // Cell-wise kernels: flux difference + SSP-RK3 stage update (with the next stage's LF
-// speeds folded in), the standalone LF-speed reduction, the single-line reconstruction and
-// the ghost-cell fill.
+// speeds folded in), the standalone LF-speed reduction, the single-line reconstruction, the
+// ghost-cell fill, and the FP64 rate probe behind wenozn_fp64_fma_rate.
 #include "launch.h"
 #include "speed_screen.cuh"
 
