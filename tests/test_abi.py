@@ -83,6 +83,34 @@ def test_null_and_bad_arguments_rejected(wz):
     assert L.wenozn_problem_init(None, 0, 1, 1, 1.0, 1.0) == wz.WENOZN_EINVAL
 
 
+def test_newer_entry_points_reject_bad_arguments_on_host(wz):
+    """The chained, keep/reverse, weight-variant and probe entry points check their arguments
+    before any CUDA call (so these run without a GPU)."""
+    L = wz.lib()
+    A = ctypes.c_void_p(256)                       # stand-in device addresses, never touched
+    p1 = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, 64, 1, 0.1, 0)
+    p2 = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 16, 16, 0.1, 0.1)
+    # chained run: no steps, non-finite dt, no state
+    assert L.wenozn_rk3_run(ctypes.byref(p1), A, 0, 0.0, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_run(ctypes.byref(p1), A, 4, float("nan"), A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_run(ctypes.byref(p1), None, 4, 0.0, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    # keep / reverse segments: 1D default scheme, positive finite dt, at least one step
+    for fn in (L.wenozn_rk3_run_keep,):
+        assert fn(ctypes.byref(p1), A, A, A, A, 0, 1e-3, A, 1 << 30, None) == wz.WENOZN_EINVAL
+        assert fn(ctypes.byref(p1), A, A, A, A, 3, 0.0, A, 1 << 30, None) == wz.WENOZN_EINVAL
+        assert fn(ctypes.byref(p2), A, A, A, A, 3, 1e-3, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_vjp_run(ctypes.byref(p1), A, A, A, A, 3, 1e-3, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_vjp_run(ctypes.byref(p2), A, A, A, A, 3, 1e-3, A, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    # weight variants: unknown weight function, bad side, non-positive eps
+    for weights, side, eps in ((4, 1, 1e-40), (-1, 1, 1e-40), (0, 2, 1e-40), (1, 1, 0.0)):
+        assert L.wenozn_reconstruct_weights(A, 10, A, side, weights, eps, 10.0, None) == wz.WENOZN_EINVAL
+    # FP64 rate probe: sizes outside [4, 2^32], no result pointer
+    g = ctypes.c_double(0.0)
+    for bad in (0, 3, (1 << 32) + 1):
+        assert L.wenozn_fp64_fma_rate(bad, ctypes.byref(g), None) == wz.WENOZN_EINVAL
+    assert L.wenozn_fp64_fma_rate(1 << 10, None, None) == wz.WENOZN_EINVAL
+
+
 def test_status_strings_and_version(wz):
     for code in range(6):
         assert wz.wenozn_status_string(code)
