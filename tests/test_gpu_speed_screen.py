@@ -132,6 +132,25 @@ def test_max_wavespeed_screen(wz, orc, kind, system, size):
         assert got[1] == orc.max_wavespeed(P, U, 1)
 
 
+@pytest.mark.parametrize("gamma", [1.1, 5.0 / 3.0, 3.0])
+@pytest.mark.parametrize("system", [1, 2])
+def test_screen_other_gammas(wz, orc, gamma, system):
+    """The estimate's bound does not depend on gamma (gamma (gamma - 1) enters rounded once)."""
+    nx, ny = (400_000, 1) if system == 1 else (640, 600)
+    U = field("near_tie", system, nx, ny, seed=21)
+    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / ny)
+    p.gamma = gamma
+    a = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wz.wenozn_max_wavespeed(p, dev(U), a, st)
+    P = orc_problem(orc, p)
+    got = a.cpu().numpy()
+    assert int(st.item()) == 0
+    assert got[0] == orc.max_wavespeed(P, U, 0)
+    if system == 2:
+        assert got[1] == orc.max_wavespeed(P, U, 1)
+
+
 @pytest.mark.parametrize("system", [1, 2])
 @pytest.mark.parametrize("bad", ["negative_pressure", "nan"])
 def test_screen_keeps_status(wz, orc, system, bad):
