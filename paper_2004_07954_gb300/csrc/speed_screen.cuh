@@ -56,6 +56,7 @@ __device__ __forceinline__ float momentum_f32(int hi, bool& ok) {
 
 struct SpeedEstimate {
     float sx, sy;   // estimates of |u| + c and |v| + c (0 where not ok)
+    float u, v, c;  // the estimates they come from (meaningful where ok)
     bool ok;        // the bound of the header holds for this cell
 };
 
@@ -78,7 +79,26 @@ __device__ __forceinline__ SpeedEstimate estimate_speeds(const double* s, float 
     est.ok = ok;
     est.sx = ok ? __fadd_rn(fabsf(u), c) : 0.0f;
     est.sy = ok && NV == 4 ? __fadd_rn(fabsf(v), c) : 0.0f;
+    est.u = u;
+    est.v = v;
+    est.c = c;
     return est;
+}
+
+// Per-field speeds |u - c|, |u|, |u + c| (and with v in 2D).  Where the estimate is ok, each
+// is within delta (|u| + c) (delta = 1.8e-5, as above) of the FP64 value: u and c carry at most
+// that relative error and the two subtractions round once each.  So against the running
+// maximum M_k of such estimates, the cell attaining the exact maximum of field k always lies
+// within 2 delta S of M_k, S the largest |u| + c (|v| + c) of the cells seen; the screen's
+// window for the fields is tau max(M_x, M_y) >= 2 delta S.
+template <int NV>
+__device__ __forceinline__ void estimate_field_speeds(const SpeedEstimate& e, float* f) {
+    f[0] = e.ok ? fabsf(__fsub_rn(e.u, e.c)) : 0.0f;
+    f[1] = e.ok ? fabsf(e.u) : 0.0f;
+    f[2] = e.ok ? fabsf(__fadd_rn(e.u, e.c)) : 0.0f;
+    f[3] = e.ok && NV == 4 ? fabsf(__fsub_rn(e.v, e.c)) : 0.0f;
+    f[4] = e.ok && NV == 4 ? fabsf(e.v) : 0.0f;
+    f[5] = e.ok && NV == 4 ? fabsf(__fadd_rn(e.v, e.c)) : 0.0f;
 }
 
 __device__ __forceinline__ float warp_max_f(float v) {
@@ -87,28 +107,26 @@ __device__ __forceinline__ float warp_max_f(float v) {
     return v;
 }
 
-// Running block-wide maxima of the estimates over the batches of T cells a block processes
+// Running block-wide maxima of N estimates over the batches of T cells a block processes
 // (one barrier per batch; two buffers, so a batch's reads never race the next batch's
 // writes).  Every thread of the block must call add() the same number of times.
-template <int T>
+template <int T, int N = 2>
 struct ScreenMax {
-    float mx = 0.0f, my = 0.0f;
+    float m[N] = {};
     int parity = 0;
-    __device__ __forceinline__ void add(float ex, float ey) {
-        __shared__ float red[2][2][T / 32];
+    __device__ __forceinline__ void add(const float* e) {
+        __shared__ float red[2][N][T / 32];
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        ex = warp_max_f(ex);
-        ey = warp_max_f(ey);
-        if (lane == 0) {
-            red[parity][0][w] = ex;
-            red[parity][1][w] = ey;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const float v = warp_max_f(e[q]);
+            if (lane == 0) red[parity][q][w] = v;
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < T / 32; ++k) {
-            mx = fmaxf(mx, red[parity][0][k]);
-            my = fmaxf(my, red[parity][1][k]);
-        }
+        for (int k = 0; k < T / 32; ++k)
+#pragma unroll
+            for (int q = 0; q < N; ++q) m[q] = fmaxf(m[q], red[parity][q][k]);
         parity ^= 1;
     }
 };

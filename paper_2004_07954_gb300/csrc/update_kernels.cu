@@ -37,7 +37,8 @@ __device__ __forceinline__ double step_dt(const UpdateArgs& a, int system) {
     return dt;
 }
 
-template <int NV, int T>
+// FIELDS: also the per-field speeds (per-field LF splitting), under the same screen
+template <int NV, int T, bool FIELDS>
 __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs a) {
     pdl_wait();
     const int system = NV == 1 ? 0 : (NV == 3 ? 1 : 2);
@@ -63,9 +64,9 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
     const bool speeds = NV != 1 && a.mode != 0 && (a.next_slot >= 0 || a.alpha_next || a.mode == 3);
     // (64-thread blocks, used for small grids, hold two warps: one of them nearly always
     // holds the block's candidate, so they skip the screen)
-    const bool screen = T >= 128 && speeds && !a.field_speeds;
+    const bool screen = T >= 128 && speeds;
     const float gg1 = __double2float_rn(a.gamma * (a.gamma - 1.0));
-    ScreenMax<T> smax;
+    ScreenMax<T, FIELDS ? 8 : 2> smax;
     // the last state this thread evaluated exactly and its speeds: a bit-identical state
     // (constant regions) reuses them
     double cs[NV];
@@ -114,13 +115,24 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
         } else if (speeds) {
             bool exact = valid;
             if (screen) {
-                const SpeedEstimate est = valid ? estimate_speeds<NV>(o, gg1) : SpeedEstimate{0.0f, 0.0f, true};
-                smax.add(est.sx, est.sy);
-                exact = valid && (!est.ok || est.sx >= smax.mx * kScreenKeep ||
-                                  (NV == 4 && est.sy >= smax.my * kScreenKeep));
+                SpeedEstimate est{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, true};
+                if (valid) est = estimate_speeds<NV>(o, gg1);
+                float e[FIELDS ? 8 : 2];
+                e[0] = est.sx;
+                e[1] = est.sy;
+                if constexpr (FIELDS) estimate_field_speeds<NV>(est, e + 2);
+                smax.add(e);
+                bool cand = !est.ok || est.sx >= smax.m[0] * kScreenKeep ||
+                            (NV == 4 && est.sy >= smax.m[1] * kScreenKeep);
+                if constexpr (FIELDS) {
+                    const float win = (1.0f - kScreenKeep) * fmaxf(smax.m[0], smax.m[1]);
+#pragma unroll
+                    for (int q = 2; q < (NV == 4 ? 8 : 5); ++q) cand = cand || e[q] >= smax.m[q] - win;
+                }
+                exact = valid && cand;
             }
             if (exact) {
-                bool same = screen && cached;
+                bool same = screen && cached;     // (a cached state's speeds are folded in already)
 #pragma unroll
                 for (int k = 0; k < NV; ++k) same = same && __double_as_longlong(o[k]) == __double_as_longlong(cs[k]);
                 if (!same) {
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
 #pragma unroll
                     for (int k = 0; k < NV; ++k) cs[k] = o[k];
                     cached = true;
-                    if (a.field_speeds) {
+                    if (FIELDS) {
                         double f[3];
                         field_speeds(u, c, f);
                         for (int k = 0; k < 3; ++k) fmx[k] = fmax(fmx[k], f[k]);
@@ -157,7 +169,7 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
         block_max2_atomic(mx, my, a.alpha_next, NV != 4);
     } else if (NV != 1 && a.next_slot >= 0) {
         block_max2_atomic(mx, my, a.ctrl->alpha[a.next_slot]);
-        if (a.field_speeds) block_max_n_atomic<6>(fmx, &a.ctrl->alpha_f[a.next_slot][0][0]);
+        if (FIELDS) block_max_n_atomic<6>(fmx, &a.ctrl->alpha_f[a.next_slot][0][0]);
     }
 }
 
@@ -183,10 +195,12 @@ __global__ void __launch_bounds__(T) max_wavespeed_kernel(const double* U, int64
         for (int k = 0; k < NV; ++k) s[k] = valid ? U[k * nc + cell] : 0.0;
         bool exact = valid;
         if (screen) {
-            const SpeedEstimate est = valid ? estimate_speeds<NV>(s, gg1) : SpeedEstimate{0.0f, 0.0f, true};
-            smax.add(est.sx, est.sy);
-            exact = valid && (!est.ok || est.sx >= smax.mx * kScreenKeep ||
-                              (NV == 4 && est.sy >= smax.my * kScreenKeep));
+            SpeedEstimate est{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, true};
+            if (valid) est = estimate_speeds<NV>(s, gg1);
+            const float e[2] = {est.sx, est.sy};
+            smax.add(e);
+            exact = valid && (!est.ok || est.sx >= smax.m[0] * kScreenKeep ||
+                              (NV == 4 && est.sy >= smax.m[1] * kScreenKeep));
         }
         if (!exact) continue;
         bool same = screen && cached;
@@ -318,12 +332,14 @@ int resident_blocks(void (*kern)(KArgs...), int threads) {
     return n;
 }
 
-template <int NV>
+template <int NV, bool FIELDS>
 void update_nv(const UpdateArgs& a, int64_t nc, cudaStream_t s) {
     const int sms = sm_count();
-    static const int occ = resident_blocks(update_kernel<NV, kThreads>, kThreads);
-    if (few_cells(nc, sms)) launch_pdl(update_kernel<NV, 64>, dim3(grid_for(nc, sms * 32, 64)), dim3(64), 0, s, a);
-    else launch_pdl(update_kernel<NV, kThreads>, dim3(grid_for(nc, sms * occ)), dim3(kThreads), 0, s, a);
+    static const int occ = resident_blocks(update_kernel<NV, kThreads, FIELDS>, kThreads);
+    if (few_cells(nc, sms))
+        launch_pdl(update_kernel<NV, 64, FIELDS>, dim3(grid_for(nc, sms * 32, 64)), dim3(64), 0, s, a);
+    else
+        launch_pdl(update_kernel<NV, kThreads, FIELDS>, dim3(grid_for(nc, sms * occ)), dim3(kThreads), 0, s, a);
 }
 
 template <int NV>
@@ -340,9 +356,9 @@ void max_wavespeed_nv(const double* U, int64_t nc, double gamma, unsigned long l
 
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
     const int64_t nc = int64_t(a.nx) * a.ny;
-    if (system == 0) update_nv<1>(a, nc, s);
-    else if (system == 1) update_nv<3>(a, nc, s);
-    else update_nv<4>(a, nc, s);
+    if (system == 0) update_nv<1, false>(a, nc, s);
+    else if (system == 1) a.field_speeds ? update_nv<3, true>(a, nc, s) : update_nv<3, false>(a, nc, s);
+    else a.field_speeds ? update_nv<4, true>(a, nc, s) : update_nv<4, false>(a, nc, s);
     return cudaGetLastError();
 }
 

@@ -207,6 +207,41 @@ def test_stage_speeds_screen(wz, orc, kind, system, nx, ny):
             assert raw[s, 1] == orc.max_wavespeed(P, Us, 1), f"stage {s} y"
 
 
+FIELD_CASES = [("four_quadrant", 2, 700, 500), ("planted", 2, 640, 600), ("near_tie", 2, 500, 400),
+               ("shu_osher", 1, 1 << 20, 1), ("near_tie", 1, 400_000, 1), ("tiny_momentum", 1, 300_000, 1),
+               ("constant_one_up", 2, 600, 600)]
+
+
+@pytest.mark.parametrize("kind,system,nx,ny", FIELD_CASES)
+def test_stage_field_speeds_screen(wz, orc, kind, system, nx, ny):
+    """Per-field LF splitting: the update kernel's screened per-field maxima |u-c|, |u|, |u+c|
+    (and with v) of U^(1), U^(2) are the exact maxima over those states."""
+    if kind == "four_quadrant":
+        U = inputs.euler2d_ic(nx, ny, seed=6)
+    elif kind == "shu_osher":
+        U = inputs.euler1d_ic(nx, seed=6)
+    else:
+        U = field(kind, system, nx, ny, seed=8)
+    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / ny)
+    p.split = wz.WENOZN_SPLIT_LF_FIELD
+    S = wz.Solver(p)
+    t = dev(U)
+    S.step(t)
+    torch.cuda.synchronize()
+    assert S.status() == 0
+    U1, U2, A = wz.workspace_stages(p, S.ws)
+    off = A.data_ptr() - S.ws.data_ptr()
+    raw = S.ws[off:off + 48 + 144].view(torch.float64).cpu().numpy()
+    af = raw[6:].reshape(3, 2, 3)
+    P = orc_problem(orc, p)
+    P.split = p.split
+    for slot, Us in ((1, U1.cpu().numpy()), (2, U2.cpu().numpy())):
+        assert raw[2 * slot] == orc.max_wavespeed(P, Us, 0)
+        for d in range(2 if system == 2 else 1):
+            for k in range(3):
+                assert af[slot, d, k] == orc.field_speed(P, Us, d, k), (slot, d, k)
+
+
 @pytest.mark.parametrize("system,nx,ny", [(2, 700, 500), (1, 1 << 20, 1)])
 def test_chained_step_dt_screen(wz, orc, system, nx, ny):
     """In a chained run the last stage's screened speeds give the next step's CFL dt."""
