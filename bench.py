@@ -654,11 +654,21 @@ def main():
            "d2h_bytes_per_step": nbytes, "steps": ke,
            "copies": "pinned host <-> device on one stream per direction, overlapped with the previous/next step"}
 
-    batched = None if args.no_batched else bench_batched(wenozn, inputs, args.seed + rank, args.batched_steps)
-    euler1d = None if args.no_euler1d else bench_euler1d(wenozn, inputs, args.seed + rank)
-    variants = None if args.no_variants else bench_variants(wenozn, inputs, args.seed + rank, n)
-    adjoint = None if args.no_adjoint else bench_adjoint(wenozn, inputs, args.seed + rank,
-                                                         steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
+    def part(skip, fn, *a, **kw):
+        """A secondary measurement; its failure is reported in its own object, the headline
+        line is printed regardless."""
+        if skip:
+            return None
+        try:
+            return fn(*a, **kw)
+        except Exception as exc:          # noqa: BLE001 - recorded, not hidden
+            return {"error": f"{type(exc).__name__}: {exc}"[:300]}
+
+    batched = part(args.no_batched, bench_batched, wenozn, inputs, args.seed + rank, args.batched_steps)
+    euler1d = part(args.no_euler1d, bench_euler1d, wenozn, inputs, args.seed + rank)
+    variants = part(args.no_variants, bench_variants, wenozn, inputs, args.seed + rank, n)
+    adjoint = part(args.no_adjoint, bench_adjoint, wenozn, inputs, args.seed + rank,
+                   steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
