@@ -214,6 +214,34 @@ def test_rk3_run_equals_repeated_steps(wz, system, nx, ny, split):
         assert S.status() == 0
 
 
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_large_1d_step_parity(wz, orc, bc):
+    """A 1D grid on the large-grid kernels (512-interface flux tiles, 256-thread update
+    blocks): one step against the oracle for every boundary, with a ragged last tile, CFL,
+    clipped and fixed steps, and the chained run equal to repeated steps."""
+    n = 200_000                                      # 390 full flux tiles + 321 interfaces
+    U0 = inputs.euler1d_ic(n, seed=9)
+    if bc == 2:
+        U0 = U0.copy()
+        U0[1] *= 0.0                                 # at rest next to the walls
+    p = gpu_problem(wz, 1, n, dx=10.0 / n, bc=bc)
+    P = orc_problem(orc, p)
+    for dt, trem in ((0.0, 0.0), (0.0, 1e-6), (2e-5, 0.0)):
+        S = wz.Solver(p)
+        t = dev(U0)
+        got = S.step(t, dt=dt, t_remaining=trem, return_dt=True)
+        want, used = orc.rk3_step(P, U0, dt, trem)
+        assert got == used
+        assert rel_linf(host(t), want) <= STEP_TOL
+        assert S.status() == 0
+    S = wz.Solver(p)
+    a, b = dev(U0), dev(U0)
+    for _ in range(3):
+        S.step(a)
+    S.steps(b, 3)
+    assert torch.equal(a, b)
+
+
 def test_rk3_fixed_and_clipped_dt(wz, orc):
     n = 300
     U = inputs.euler1d_ic(n, seed=2)
