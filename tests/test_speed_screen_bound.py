@@ -27,6 +27,24 @@ def in_range(x):
     return (x >= 2.0 ** -30) & (x < 2.0 ** 30)
 
 
+def estimate_parts(U):
+    """(ok, u, v, c) of the single-precision estimate."""
+    rho, m, E = U[0], U[1], U[-1]
+    n = U[2] if U.shape[0] == 4 else np.zeros_like(rho)
+    ok = in_range(rho) & in_range(E) & (np.abs(m) < 2.0 ** 30) & (np.abs(n) < 2.0 ** 30)
+    with np.errstate(all="ignore"):
+        mf = np.where(np.abs(m) < 2.0 ** -100, np.float32(0), trunc20(m))
+        nf = np.where(np.abs(n) < 2.0 ** -100, np.float32(0), trunc20(n))
+        rf, Ef = trunc20(rho), trunc20(E)
+        r = np.float32(1) / rf
+        u, v = mf * r, nf * r
+        kin = np.float32(0.5) * (mf * u + nf * v)
+        e = Ef - kin
+        ok &= e >= np.float32(0.125) * Ef
+        c = np.sqrt(np.float32(GAMMA * (GAMMA - 1.0)) * e * r)
+    return ok, u, v, c
+
+
 def estimate(U):
     rho, m, E = U[0], U[1], U[-1]
     n = U[2] if U.shape[0] == 4 else np.zeros_like(rho)
@@ -91,6 +109,25 @@ def test_estimate_within_delta(two_d, seed):
     kin = (0.5 * rho) * ((m / rho) ** 2 + ((U[2] / rho) ** 2 if two_d else 0.0))
     assert np.all(((GAMMA - 1.0) * (E - kin))[ok] > 0.0)
     assert np.all(np.isfinite(sx[ok]))
+
+
+@pytest.mark.parametrize("two_d", [False, True])
+def test_field_estimates_within_delta_of_the_lf_speed(two_d):
+    """Per-field speeds |u-c|, |u|, |u+c|: each estimate is within delta (|u| + c) of the
+    FP64 value (the window of the per-field screen is relative to the LF speed)."""
+    U = states(11, 400_000, two_d)
+    ok, uf, vf, cf = estimate_parts(U)
+    rho, m, E = U[0], U[1], U[-1]
+    u = m / rho
+    v = U[2] / rho if two_d else np.zeros_like(u)
+    kin = (0.5 * rho) * (u * u + v * v)
+    c = np.sqrt(GAMMA * ((GAMMA - 1.0) * (E - kin)) / rho)
+    with np.errstate(all="ignore"):
+        for w, wf in ((u, uf), (v, vf)):
+            s = np.abs(w) + c
+            for exact, est in ((np.abs(w - c), np.abs(wf - cf)), (np.abs(w), np.abs(wf)), (np.abs(w + c), np.abs(wf + cf))):
+                err = np.abs(est.astype(np.float64) - exact)[ok] / s[ok]
+                assert err.max() <= DELTA, err.max()
 
 
 def test_window_covers_twice_delta():
