@@ -422,17 +422,19 @@ __global__ void __launch_bounds__(3 * kGatherCells) vjp_gather_euler(VjpArgs a) 
         }
     }
     sF[m][lane] = Fs;
+    double rho = 1.0, mom = 0.0, E = 0.0;
+    if (i < n) {                                 // the cell's state, loaded before the barrier
+        rho = a.U[i];
+        mom = a.U[n + i];
+        E = a.U[2 * int64_t(n) + i];
+    }
     __syncthreads();
     double Ub = 0.0;
-    double rho = 1.0, mom = 0.0, E = 0.0;
     if (i < n) {
         const double F0 = sF[0][lane], F1 = sF[1][lane], F2 = sF[2][lane];
         const double alpha = __longlong_as_double((long long)a.alpha_bits[0]);
         const double gm1 = a.gamma - 1.0;
-        rho = a.U[i];
-        mom = a.U[n + i];
-        E = a.U[2 * int64_t(n) + i];
-        const double r = 1.0 / rho, u = mom * r;
+        const double r = rcp_nr(rho), u = mom * r;
         const double p = gm1 * (E - 0.5 * mom * u);
         const double Ep = E + p;
         // F = (mom, mom u + p, u (E + p)), u = mom/rho, p = (gamma-1)(E - mom u/2)
