@@ -127,12 +127,16 @@ struct EulerSmem {
 
 __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
     __shared__ EulerSmem sm;
-    pdl_wait();
+    // Inside a chain the launch before is the previous stage's gather, which writes lam and
+    // the control words only: the cell phase, the Roe state and the projections (from U and
+    // alpha, written long before) then overlap its tail, and the wait comes before lam is read.
+    if (!a.early) pdl_wait();
     const int n = a.n, j0 = blockIdx.x * kTI, tid = threadIdx.x;
     const int64_t P = int64_t(n) + 1;
     const double gm1 = a.gamma - 1.0;
     const unsigned long long abits = a.alpha_bits[0];
     const double alpha = __longlong_as_double((long long)abits);
+    int cand = -1;                               // this thread's LF-argmax candidate cell
     for (int c = tid; c < kCells; c += 3 * kTI) {
         const int g = j0 - 3 + c;
         const int src = ghost_src(g, n, a.bc);
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         if (g == src && c >= 3 && c < 3 + kTI) {   // a grid cell of this block: is it the LF argmax?
             double sx, sy;
             wave_speeds<3>(s, a.gamma, sx, sy);
-            if ((unsigned long long)__double_as_longlong(sx) == abits) atomicMax(&a.ctl[0], ~unsigned(g));
+            if ((unsigned long long)__double_as_longlong(sx) == abits) cand = g;
         }
     }
     __syncthreads();
@@ -166,6 +170,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
     const bool live = j <= n;
     const int cl = i + 2, cr = i + 3;            // cells j-1, j
     double ut = 0, Ht = 0, c = 0, rc = 0, b1 = 0, wl = 0, wr = 0, rS = 0;
+    double L0 = 0, L1 = 0, L2 = 0, R1 = 0, R2 = 0;
+    double fp[5] = {}, fm[5] = {};
     if (live) {
         // Roe state and row k of L, column k of R (R[0][k] = 1)
         const double sl = sm.sq[cl], sr = sm.sq[cr];
@@ -179,7 +185,6 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         c = c2 * rc;
         b1 = gm1 * rc * rc;
         const double b2 = 0.5 * ut * ut * b1;
-        double L0, L1, L2, R1, R2;
         if (k == 0) {
             L0 = 0.5 * fma(ut, rc, b2); L1 = -0.5 * fma(b1, ut, rc); L2 = 0.5 * b1;
             R1 = ut - c; R2 = fma(-ut, c, Ht);
@@ -190,6 +195,16 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             L0 = 0.5 * fma(-ut, rc, b2); L1 = -0.5 * fma(b1, ut, -rc); L2 = 0.5 * b1;
             R1 = ut + c; R2 = fma(ut, c, Ht);
         }
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
+            fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
+        }
+    }
+    if (a.early) pdl_wait();                     // lam and the control words are read from here on
+    if (cand >= 0) atomicMax(&a.ctl[0], ~unsigned(cand));
+    if (live) {
+        double fpb[5], fmb[5];
         double Fb[3];
         for (int m = 0; m < 3; ++m) {
             const double right = j < n ? a.lam[int64_t(m) * n + j] : 0.0;
@@ -197,12 +212,6 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             Fb[m] = (right - left) * a.rdx;
         }
         const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
-        double fp[5], fm[5], fpb[5], fmb[5];
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
-            fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
-        }
         const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, a.fast_rcp, fpb) +
                           zn_vjp(fm, ghb, a.eps4, a.kappa, a.fast_rcp, fmb);
         double Lb[3] = {0, 0, 0};

@@ -122,6 +122,9 @@ struct VjpArgs {
     const double* X3;
     double c1, c2, c3, d;
     int n, bc, fast_rcp, nblocks;          // nblocks = vjp_partial_count(n)
+    int early;                             // the launch before is this chain's gather: work that reads
+                                           // neither lam nor the control words runs before the
+                                           // programmatic-dependence wait
     double rdx, gamma, eps4, kappa, adv_speed;
 };
 int vjp_partial_count(int n);
