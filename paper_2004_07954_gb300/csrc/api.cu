@@ -140,6 +140,7 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     if (dir != 0 && !(dir == 1 && p->system == WENOZN_EULER_2D)) return WENOZN_EINVAL;
     FluxArgs fa;
     fa.U = U;
+    fa.after_x = 0;
     fa.alpha_bits = reinterpret_cast<const unsigned long long*>(alpha);
     fa.alpha_f_bits = alpha ? fa.alpha_bits + 2 : nullptr;
     fa.weights = p->weights;

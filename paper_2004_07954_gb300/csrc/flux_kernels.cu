@@ -37,7 +37,12 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     constexpr int NC = CL * TA;           // cells per tile
     extern __shared__ double smem[];
     const CellPlanes<NV> sp(smem, NC);
-    pdl_wait();
+    // The y sweep of a stage follows the x sweep, which writes only the x fluxes: it starts
+    // at once (its inputs, from the launches before, are complete once the x sweep's blocks
+    // have started), and waits for the x sweep only before it ends, so that whatever follows
+    // the y sweep also finds the x fluxes complete.
+    const bool overlap = DIR == 1 && a.after_x;
+    if (!overlap) pdl_wait();
 
     const int n = DIR == 0 ? a.nx : a.ny;           // cells along the sweep
     const int nlines = DIR == 0 ? a.ny : a.nx;
@@ -106,6 +111,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
             a.Fout[3 * stride + base] = Fh[3];
         }
     }
+    if (overlap) pdl_wait();
 }
 
 template <int NV, int DIR, bool SMALL, bool GEN>

@@ -86,6 +86,7 @@ inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsign
     fa.adv_speed = p.adv_speed;
     fa.Fout = nullptr;
     fa.bc = p.bc_x;
+    fa.after_x = 0;
     return fa;
 }
 
@@ -100,6 +101,7 @@ inline cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const
     if (e != cudaSuccess || p.system != WENOZN_EULER_2D) return e;
     fa.Fout = gy;
     fa.bc = p.bc_y;
+    fa.after_x = 1;
     return launch_flux(p.system, 1, fa, s);
 }
 

@@ -39,6 +39,8 @@ struct FluxArgs {
     int nx, ny, bc;                        // bc of the sweep direction (0 periodic, 1 outflow, 2 reflective)
     int fast_rcp;                          // 1: Newton reciprocal for f^ = num/den (see zn_flux)
     int weights, split;                    // weight function and flux splitting (wenozn.h enums)
+    int after_x;                           // y sweep launched right after the x sweep of the same
+                                           // stage input: it reads nothing that sweep writes
     double eps4, kappa, gamma, adv_speed;  // eps4 = 4 eps, kappa = 2 / sqrt(A) (see zn_parts)
 };
 // Whether the reconstruction's common denominator is guaranteed positive and normal, so the

@@ -90,6 +90,7 @@ extern "C" wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const doubl
                                  &ctrl->status, s, per_field ? &ctrl->alpha_f[0][0][0] : nullptr);
     FluxArgs fa;
     fa.U = U;
+    fa.after_x = 0;
     fa.alpha_bits = ctrl->alpha[0];
     fa.alpha_f_bits = &ctrl->alpha_f[0][0][0];
     fa.weights = p->weights;
