@@ -40,8 +40,8 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "8e7724a3466dd1fd", "n": 4096, "bytes": 965.4e6,
-                   "fp64_pipe": {"x": 0.886, "y": 0.887}}   # ncu FP64-pipe busy, same capture
+TRAFFIC_CAPTURE = {"sha256_16": "bf926e69f14cafd5", "n": 4096, "bytes": 965.7e6,
+                   "fp64_pipe": {"x": 0.888, "y": 0.889}}   # ncu FP64-pipe busy, same capture
 
 
 def hbm_peak() -> tuple:
