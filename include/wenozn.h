@@ -131,7 +131,10 @@ wenozn_status wenozn_reconstruct_weights(const double* f_padded, int64_t n, doub
 /* Global Lax-Friedrichs speeds (Sec. 4.3 / 4.4): alpha_out[0] = max_ij(|u| + c),
  * alpha_out[1] = max_ij(|v| + c) (2D; 0 otherwise); |a| for advection.  With the per-field
  * splitting also alpha_out[2..4] = max |u - c|, max |u|, max |u + c| and alpha_out[5..7] the
- * same with v (2D; 0 otherwise).
+ * same with v (2D; 0 otherwise).  The maxima are those of the per-cell speeds evaluated with
+ * IEEE operations in the order u = m/rho, p = (gamma-1)(E - rho u^2/2), c = sqrt(gamma p/rho)
+ * (bit-identical whatever the grid's decomposition; a single-precision estimate with a
+ * proven error bound only decides which cells need that evaluation).
  *   U         : device state [nvar][ny][nx].
  *   alpha_out : device, 2 doubles (8 with the per-field splitting), overwritten.
  *   status_dev: device int32 status word or NULL; a NaN/Inf, rho <= 0 or p <= 0 ORs
