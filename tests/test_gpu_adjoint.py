@@ -165,6 +165,35 @@ def test_chained_keep_and_reverse_equal_the_single_steps(wz):
     assert torch.equal(l1, l2)
 
 
+def test_chained_reverse_is_repeatable_at_the_benchmark_size(wz):
+    """N = 8192, 150 steps: inside a chain the interface kernels start before the previous
+    gather has finished (only lam-free work runs before their wait).  Three runs of the
+    chained reverse and the step-by-step reverse (each step's first stage waits first) agree
+    bit for bit."""
+    n, m = 8192, 150
+    p = wz.wenozn_problem_init(1, n, 1, 10.0 / n, 1.0, bc_x=0)
+    U0 = dev(inputs.adjoint_ic(n, seed=3))
+    dt = 0.4 * p.dx
+    ws = wz.vjp_workspace(p)
+    X = torch.empty((m + 1,) + tuple(U0.shape), dtype=torch.float64, device="cuda")
+    S1, S2 = torch.empty_like(X[:m]), torch.empty_like(X[:m])
+    A = torch.empty(3 * m + 1, dtype=torch.float64, device="cuda")
+    X[0].copy_(U0)
+    wz.wenozn_rk3_run_keep(p, X, S1, S2, A, m, dt, ws)
+    lam0 = dev(np.random.default_rng(5).normal(size=tuple(U0.shape)))
+    runs = []
+    for _ in range(3):
+        lam = lam0.clone()
+        wz.wenozn_rk3_vjp_run(p, X, S1, S2, A, m, dt, lam, ws)
+        runs.append(lam)
+    step = lam0.clone()
+    for k in reversed(range(m)):
+        wz.wenozn_rk3_step_vjp_stages(p, X[k], S1[k], S2[k], A[3 * k:3 * k + 3], dt, step, ws)
+    for r in runs:
+        assert torch.equal(r, runs[0])
+    assert torch.equal(step, runs[0])
+
+
 def _loss_grad(wz, p, U0, dt, steps, target, every=1):
     from paper_2004_07954_gb300.rollout import rollout
     U = dev(U0).requires_grad_(True)
