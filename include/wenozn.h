@@ -22,6 +22,17 @@
  *    anything.  Launch failures return WENOZN_ECUDA.  Conditions detected on the device
  *    (non-finite values, rho <= 0 or p <= 0) set bits in the workspace status word, read
  *    with wenozn_workspace_status; the kernels never trap.
+ *  - Range of the reconstruction.  The weights are evaluated division-free (their common
+ *    denominator is a fifth-degree product of the smoothness indicators).  When that
+ *    product leaves the double range (stencil differences above about 1e26, or data far
+ *    below the scale of eps), the weights are evaluated again on the stencil scaled by an
+ *    exact power of two, which is exact algebra.  With the admissible constants
+ *    (1e-60 <= eps <= 1, 1e-6 <= A <= 1e6; other values return WENOZN_EINVAL) every
+ *    reconstruction is therefore finite and accurate to rounding for stencils whose first
+ *    differences stay below 2^440 (about 2.8e132) in magnitude; for Euler these are the
+ *    differences of the split characteristic fluxes.  Beyond that bound (where the plain
+ *    evaluation of Eq. (new) itself overflows: tau8 / eps exceeds the double range) results
+ *    may be non-finite, which the stepping calls report as WENOZN_ENONFINITE.
  */
 #ifndef WENOZN_H
 #define WENOZN_H
@@ -82,8 +93,8 @@ typedef struct {
     int32_t flags;           /* reserved, 0                                    */
     double dx, dy;           /* uniform spacing (> 0; dy ignored in 1D)        */
     double gamma;            /* ratio of specific heats (Euler)                */
-    double eps;              /* epsilon of Eq. (function) / Eq. (new)          */
-    double A;                /* constant A of Eq. (function), > 0              */
+    double eps;              /* epsilon of Eq. (function) / Eq. (new), 1e-60 .. 1 */
+    double A;                /* constant A of Eq. (function), 1e-6 .. 1e6      */
     double cfl;              /* CFL number sigma of the time-step formulas     */
     double adv_speed;        /* advection speed a (advection only)             */
 } wenozn_problem;
@@ -119,7 +130,9 @@ wenozn_status wenozn_fill_ghosts(const wenozn_problem* p, double* U_padded, void
  *   side     : +1 for f^+_{j-1/2} (stencil f_{j-3..j+1}); -1 for f^-_{j-1/2}, the same
  *              formula applied to the mirrored stencil (f_{j+2}, f_{j+1}, f_j, f_{j-1},
  *              f_{j-2}) (Sec. 2: "symmetric rule about x_{i+1/2}").
- *   eps, A   : Eq. (function) / (new) constants (eps > 0, A > 0). */
+ *   eps, A   : Eq. (function) / (new) constants, 1e-60 <= eps <= 1 and 1e-6 <= A <= 1e6
+ *              (WENOZN_EINVAL otherwise).  Finite and accurate for stencils whose first
+ *              differences stay below 2^440 (see "Range of the reconstruction" above). */
 wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat, int32_t side,
                                  double eps, double A, void* stream);
 
@@ -161,7 +174,9 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
  * with global LF flux splitting (alpha of this U), Roe-averaged characteristic fields
  * (Euler) and WENO-ZN reconstruction of both split parts, ghost cells by index map.
  *   U, L : device, [nvar][ny][nx]; L is overwritten; U and L must not overlap.
- *   ws   : device workspace of ws_bytes >= wenozn_workspace_size. */
+ *   ws   : device workspace of ws_bytes >= wenozn_workspace_size.
+ * A non-finite input state, rho <= 0, p <= 0, or a non-finite value of L (a stencil beyond
+ * the reconstruction's range) sets WENOZN_ENONFINITE in the workspace status word. */
 wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, void* ws,
                          size_t ws_bytes, void* stream);
 
@@ -173,11 +188,13 @@ wenozn_status wenozn_rhs(const wenozn_problem* p, const double* U, double* L, vo
  * Scratch comes from one 8 MiB array in the library's device memory, held on every GPU that
  * loads the library until the process exits.  Problems that need more (2D Euler beyond about
  * 131,000 cells, 1D Euler beyond about 349,000, advection beyond about 1,048,000) return
- * WENOZN_ENOMEM_WS.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture on that device.  All
- * calls share the array and each clears what must start at zero; calls whose GPU work
- * overlaps (unordered streams) race and give wrong results.  Device-detected conditions
- * (non-finite values, rho <= 0, p <= 0) are not reported.  Allocates nothing. */
+ * WENOZN_ENOMEM_WS.  Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so it stays valid across a device reset;
+ * the first call on a device also loads the library's device code there and should come
+ * before any stream capture on that device.  All calls share the array and each clears what
+ * must start at zero; calls whose GPU work overlaps (unordered streams) race and give wrong
+ * results.  Device-detected conditions (non-finite values, rho <= 0, p <= 0) are not
+ * reported, neither here nor through wenozn_last_error.  Allocates nothing. */
 wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const double* U, double* L, void* stream);
 
 /* One third-order TVD Runge-Kutta step (Shu & Osher, cited in Sec. 4), in place:
@@ -224,7 +241,7 @@ wenozn_status wenozn_workspace_status(void* ws, int32_t* status, int32_t clear, 
 
 /* Synchronises `stream` and returns in *device_status the device status bits (as
  * wenozn_workspace_status reports them) raised in the control block that the most recent
- * stepping call on `stream` used (wenozn_rhs, wenozn_rhs_noalloc, wenozn_rk3_step, wenozn_rk3_run,
+ * stepping call on `stream` used (wenozn_rhs, wenozn_rk3_step, wenozn_rk3_run,
  * wenozn_rk3_step_keep, wenozn_rhs_vjp, wenozn_rk3_step_vjp, wenozn_batch_rk3_step), then
  * clears them; 0 when nothing ran on the stream.  That workspace must still be allocated. */
 wenozn_status wenozn_last_error(void* stream, int32_t* device_status);
@@ -235,6 +252,9 @@ wenozn_status wenozn_last_error(void* stream, int32_t* device_status);
  * non-smooth points: the global LF speed alpha = max_i(|u_i| + c_i) is differentiated
  * through its argmax cell (the lowest index on ties), d|x|/dx = 0 at x = 0 (in |u| and in
  * tau5 = |IS_0 - IS_2| of Eq. (tau)), and the time step of an RK3 step is a fixed input.
+ * The adjoint kernels evaluate the weights without the rescaled fallback: their products
+ * are exact for stencil differences between about 1e-100 and 1e25 in magnitude (with the
+ * default eps = 1e-40), which covers physical Euler states by a wide margin.
  * --------------------------------------------------------------------------------------- */
 
 /* Workspace bytes of wenozn_rhs_vjp / wenozn_rk3_step_vjp: the forward workspace of

@@ -72,6 +72,8 @@ def lib():
                 "oracle_weno5_parts": (None, [_D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
                 "oracle_reconstruct": (None, [_D, ctypes.c_int64, _D, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int]),
+                "oracle_reconstruct_quad": (None, [_D, ctypes.c_int64, _D, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_int]),
                 "oracle_critical_point_error": (ctypes.c_double, [ctypes.c_int, ctypes.c_double,
                                                                   ctypes.c_int, ctypes.c_double, ctypes.c_int]),
                 "oracle_fill_ghosts_line": (None, [_D, ctypes.c_int64, ctypes.c_int]),
@@ -140,6 +142,15 @@ def reconstruct(f_padded, side=+1, eps=1e-40, A=10.0, kind=W_ZN) -> np.ndarray:
     n = f.shape[0] - 6
     out = np.zeros(n + 1)
     lib().oracle_reconstruct(_ptr(f), n, _ptr(out), int(side), eps, A, kind)
+    return out
+
+
+def reconstruct_quad(f_padded, side=+1, eps=1e-40, A=10.0, kind=W_ZN) -> np.ndarray:
+    """`reconstruct` evaluated in binary128 and rounded to double (no overflow for any input)."""
+    f = _f64(f_padded)
+    n = f.shape[0] - 6
+    out = np.zeros(n + 1)
+    lib().oracle_reconstruct_quad(_ptr(f), n, _ptr(out), int(side), eps, A, kind)
     return out
 
 

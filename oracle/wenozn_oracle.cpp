@@ -686,6 +686,21 @@ void oracle_reconstruct(const double* f_padded, int64_t n, double* fhat, int sid
     }
 }
 
+// The same reconstruction evaluated in binary128 (inputs and eps converted exactly, results
+// rounded to double): its exponent range (about 1e+-4932) holds every intermediate of Eq.
+// (function) and Eq. (new) for any double input, so it is the reference where the plain
+// double evaluation overflows (e.g. C when tau5 = 0 and the indicators exceed about 1e114).
+void oracle_reconstruct_quad(const double* f_padded, int64_t n, double* fhat, int side, double eps,
+                             double A, int kind) {
+    std::vector<Quad> f(n + 6);
+    for (int64_t j = 0; j < n + 6; ++j) f[j] = Quad(f_padded[j]);
+    for (int64_t j = 0; j <= n; ++j) {
+        const Quad r = side > 0 ? weno5(&f[j], Quad(eps), Quad(A), kind).fhat
+                                : weno5_minus(&f[j + 1], Quad(eps), Quad(A), kind);
+        fhat[j] = double(r);
+    }
+}
+
 double oracle_critical_point_error(int k, double dx, int kind, double eps, int quad) {
     return quad ? critical_point_error<Quad>(k, dx, kind, eps)
                 : critical_point_error<double>(k, dx, kind, eps);

@@ -13,7 +13,6 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     v.ctl = reinterpret_cast<unsigned*>(ws_base(ws) + L.vjp_ctl);
     v.n = p.nx;
     v.bc = p.bc_x;
-    v.fast_rcp = zn_fast_rcp(p.eps, p.A);
     v.nblocks = vjp_partial_count(p.nx);
     v.rdx = 1.0 / p.dx;
     v.gamma = p.gamma;
@@ -48,14 +47,10 @@ wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws,
     // the control word is zero after every gather; clear it before a sequence starts
     cudaError_t e = clear_ctl ? cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s) : cudaSuccess;
     if (e != cudaSuccess) return WENOZN_ECUDA;
-    // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam.  Inside a chain (no clear) the launch before is the
-    // previous step's last gather, so this interface kernel may start its lam-free work early;
-    // the later stages always follow this sequence's own gathers.
+    // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
     v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
     v.X1 = lam; v.c1 = 2.0 / 3.0; v.d = (2.0 / 3.0) * dt;
-    v.early = clear_ctl ? 0 : 1;
     e = launch_vjp(p.system, v, s);
-    v.early = 1;
     if (e == cudaSuccess) {                 // Ub1 = 1/4 Ub2 + 1/4 dt J(U1)^T Ub2
         v.U = U1; v.lam = ub2; v.alpha_bits = a1; v.out = ub1;
         v.X1 = ub2; v.c1 = 0.25; v.d = 0.25 * dt;

@@ -21,10 +21,11 @@ namespace {
 
 // Reverse of zn_flux: given f[0..4] and the cotangent Wb of f^ = W(f), writes dW/df * Wb to
 // fb[0..4] and returns W(f).
-__host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double kappa, int fast,
+__host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, double eps4, double kappa,
                                                   double* fb) {
     const double a = f[0], b = f[1], c = f[2], d = f[3], e = f[4];
-    // the forward of zn_parts: first differences, second (s_k) and one-sided (t_k)
+    // the forward of zn_num_den (fast evaluation only: the adjoint is exact for stencil
+    // differences between about 1e-100 and 1e25 in magnitude): first differences, second (s_k) and one-sided (t_k)
     // differences, scaled indicators b_k, weights a_k = m^2 b0 b1 b2 + (kappa d4 P)^2 prod_{j!=k} b_j,
     // W = c + N / D with the sub-stencil fluxes q_k - c from the first differences
     const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
@@ -58,7 +59,7 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
     const double q2 = fma(-2.0, D3, 0.5 * D4);                       // 3 (q_2 - c)
     const double N = fma(a0, q0, fma(-a1, q1n, a2 * q2));
     const double D = fma(6.0, a1, fma(3.0, a2, a0));
-    const double rD = fast ? rcp_nr(D) : 1.0 / D;
+    const double rD = rcp_nr(D);
     const double R = N * rD;
     // reverse
     const double Nb = Wb * rD, Db = -Nb * R;
@@ -127,10 +128,7 @@ struct EulerSmem {
 
 __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
     __shared__ EulerSmem sm;
-    // Inside a chain the launch before is the previous stage's gather, which writes lam and
-    // the control words only: the cell phase, the Roe state and the projections (from U and
-    // alpha, written long before) then overlap its tail, and the wait comes before lam is read.
-    if (!a.early) pdl_wait();
+    pdl_wait();
     const int n = a.n, j0 = blockIdx.x * kTI, tid = threadIdx.x;
     const int64_t P = int64_t(n) + 1;
     const double gm1 = a.gamma - 1.0;
@@ -201,7 +199,6 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
         }
     }
-    if (a.early) pdl_wait();                     // lam and the control words are read from here on
     if (cand >= 0) atomicMax(&a.ctl[0], ~unsigned(cand));
     if (live) {
         double fpb[5], fmb[5];
@@ -212,8 +209,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             Fb[m] = (right - left) * a.rdx;
         }
         const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
-        const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, a.fast_rcp, fpb) +
-                          zn_vjp(fm, ghb, a.eps4, a.kappa, a.fast_rcp, fmb);
+        const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, fpb) +
+                          zn_vjp(fm, ghb, a.eps4, a.kappa, fmb);
         double Lb[3] = {0, 0, 0};
         const double Lk[3] = {L0, L1, L2};
 #pragma unroll
@@ -320,8 +317,8 @@ __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
         fp[s] = hp[i + s];
         fm[4 - s] = hm[i + s + 1];
     }
-    zn_vjp(fp, Fb, a.eps4, a.kappa, a.fast_rcp, fpb);
-    zn_vjp(fm, Fb, a.eps4, a.kappa, a.fast_rcp, fmb);
+    zn_vjp(fp, Fb, a.eps4, a.kappa, fpb);
+    zn_vjp(fm, Fb, a.eps4, a.kappa, fmb);
     for (int s = 0; s < 6; ++s) {
         const double hpb = s <= 4 ? fpb[s] : 0.0, hmb = s >= 1 ? fmb[5 - s] : 0.0;
         a.C[(2 * s) * P + j] = 0.5 * (hpb + hmb);

@@ -103,7 +103,7 @@ wenozn_status wenozn_reconstruct(const double* f_padded, int64_t n, double* fhat
                                  double eps, double A, void* stream) {
     if (!f_padded || !fhat || n < 1 || n > (int64_t(1) << 31) - 8) return WENOZN_EINVAL;
     if (side != 1 && side != -1) return WENOZN_EINVAL;
-    if (!finite_pos(eps) || !finite_pos(A)) return WENOZN_EINVAL;
+    if (!finite_pos(eps) || !finite_pos(A) || !zn_constants_ok(eps, A)) return WENOZN_EINVAL;
     return cuda_status(launch_reconstruct(f_padded, n, fhat, side, eps, A,
                                           static_cast<cudaStream_t>(stream)));
 }
@@ -113,7 +113,7 @@ wenozn_status wenozn_reconstruct_weights(const double* f_padded, int64_t n, doub
     if (!f_padded || !fhat || n < 1 || n > (int64_t(1) << 31) - 8) return WENOZN_EINVAL;
     if (side != 1 && side != -1) return WENOZN_EINVAL;
     if (weights < 0 || weights > 3) return WENOZN_EINVAL;
-    if (!finite_pos(eps) || !finite_pos(A)) return WENOZN_EINVAL;
+    if (!finite_pos(eps) || !finite_pos(A) || !zn_constants_ok(eps, A)) return WENOZN_EINVAL;
     return cuda_status(launch_reconstruct(f_padded, n, fhat, side, eps, A, static_cast<cudaStream_t>(stream),
                                           weights));
 }
@@ -140,7 +140,6 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     if (dir != 0 && !(dir == 1 && p->system == WENOZN_EULER_2D)) return WENOZN_EINVAL;
     FluxArgs fa;
     fa.U = U;
-    fa.after_x = 0;
     fa.alpha_bits = reinterpret_cast<const unsigned long long*>(alpha);
     fa.alpha_f_bits = alpha ? fa.alpha_bits + 2 : nullptr;
     fa.weights = p->weights;
@@ -149,7 +148,6 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     fa.ny = p->ny;
     fa.eps4 = 4.0 * p->eps;
     fa.kappa = zn_kappa(p->A);
-    fa.fast_rcp = zn_fast_rcp(p->eps, p->A, p->weights);
     fa.gamma = p->gamma;
     fa.adv_speed = p->adv_speed;
     fa.Fout = Fout;

@@ -39,7 +39,7 @@ wenozn_status check_batch(const wenozn_batch_params* bp, const int64_t* offsets,
     if (bp->shape < -1 || bp->shape >= kNumBatchShapes) return WENOZN_EINVAL;
     if (!(std::isfinite(bp->gamma) && bp->gamma > 1.0) || !(std::isfinite(bp->eps) && bp->eps > 0.0) ||
         !(std::isfinite(bp->A) && bp->A > 0.0) || !(std::isfinite(bp->cfl) && bp->cfl > 0.0) ||
-        std::isnan(bp->t_final))
+        std::isnan(bp->t_final) || !zn_constants_ok(bp->eps, bp->A))
         return WENOZN_EINVAL;
     if (offsets[0] != 0) return WENOZN_EINVAL;
     for (int b = 0; b < bp->nbatch; ++b) {
@@ -112,7 +112,6 @@ BatchArgs args_of(const wenozn_batch_params* bp, const Ptrs& p, int64_t cells, i
     a.t = p.t;
     a.status = &p.ctrl->status;
     a.bc = bp->bc;
-    a.fast_rcp = zn_fast_rcp(bp->eps, bp->A);
     a.gamma = bp->gamma;
     a.eps4 = 4.0 * bp->eps;
     a.kappa = zn_kappa(bp->A);

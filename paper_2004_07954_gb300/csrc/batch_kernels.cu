@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
         __syncthreads();
         for (int jl = threadIdx.x; jl <= ncell; jl += THREADS) {     // interfaces c0 .. c0+ncell
             double Fh[NV];
-            interface_flux<NV>(sp, jl, 1, gm1, a.eps4, a.kappa, a.fast_rcp != 0, Fh);
+            interface_flux<NV>(sp, jl, 1, gm1, a.eps4, a.kappa, Fh);
 #pragma unroll
             for (int k = 0; k < NV; ++k) sF[k * TI + jl] = Fh[k];
         }

@@ -151,14 +151,13 @@ __device__ __forceinline__ void split_cell_gen(const double* Uc, int split, doub
 // Fh is in the sweep direction's frame.
 template <int NV>
 __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base, int stride,
-                                               double gm1, double eps4, double kappa, bool fast_rcp,
-                                               double* Fh) {
+                                               double gm1, double eps4, double kappa, double* Fh) {
     const int NC = s.NC;
     if (NV == 1) {
         Fh[0] = zn_split_flux(s.hp[base], s.hp[base + stride], s.hp[base + 2 * stride],
                               s.hp[base + 3 * stride], s.hp[base + 4 * stride],
                               s.hm[base + stride], s.hm[base + 2 * stride], s.hm[base + 3 * stride],
-                              s.hm[base + 4 * stride], s.hm[base + 5 * stride], eps4, kappa, fast_rcp);
+                              s.hm[base + 4 * stride], s.hm[base + 5 * stride], eps4, kappa);
         return;
     }
     // Roe average between the stencil's cells 2 and 3
@@ -205,7 +204,7 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
 #pragma unroll
     for (int k = 0; k < NV; ++k)
         gh[k] = zn_split_flux(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k],
-                              gm[0][k], gm[1][k], gm[2][k], gm[3][k], gm[4][k], eps4, kappa, fast_rcp);
+                              gm[0][k], gm[1][k], gm[2][k], gm[3][k], gm[4][k], eps4, kappa);
     // back-projection F^ = R g^ with the right eigenvectors (columns)
     //   r_{u-c} = (1, u-c, [v,] H-uc), r_u = (1, u, [v,] q^2/2), r_shear = (0, 0, 1, v),
     //   r_{u+c} = (1, u+c, [v,] H+uc)
@@ -231,7 +230,7 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
 // 0 u-c, 1 u, 2 u+c) or the largest |u_n| + c of the six cells (split 2).
 template <int NV>
 __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int base, int stride, double gm1,
-                                                   double eps4, double kappa, bool fast_rcp, int weights, int split,
+                                                   double eps4, double kappa, int weights, int split,
                                                    const double* alpha_f, double* Fh) {
     const int NC = s.NC;
     if (NV == 1) {
@@ -239,8 +238,8 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
         const double p3 = s.hp[base + 3 * stride], p4 = s.hp[base + 4 * stride];
         const double m0 = s.hm[base + stride], m1 = s.hm[base + 2 * stride], m2 = s.hm[base + 3 * stride];
         const double m3 = s.hm[base + 4 * stride], m4 = s.hm[base + 5 * stride];
-        Fh[0] = zn_flux_w(p0, p1, p2, p3, p4, eps4, kappa, fast_rcp, weights) +
-                zn_flux_w(m4, m3, m2, m1, m0, eps4, kappa, fast_rcp, weights);
+        Fh[0] = zn_flux_w(p0, p1, p2, p3, p4, eps4, kappa, weights) +
+                zn_flux_w(m4, m3, m2, m1, m0, eps4, kappa, weights);
         return;
     }
     const int cl = base + 2 * stride, cr = base + 3 * stride;
@@ -305,8 +304,8 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
     double gh[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-        gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, kappa, fast_rcp, weights) +
-                zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, kappa, fast_rcp, weights);
+        gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, kappa, weights) +
+                zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, kappa, weights);
     const double uc = u * c;
     if (NV == 3) {
         const double d20 = gh[2] - gh[0];

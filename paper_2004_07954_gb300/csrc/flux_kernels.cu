@@ -37,12 +37,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     constexpr int NC = CL * TA;           // cells per tile
     extern __shared__ double smem[];
     const CellPlanes<NV> sp(smem, NC);
-    // The y sweep of a stage follows the x sweep, which writes only the x fluxes: it starts
-    // at once (its inputs, from the launches before, are complete once the x sweep's blocks
-    // have started), and waits for the x sweep only before it ends, so that whatever follows
-    // the y sweep also finds the x fluxes complete.
-    const bool overlap = DIR == 1 && a.after_x;
-    if (!overlap) pdl_wait();
+    pdl_wait();
 
     const int n = DIR == 0 ? a.nx : a.ny;           // cells along the sweep
     const int nlines = DIR == 0 ? a.ny : a.nx;
@@ -92,10 +87,10 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         if (j >= nint || line >= nlines) continue;
         double Fh[NV];
         if (GEN)
-            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.fast_rcp != 0, a.weights,
+            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.weights,
                                    a.split, alpha_f, Fh);
         else
-            interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.fast_rcp != 0, Fh);
+            interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, Fh);
         // store, undoing the direction frame
         if (DIR == 0) {
             const int64_t base = int64_t(line) * (a.nx + 1) + j;
@@ -111,7 +106,6 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
             a.Fout[3 * stride + base] = Fh[3];
         }
     }
-    if (overlap) pdl_wait();
 }
 
 template <int NV, int DIR, bool SMALL, bool GEN>

@@ -59,6 +59,7 @@ inline wenozn_status check_problem(const wenozn_problem* p) {
     if (two_d && (p->bc_y < WENOZN_BC_PERIODIC || p->bc_y > WENOZN_BC_REFLECTIVE)) return WENOZN_EINVAL;
     if (!finite_pos(p->dx) || (two_d && !finite_pos(p->dy))) return WENOZN_EINVAL;
     if (!finite_pos(p->eps) || !finite_pos(p->A) || !finite_pos(p->cfl)) return WENOZN_EINVAL;
+    if (!zn_constants_ok(p->eps, p->A)) return WENOZN_EINVAL;
     if (p->system == WENOZN_ADVECTION_1D) {
         if (!std::isfinite(p->adv_speed) || p->adv_speed == 0.0) return WENOZN_EINVAL;
     } else if (!std::isfinite(p->gamma) || p->gamma <= 1.0) {
@@ -81,12 +82,10 @@ inline FluxArgs flux_args(const wenozn_problem& p, const double* U, const unsign
     fa.ny = p.ny;
     fa.eps4 = 4.0 * p.eps;
     fa.kappa = zn_kappa(p.A);
-    fa.fast_rcp = zn_fast_rcp(p.eps, p.A, p.weights);
     fa.gamma = p.gamma;
     fa.adv_speed = p.adv_speed;
     fa.Fout = nullptr;
     fa.bc = p.bc_x;
-    fa.after_x = 0;
     return fa;
 }
 
@@ -101,7 +100,6 @@ inline cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const
     if (e != cudaSuccess || p.system != WENOZN_EULER_2D) return e;
     fa.Fout = gy;
     fa.bc = p.bc_y;
-    fa.after_x = 1;
     return launch_flux(p.system, 1, fa, s);
 }
 

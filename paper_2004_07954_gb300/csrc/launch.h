@@ -37,19 +37,14 @@ struct FluxArgs {
     const unsigned long long* alpha_bits;  // LF speeds (x, y) of U as bit patterns; unused for advection
     const unsigned long long* alpha_f_bits;  // per-field speeds [dir][3] (split 1 only)
     int nx, ny, bc;                        // bc of the sweep direction (0 periodic, 1 outflow, 2 reflective)
-    int fast_rcp;                          // 1: Newton reciprocal for f^ = num/den (see zn_flux)
     int weights, split;                    // weight function and flux splitting (wenozn.h enums)
-    int after_x;                           // y sweep launched right after the x sweep of the same
-                                           // stage input: it reads nothing that sweep writes
     double eps4, kappa, gamma, adv_speed;  // eps4 = 4 eps, kappa = 2 / sqrt(A) (see zn_parts)
 };
-// Whether the reconstruction's common denominator is guaranteed positive and normal, so the
-// Newton reciprocal applies: WENO-ZN needs A > 0 and eps >= 1e-60, WENO-Z and Jiang-Shu
-// eps >= 1e-60, the linear weights always.
-inline int zn_fast_rcp(double eps, double A, int weights = 0) {
-    (void)A;
-    if (weights == 2) return 1;
-    return eps >= 1e-60 ? 1 : 0;
+// Admissible constants of the weights: with 1e-60 <= eps <= 1 and 1e-6 <= A <= 1e6 the
+// reconstruction's common denominator is a positive normal number and its range guard
+// (zn_flux) covers every stencil whose differences stay below 2^440.
+inline bool zn_constants_ok(double eps, double A) {
+    return eps >= 1e-60 && eps <= 1.0 && A >= 1e-6 && A <= 1e6;
 }
 // The WENO-ZN weights carry A as kappa = 2 / sqrt(A) (A > 0, checked on entry).
 inline double zn_kappa(double A) { return 2.0 / std::sqrt(A); }
@@ -99,7 +94,6 @@ struct BatchArgs {
     int32_t* status;
     int stage;                 // 0, 1, 2
     int bc;                    // ghost map of every instance
-    int fast_rcp;
     double gamma, eps4, kappa, cfl;
     double t_final;            // > 0: no instance steps past it
 };
@@ -123,10 +117,7 @@ struct VjpArgs {
     const double* X2;
     const double* X3;
     double c1, c2, c3, d;
-    int n, bc, fast_rcp, nblocks;          // nblocks = vjp_partial_count(n)
-    int early;                             // the launch before is this chain's gather: work that reads
-                                           // neither lam nor the control words runs before the
-                                           // programmatic-dependence wait
+    int n, bc, nblocks;                    // nblocks = vjp_partial_count(n)
     double rdx, gamma, eps4, kappa, adv_speed;
 };
 int vjp_partial_count(int n);

@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
             if (a.mode == 0) {
                 r = -(dF * a.rdx);
                 if (NV == 4) r = fma(-dG, a.rdy, r);
+                // a non-finite L (a stencil beyond the reconstruction's range): exponent test
+                bad |= (__double2hiint(r) & 0x7ff00000) == 0x7ff00000;
             } else {
                 const double us = a.Us[k * nc + cell];
                 double base = us;
@@ -240,12 +242,12 @@ __global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, u
 
 __global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, int64_t n, double* fhat,
                                                                 int side, double eps4, double kappa,
-                                                                int fast_rcp, int weights) {
+                                                                int weights) {
     const int64_t j = blockIdx.x * int64_t(kThreads) + threadIdx.x;
     if (j > n) return;
     const double* s = f + j;
-    fhat[j] = side > 0 ? zn_flux_w(s[0], s[1], s[2], s[3], s[4], eps4, kappa, fast_rcp != 0, weights)
-                       : zn_flux_w(s[5], s[4], s[3], s[2], s[1], eps4, kappa, fast_rcp != 0, weights);
+    fhat[j] = side > 0 ? zn_flux_w(s[0], s[1], s[2], s[3], s[4], eps4, kappa, weights)
+                       : zn_flux_w(s[5], s[4], s[3], s[2], s[1], eps4, kappa, weights);
 }
 
 __global__ void __launch_bounds__(kThreads) rcp_check_kernel(const double* d, int64_t n, double* fast,
@@ -377,8 +379,7 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
                                double eps, double A, cudaStream_t s, int weights) {
     const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
-    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A),
-                                                 zn_fast_rcp(eps, A, weights), weights);
+    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A), weights);
     return cudaGetLastError();
 }
 

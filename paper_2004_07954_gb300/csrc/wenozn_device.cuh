@@ -7,6 +7,7 @@
 // only the rounding differs from the plain evaluation order.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 namespace wz {
@@ -41,13 +42,20 @@ namespace wz {
 //    difference and kappa = 2 / sqrt(A) (A > 0), all positive (a_k >= (4 eps)^5 > 0); the
 //    optimal weights (1, 6, 3)/10
 //    then enter through 6 q_1 and 3 q_2 and the denominator a_0 + 6 a_1 + 3 a_2, leaving one
-//    division per reconstruction.  The fourth difference is d4 = t_0 + t_2.
-// Range: finite for |f| below ~1e20.
+//    division per reconstruction.  The fourth difference is d4 = t0 + t2.
+//
+// Range.  The a_k are fifth powers of the indicators, so for stencils whose differences
+// exceed about 2^88 they overflow, and for data far below the scale of eps (differences
+// under about sqrt(eps) times 1e-100) the numerator underflows.  Every quantity above is
+// homogeneous once eps is scaled with the data: with the first differences multiplied by s
+// and eps by s^2, each b_k scales by s^2, each a_k by s^10 and num/den by s.  So the fast
+// evaluation is kept, its num and den are checked on the integer pipe, and in the rare case
+// they left the double range the weights are evaluated again on the differences scaled by
+// an exact power of two that brings the largest indicator near 2^100 (zn_correction_rescaled;
+// the Jiang-Shu variant divides the smallest indicator out instead).
+// With 1e-60 <= eps <= 1 and 1e-6 <= A <= 1e6 the result is then finite and accurate for
+// every stencil whose first differences stay below 2^440 (about 2.8e132) in magnitude.
 // ------------------------------------------------------------------------------------
-struct ZnParts {
-    double num, den, c;  // f^ = c + num / den
-};
-
 // Reciprocal of a positive, normal double: start from the hardware approximation
 // r0 (rcp.approx.ftz.f64, about 23 correct bits), form e = 1 - d r0 and take one step of
 // the cubically convergent series 1/d = r0 (1 + e + e^2 + ...) truncated after e^2
@@ -64,11 +72,11 @@ __host__ __device__ __forceinline__ double rcp_nr(double d) {
 #endif
 }
 
-__host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double c, double d, double e,
-                                                     double eps4, double kappa) {
-    // first differences, then the second (s_k) and one-sided (t_k) differences from them:
-    // equal inputs give exact zeros
-    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+// WENO-ZN numerator and denominator of f^ - c from the first differences D1..D4 (the
+// evaluation described above).
+__host__ __device__ __forceinline__ void zn_num_den(double D1, double D2, double D3, double D4, double eps4,
+                                                    double kappa, double& num, double& den) {
+    // second (s_k) and one-sided (t_k) differences from the first: equal inputs give exact zeros
     const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
     const double k13_3 = 13.0 / 3.0;
@@ -100,29 +108,8 @@ __host__ __device__ __forceinline__ ZnParts zn_parts(double a, double b, double 
     const double q0 = fma(1.0 / 3.0, D1, (-5.0 / 6.0) * D2);
     const double q1n = fma(2.0, D3, D2);
     const double q2 = fma(-2.0, D3, 0.5 * D4);
-    ZnParts r;
-    r.num = fma(a0, q0, fma(-a1, q1n, a2 * q2));
-    r.den = fma(6.0, a1, fma(3.0, a2, a0));
-    r.c = c;
-    return r;
-}
-
-// f^ = c + num / den.  With eps >= 1e-60, den >= 10 (4 eps)^5 is a positive
-// normal number, so the Newton reciprocal applies (fast_rcp = true, chosen by the host);
-// otherwise the IEEE division is used.
-__host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
-                                                   double eps4, double kappa, bool fast_rcp) {
-    const ZnParts r = zn_parts(a, b, c, d, e, eps4, kappa);
-    return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
-}
-
-// f^+ + f^- at one interface: plus side from (p0..p4) = h+_{i-2..i+2}, minus side from the
-// mirrored stencil (m4, m3, m2, m1, m0) where (m0..m4) = h-_{i-1..i+3} (Sec. 2, the
-// "symmetric rule about x_{i+1/2}").
-__device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2, double p3, double p4,
-                                                double m0, double m1, double m2, double m3, double m4,
-                                                double eps4, double kappa, bool fast_rcp) {
-    return zn_flux(p0, p1, p2, p3, p4, eps4, kappa, fast_rcp) + zn_flux(m4, m3, m2, m1, m0, eps4, kappa, fast_rcp);
+    num = fma(a0, q0, fma(-a1, q1n, a2 * q2));
+    den = fma(6.0, a1, fma(3.0, a2, a0));
 }
 
 // ------------------------------------------------------------------------------------
@@ -134,11 +121,14 @@ __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2,
 //            times b_0 b_1 b_2: a_k = b_0 b_1 b_2 + T prod_{j != k} b_j;
 //   JS:      alpha_k / c_k = 16 / b_k^2; times (b_0 b_1 b_2)^2 / 16: a_k = (prod_{j != k} b_j)^2;
 //   linear:  a_k = 1.
+// Each is homogeneous in the data with eps scaled alike, so the range guard above applies.
 // ------------------------------------------------------------------------------------
-__host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, double c, double d, double e,
-                                                       double eps4, double kappa, int weights) {
-    if (weights == 0) return zn_parts(a, b, c, d, e, eps4, kappa);
-    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+__host__ __device__ __forceinline__ void zn_num_den_w(double D1, double D2, double D3, double D4, double eps4,
+                                                      double kappa, int weights, double& num, double& den) {
+    if (weights == 0) {
+        zn_num_den(D1, D2, D3, D4, eps4, kappa, num, den);
+        return;
+    }
     const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
     const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
     const double k13_3 = 13.0 / 3.0;
@@ -164,17 +154,97 @@ __host__ __device__ __forceinline__ ZnParts zn_parts_w(double a, double b, doubl
             a2 = b01 * b01;
         }
     }
-    ZnParts r;
-    r.num = fma(a0, q0, fma(a1, q1, a2 * q2));
-    r.den = fma(6.0, a1, fma(3.0, a2, a0));
-    r.c = c;
-    return r;
+    num = fma(a0, q0, fma(a1, q1, a2 * q2));
+    den = fma(6.0, a1, fma(3.0, a2, a0));
+}
+
+// Whether the fast evaluation left the double range: den (a sum of positive terms) not a
+// positive normal number, num not finite, or num flushed to zero or subnormal by underflow
+// while the data are not constant.  Integer operations on the bit patterns only.
+__host__ __device__ __forceinline__ bool zn_out_of_range(double num, double den, double D1, double D2, double D3,
+                                                         double D4) {
+#ifdef __CUDA_ARCH__
+    const unsigned ed = (unsigned(__double2hiint(den)) >> 20) & 0x7ffu;
+    const unsigned en = (unsigned(__double2hiint(num)) >> 20) & 0x7ffu;
+    if (ed - 1u < 0x7feu && en != 0x7ffu && en != 0u) return false;
+    const unsigned long long any = (__double_as_longlong(D1) | __double_as_longlong(D2) |
+                                    __double_as_longlong(D3) | __double_as_longlong(D4)) << 1;   // sign dropped
+    return !(ed - 1u < 0x7feu && en != 0x7ffu) || any != 0ull;
+#else
+    if (!(den > 0.0) || !std::isnormal(den) || !std::isfinite(num)) return true;
+    return (num == 0.0 || !std::isnormal(num)) && (D1 != 0.0 || D2 != 0.0 || D3 != 0.0 || D4 != 0.0);
+#endif
+}
+
+// f^ - c re-evaluated where the fast evaluation left the double range; exact algebra.
+//  * WENO-ZN, WENO-Z: the differences scaled by 2^k and eps by 2^2k, with k chosen so that the
+//    largest scaled indicator lies in [2^99, 2^102); the scaling is undone on the quotient.
+//    Every a_k keeps at most one factor near eps against the largest indicators (sub-stencils
+//    0 and 2 share f_i, so they cannot both be flat unless all three are), so nothing of
+//    weight underflows.
+//  * Jiang-Shu: a_k = (prod_{j != k} b_j)^2 spans the square of the indicators' ratio, which
+//    no common scale keeps in range; with the smallest indicator divided out instead,
+//    a_k = (b_min / b_k)^2 lies in (0, 1].
+__host__ __device__ __forceinline__ double zn_correction_rescaled(double D1, double D2, double D3, double D4,
+                                                                  double eps4, double kappa, int weights) {
+    const double s0 = D1 - D2, s1 = D2 - D3, s2 = D3 - D4;
+    const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
+    const double k13_3 = 13.0 / 3.0;
+    const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));
+    const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
+    const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
+    if (weights == 3) {
+        const double bm = fmin(b0, fmin(b1, b2));
+        const double r0 = bm * rcp_nr(b0), r1 = bm * rcp_nr(b1), r2 = bm * rcp_nr(b2);
+        const double a0 = r0 * r0, a1 = r1 * r1, a2 = r2 * r2;
+        const double q0 = fma(1.0 / 12.0, s0, 0.25 * t0);
+        const double q1 = fma(0.5, s1, -1.5 * t1);
+        const double q2 = fma(0.25, s2, -0.75 * t2);
+        const double num = fma(a0, q0, fma(a1, q1, a2 * q2));
+        const double den = fma(6.0, a1, fma(3.0, a2, a0));
+        return num * rcp_nr(den);
+    }
+    // the largest indicator 4 (IS_k + eps) of the unscaled data fixes the scale
+    const double B = fmax(b0, fmax(b1, b2));
+    int eb = 0;
+    (void)frexp(B, &eb);                       // B in [2^(eb-1), 2^eb)
+    int k = (101 - eb) >> 1;                   // B 2^2k in [2^99, 2^102)
+    k = k < -500 ? -500 : (k > 500 ? 500 : k);
+    const double s = ldexp(1.0, k), si = ldexp(1.0, -k);
+    double num, den;
+    zn_num_den_w(D1 * s, D2 * s, D3 * s, D4 * s, (eps4 * s) * s, kappa, weights, num, den);
+    return (num * rcp_nr(den)) * si;
+}
+
+// f^ = c + num / den, with the rescaled evaluation when the fast one left the double range.
+// den is then a positive normal number (eps >= 1e-60 makes den >= 10 (4 eps)^5), so the
+// Newton reciprocal applies.
+__host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
+                                                   double eps4, double kappa) {
+    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+    double num, den;
+    zn_num_den(D1, D2, D3, D4, eps4, kappa, num, den);
+    if (zn_out_of_range(num, den, D1, D2, D3, D4)) return c + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, 0);
+    return fma(num, rcp_nr(den), c);
+}
+
+// f^+ + f^- at one interface: plus side from (p0..p4) = h+_{i-2..i+2}, minus side from the
+// mirrored stencil (m4, m3, m2, m1, m0) where (m0..m4) = h-_{i-1..i+3} (Sec. 2, the
+// "symmetric rule about x_{i+1/2}").
+__device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2, double p3, double p4,
+                                                double m0, double m1, double m2, double m3, double m4,
+                                                double eps4, double kappa) {
+    return zn_flux(p0, p1, p2, p3, p4, eps4, kappa) + zn_flux(m4, m3, m2, m1, m0, eps4, kappa);
 }
 
 __host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
-                                                     double eps4, double kappa, bool fast_rcp, int weights) {
-    const ZnParts r = zn_parts_w(a, b, c, d, e, eps4, kappa, weights);
-    return fast_rcp ? fma(r.num, rcp_nr(r.den), r.c) : r.c + r.num / r.den;
+                                                     double eps4, double kappa, int weights) {
+    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+    double num, den;
+    zn_num_den_w(D1, D2, D3, D4, eps4, kappa, weights, num, den);
+    if (zn_out_of_range(num, den, D1, D2, D3, D4))
+        return c + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, weights);
+    return fma(num, rcp_nr(den), c);
 }
 
 // ------------------------------------------------------------------------------------

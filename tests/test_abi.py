@@ -56,7 +56,8 @@ def test_workspace_size_layout(wz):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", 0), ("system", 7), ("bc_x", 3), ("dx", 0.0),
                                          ("dx", float("nan")), ("eps", 0.0), ("A", -1.0), ("cfl", 0.0),
-                                         ("gamma", 1.0), ("flags", 1)])
+                                         ("gamma", 1.0), ("flags", 1), ("eps", 1e-61), ("eps", 2.0),
+                                         ("A", 1e-7), ("A", 2e6)])
 def test_invalid_problem_rejected_on_host(wz, field, value):
     p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 16, 16, 0.1, 0.1)
     setattr(p, field, value)
@@ -102,8 +103,12 @@ def test_newer_entry_points_reject_bad_arguments_on_host(wz):
     assert L.wenozn_rk3_vjp_run(ctypes.byref(p1), A, A, A, A, 3, 1e-3, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
     assert L.wenozn_rk3_vjp_run(ctypes.byref(p2), A, A, A, A, 3, 1e-3, A, A, 1 << 30, None) == wz.WENOZN_EINVAL
     # weight variants: unknown weight function, bad side, non-positive eps
-    for weights, side, eps in ((4, 1, 1e-40), (-1, 1, 1e-40), (0, 2, 1e-40), (1, 1, 0.0)):
+    for weights, side, eps in ((4, 1, 1e-40), (-1, 1, 1e-40), (0, 2, 1e-40), (1, 1, 0.0), (0, 1, 1e-61),
+                               (3, 1, 1.5)):
         assert L.wenozn_reconstruct_weights(A, 10, A, side, weights, eps, 10.0, None) == wz.WENOZN_EINVAL
+    # the constant A of Eq. (function) outside [1e-6, 1e6]
+    for a in (0.0, 1e-7, 1e7):
+        assert L.wenozn_reconstruct(A, 10, A, 1, 1e-40, a, None) == wz.WENOZN_EINVAL
     # FP64 rate probe: sizes outside [4, 2^32], no result pointer
     g = ctypes.c_double(0.0)
     for bad in (0, 3, (1 << 32) + 1):

@@ -225,3 +225,51 @@ def test_ghost_fill_line(orc):
     for g in range(1, 4):
         assert per[3 - g] == vals[n - g] and per[n + 2 + g] == vals[g - 1]
         assert out[3 - g] == vals[0] and out[n + 2 + g] == vals[n - 1]
+
+
+# ------------------------------------------------------------------ binary128 line reconstruction
+@pytest.mark.parametrize("kind,eps", [(0, EPS), (1, EPS), (3, 1e-6)])
+def test_quad_reconstruction_equals_double_on_ordinary_data(orc, kind, eps):
+    """The binary128 evaluation (the range reference) rounds to the double evaluation on data
+    where the latter stays in range."""
+    g = np.random.default_rng(3 + kind)
+    f = g.normal(size=506)
+    f[g.random(506) < 0.1] += 5.0
+    for side in (1, -1):
+        d = orc.reconstruct(f, side, eps=eps, kind=kind)
+        q = orc.reconstruct_quad(f, side, eps=eps, kind=kind)
+        assert np.abs(d - q).max() <= 1e-13 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("k", [150, 300, 433])
+def test_quad_reconstruction_homogeneous_in_data_and_eps(orc, k):
+    """Eq. (function) and Eq. (new) are homogeneous: f -> s f with eps -> s^2 eps scales every
+    IS_k, tau5, tau8 by s^2 and leaves C and the weights unchanged, so f^(s f; eps) =
+    s f^(f; eps / s^2) exactly for a power of two s; the binary128 evaluation keeps this at
+    scales where the double one overflows."""
+    s = 2.0 ** k
+    g = np.random.default_rng(k)
+    f = g.normal(size=206)
+    f[g.random(206) < 0.1] += 5.0
+    for side in (1, -1):
+        big = orc.reconstruct_quad(f * s, side, eps=EPS)
+        small = orc.reconstruct_quad(f, side, eps=EPS / s ** 2)
+        assert np.all(np.isfinite(big))
+        assert np.abs(big - small * s).max() <= 1e-15 * np.abs(f * s).max()
+
+
+def test_quad_reconstruction_linear_limit_at_equal_large_indicators(orc):
+    """Where tau5 = |IS_0 - IS_2| = 0 and the indicators are huge, C = A ((IS_0 + IS_2 + eps)
+    / eps)^2 dwarfs tau8 / (IS_k + eps) and the weights are the linear ones to far below
+    double rounding: the plain double evaluation overflows C there (NaN), the binary128 one
+    gives the linear scheme's flux."""
+    f = np.full(26, 0.7)
+    f[12] = -2.0                                       # IS_0 = IS_2 at the interface beside the spike
+    f *= 1e100
+    lin = orc.reconstruct(f, 1, kind=2)
+    q = orc.reconstruct_quad(f, 1)
+    d = orc.reconstruct(f, 1)
+    bad = ~np.isfinite(d)
+    assert bad.any()                                   # the double evaluation's own overflow
+    assert np.abs(q[bad] - lin[bad]).max() <= 1e-15 * np.abs(f).max()
+    assert np.abs(q[~bad] - d[~bad]).max() <= 1e-13 * np.abs(f).max()
