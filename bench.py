@@ -40,7 +40,8 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "bf926e69f14cafd5", "n": 4096, "bytes": 965.7e6,
+TRAFFIC_CAPTURE = {"sha256_16": "bf926e69f14cafd5", "n": 4096, "bytes": 965.7e6, "capture_n": 2560,
+                   "profile": "profiles/flux_kernel_euler2d_2560.md",
                    "fp64_pipe": {"x": 0.888, "y": 0.889}}   # ncu FP64-pipe busy, same capture
 
 
@@ -96,7 +97,8 @@ def parse_args():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-euler1d", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "variants", "euler1d"], default=None,
+    ap.add_argument("--no-euler2d-1024", action="store_true")
+    ap.add_argument("--only", choices=["batched", "adjoint", "variants", "euler1d", "euler2d_1024"], default=None,
                     help="run only this part and print its object (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
@@ -292,6 +294,45 @@ def bench_euler1d(wenozn, inputs, seed: int, n: int = 1 << 20, K: int = 100) -> 
             "device_status": status}
 
 
+def bench_euler2d(wenozn, inputs, seed: int, n: int, K: int, reps: int = 5) -> dict:
+    """The headline workload on an n x n grid: K chained RK3 steps after 3 warm-up steps
+    (CUDA events on the launching stream), and the x-flux kernel alone for its FP64 fraction."""
+    import torch
+    p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_2D, n, n, 1.0 / n, 1.0 / n)
+    U = torch.from_numpy(inputs.euler2d_ic(n, n, seed)).cuda()
+    S = wenozn.Solver(p)
+    S.steps(U, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S.steps(U, K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    status = S.status()
+    alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
+    wenozn.wenozn_max_wavespeed(p, U, alpha)
+    kern = {}
+    for d in (0, 1):
+        buf = torch.empty(wenozn.flux_shape(p, d), dtype=torch.float64, device="cuda")
+        wenozn.wenozn_flux(p, U, alpha, d, buf)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            wenozn.wenozn_flux(p, U, alpha, d, buf)
+        e1.record()
+        torch.cuda.synchronize()
+        kern[d] = e0.elapsed_time(e1) / reps
+    fl = algorithmic_flops(n, n)
+    return {"workload": f"2D Euler {n}x{n} seeded four-quadrant Riemann problem (seed {seed}), outflow, "
+                        f"CFL 0.5, {K} chained SSP-RK3 steps",
+            "metric": "cell-updates/s", "value": n * n / (ms / 1e3), "ms_per_step": round(ms, 4),
+            "step_frac": round(fl["step"] / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+            "x_flux": {"ms": round(kern[0], 4), "frac": round(fl["x_flux"] / (kern[0] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
+            "y_flux": {"ms": round(kern[1], 4), "frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
+            "device_status": status}
+
+
 VARIANTS = [("weno_z", 1, 0), ("jiang_shu", 3, 0), ("per_field_lf", 0, 1), ("local_lf", 0, 2),
             ("steger_warming", 0, 3)]
 
@@ -352,7 +393,7 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
     p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_1D, n, 1, 10.0 / n, 1.0, bc_x=wenozn.WENOZN_BC_PERIODIC)
     ws = wenozn.vjp_workspace(p)
     U0 = torch.from_numpy(inputs.adjoint_ic(n, seed)).cuda()
-    dt = cfl_step(p, U0)
+    dt = cfl_step(p, U0, ws)
     with torch.no_grad():
         target = rollout(torch.from_numpy(inputs.adjoint_ic(n, seed + 1)).cuda(), p, dt, steps, ws=ws)[0].clone()
 
@@ -525,6 +566,8 @@ def main():
             part = bench_variants(wenozn, inputs, args.seed + rank, args.n)
         elif args.only == "euler1d":
             part = bench_euler1d(wenozn, inputs, args.seed + rank)
+        elif args.only == "euler2d_1024":
+            part = bench_euler2d(wenozn, inputs, args.seed + rank, 1024, 100)
         else:
             part = bench_adjoint(wenozn, inputs, args.seed + rank, steps=args.adjoint_steps,
                                  fd_dirs=args.adjoint_fd_dirs)
@@ -604,55 +647,56 @@ def main():
                                            "(wenozn_fp64_fma_rate), measured in this run"},
                 # ncu counters of the same kernels (null once the kernel sources changed)
                 "fp64_pipe_ncu": TRAFFIC_CAPTURE["fp64_pipe"] if captured else None,
+                "traffic_source": {"measured_in_this_run": False,
+                                   "capture": f"ncu, {TRAFFIC_CAPTURE['capture_n']}^2 case of the same kernel "
+                                              f"({TRAFFIC_CAPTURE['profile']})",
+                                   "scaled": f"by the interface count to {n}^2",
+                                   "kernel_sources_sha256_16": TRAFFIC_CAPTURE["sha256_16"],
+                                   "sources_match": captured},
                 "dram": None if traffic is None else {
                     "gbs": round(traffic / (kern[0] / 1e3) / 1e9, 1), "peak_gbs": hbm_gbs,
                     "frac": round(traffic / (kern[0] / 1e3) / 1e9 / hbm_gbs, 5), "peak_source": hbm_src}}
 
     # ---- end to end: host buffers, copies inside the timed region --------------------
-    # Every step copies its input from pinned host memory and its result back.  The copies
-    # run on their own streams (one per direction) into two device buffers, so step k's
-    # compute overlaps the upload of step k+1 and the download of step k-1.
+    # Every step goes through the library's host-buffer call (wenozn_rk3_step_host): it copies
+    # the step's input from pinned host memory to a device staging buffer, takes one RK3 step
+    # and copies the result back, all on its stream.  Steps alternate between two streams,
+    # each with its own staging buffer and workspace, so one step's copies overlap the other
+    # stream's computation.
     host_in = torch.from_numpy(U0).pin_memory()
     host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
     bufs = [torch.empty_like(U) for _ in range(2)]
-    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    solvers = [S, wenozn.Solver(p)]
+    streams = [stream, torch.cuda.Stream()]
     ke = max(1, args.e2e_steps)
 
-    def e2e_run(k_steps, e_start=None):
-        up = [torch.cuda.Event() for _ in range(k_steps)]
-        done = [torch.cuda.Event() for _ in range(k_steps)]
-        down = [torch.cuda.Event() for _ in range(k_steps)]
-        if e_start is not None:
-            h2d.wait_event(e_start)
+    def e2e_run(k_steps):
+        start = torch.cuda.Event()
+        start.record(streams[0])
+        streams[1].wait_event(start)
         for k in range(k_steps):
-            b = bufs[k % 2]
-            with torch.cuda.stream(h2d):
-                if k >= 2:
-                    h2d.wait_event(down[k - 2])          # buffer free again
-                b.copy_(host_in, non_blocking=True)
-                up[k].record(h2d)
-            stream.wait_event(up[k])
-            S.step(b, stream=stream)
-            done[k].record(stream)
-            with torch.cuda.stream(d2h):
-                d2h.wait_event(done[k])
-                host_out[k % 2].copy_(b, non_blocking=True)
-                down[k].record(d2h)
-        stream.wait_event(down[k_steps - 1])
+            i = k % 2
+            wenozn.wenozn_rk3_step_host(p, host_in, host_out[i], bufs[i], solvers[i].ws, stream=streams[i])
+        done = torch.cuda.Event()
+        done.record(streams[1])
+        streams[0].wait_event(done)
 
-    e2e_run(1)
+    e2e_run(2)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    e2e_run(ke, e0)
+    e2e_run(ke)
     e1.record(stream)
     torch.cuda.synchronize()
     ems = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_status = max(sv.status() for sv in solvers)
     nbytes = U.numel() * U.element_size()
     e2e = {"value": job_throughput(n * n, ke, world, ems), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": ke,
-           "copies": "pinned host <-> device on one stream per direction, overlapped with the previous/next step"}
+           "d2h_bytes_per_step": nbytes, "steps": ke, "device_status": e2e_status,
+           "api": "wenozn_rk3_step_host (host buffers in and out, one C-ABI call per step)",
+           "copies": "pinned host <-> device inside the call, steps alternating between two streams"}
+    del bufs, solvers[1]
 
     def part(skip, fn, *a, **kw):
         """A secondary measurement; its failure is reported in its own object, the headline
@@ -666,6 +710,7 @@ def main():
 
     batched = part(args.no_batched, bench_batched, wenozn, inputs, args.seed + rank, args.batched_steps)
     euler1d = part(args.no_euler1d, bench_euler1d, wenozn, inputs, args.seed + rank)
+    euler2d_1024 = part(args.no_euler2d_1024, bench_euler2d, wenozn, inputs, args.seed + rank, 1024, 100)
     variants = part(args.no_variants, bench_variants, wenozn, inputs, args.seed + rank, n)
     adjoint = part(args.no_adjoint, bench_adjoint, wenozn, inputs, args.seed + rank,
                    steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
@@ -684,7 +729,7 @@ def main():
                            "parallelism": f"{world} independent replica(s), one per GPU",
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "variants": variants, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "euler2d_1024": euler2d_1024, "variants": variants, "adjoint": adjoint,
                 "gpu_launches": 9 * args.steps + 1, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

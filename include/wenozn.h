@@ -211,6 +211,29 @@ wenozn_status wenozn_rhs_noalloc(const wenozn_problem* p, const double* U, doubl
 wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, double t_remaining,
                               double* dt_out, void* ws, size_t ws_bytes, void* stream);
 
+/* wenozn_rk3_step on a state held in host memory, in one call: U_host_in is copied to the
+ * device buffer U_dev, advanced by one step exactly as wenozn_rk3_step advances it (the same
+ * dt, t_remaining and dt_out conventions), and copied back to U_host_out, all enqueued on
+ * `stream` (cudaMemcpyAsync; with pinned host buffers the copies are asynchronous and overlap
+ * work on other streams).  Alternating two streams, each with its own device buffer and
+ * workspace, overlaps one step's copies with another's computation.
+ *   U_host_in, U_host_out : host, [nvar][ny][nx]; they may be the same buffer.
+ *   U_dev                 : device, [nvar][ny][nx], caller-owned staging buffer.
+ * Allocates nothing. */
+wenozn_status wenozn_rk3_step_host(const wenozn_problem* p, const double* U_host_in, double* U_host_out,
+                                   double* U_dev, double dt, double t_remaining, double* dt_out, void* ws,
+                                   size_t ws_bytes, void* stream);
+
+/* The CFL step of the state U (device, [nvar][ny][nx]): the step wenozn_rk3_step takes with
+ * dt <= 0 (1D: cfl dx / max(|u|+c), Sec. 4.3; 2D: cfl dtx dty / (dtx + dty) with
+ * dtx = dx / max(|u|+c), dty = dy / max(|v|+c), Sec. 4.4; advection: cfl dx / |a|), from
+ * the LF speeds evaluated on the device in the same IEEE operation order, so bit for bit the
+ * step that call would take.  Left in the workspace's step word (wenozn_workspace_dt); when
+ * the host pointer dt_out is non-NULL it is copied there and the stream is synchronised.  A
+ * non-finite state, rho <= 0 or p <= 0 sets WENOZN_ENONFINITE in the status word. */
+wenozn_status wenozn_cfl_dt(const wenozn_problem* p, const double* U, double* dt_out, void* ws, size_t ws_bytes,
+                            void* stream);
+
 /* nsteps SSP-RK3 steps of U in place, each with the fixed step dt > 0 or, for dt <= 0, its
  * CFL step; the same results as nsteps calls of wenozn_rk3_step, bit for bit.  The LF speeds
  * of each new state come from the last stage's update (which evaluates them anyway), so the
@@ -325,7 +348,9 @@ wenozn_status wenozn_workspace_stages(void* ws, const wenozn_problem* p, const d
 typedef struct {
     int32_t nbatch;   /* instances B, 1 .. 2^24                                            */
     int32_t bc;       /* wenozn_bc of every instance                                       */
-    int32_t shape;    /* kernel tile shape, 0 .. wenozn_batch_num_shapes()-1; -1 = default */
+    int32_t shape;    /* kernel tile shape, 0 .. wenozn_batch_num_shapes()-1; -1 = the tuned
+                         shape of this batch's size class if the tuner ran on one in this
+                         process (wenozn_batch_tune), else the default                      */
     int32_t flags;    /* reserved, 0                                                       */
     double gamma;     /* 1.4 (Sec. 4.3)                                                     */
     double eps;       /* Eq. (new), 1e-40                                                   */
@@ -358,32 +383,24 @@ wenozn_status wenozn_batch_rk3_step(const wenozn_batch_params* bp, const int64_t
                                     void* ws, size_t ws_bytes, void* stream);
 
 /* Autotuner: times `steps` RK3 steps (after one warm-up step) of every compiled shape on
- * this batch and stores the fastest in bp->shape; ms_per_step (host, num_shapes floats) or
- * NULL receives the timings.  U is advanced by the trial steps: tune on a copy.
- * Synchronises `stream`. */
+ * this batch, stores the fastest in bp->shape and records it in a process-wide table under
+ * the batch's size class (the device, bp->bc, and floor(log2) of the mean instance size and
+ * of the total cell count); ms_per_step (host, num_shapes floats) or NULL receives the
+ * timings.  steps = 0 takes the table's entry for this size class without timing anything
+ * (ms_per_step then holds zeros), and times 2 steps per shape when there is none yet.
+ * Steps of any batch of a tuned size class with bp->shape = -1 use the recorded shape.
+ * U is advanced by the trial steps: tune on a copy.  Synchronises `stream` when it times. */
 wenozn_status wenozn_batch_tune(wenozn_batch_params* bp, const int64_t* offsets, double* U, void* ws,
                                 size_t ws_bytes, int32_t steps, float* ms_per_step, void* stream);
+
+/* The tile shape wenozn_batch_rk3_step uses for this batch: bp->shape if >= 0, else the
+ * tuning table's entry for its size class, else the default.  Host only. */
+wenozn_status wenozn_batch_resolved_shape(const wenozn_batch_params* bp, const int64_t* offsets, int32_t* shape);
 
 /* Device addresses of the per-instance time t[B], step dt[B] (of the last RK3 step) and the
  * batch's status word inside the workspace (any output pointer may be NULL). */
 wenozn_status wenozn_batch_state(void* ws, int32_t nbatch, const int64_t* offsets, double** t,
                                  double** dt, int32_t** status);
-
-/* Diagnostic: evaluates, for n positive normal doubles d, the reciprocal the reconstruction
- * uses for f^ = num/den (Newton-Raphson refinement of the hardware approximation) into
- * `fast` and CUDA's IEEE 1/d into `ieee`, so that tests can bound the former's error.
- *   d, fast, ieee : device, n doubles (1 <= n <= 2^31). */
-wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, double* ieee,
-                                      void* stream);
-
-/* Measurement: the FP64 FMA rate this GPU sustains on pure register arithmetic (two blocks
- * of 256 threads per SM, four independent FMA chains per thread, fmas_per_thread FMAs each,
- * no memory traffic), timed with CUDA events on `stream` after one warm-up launch; the
- * call synchronizes `stream`.  Writes GFLOP/s (2 flops per FMA) to the host double
- * *gflops.  It is the achievable ceiling beside the nominal peak (2 FP64 FMA lanes per SM
- * per clock) against which the FP64-bound kernels of Sec. 2 and Sec. 4 are measured.
- * EINVAL unless 4 <= fmas_per_thread <= 2^32 and gflops is non-NULL. */
-wenozn_status wenozn_fp64_fma_rate(int64_t fmas_per_thread, double* gflops, void* stream);
 
 /* Static description of a status code. */
 const char* wenozn_status_string(wenozn_status s);

@@ -364,11 +364,14 @@ template <class T> struct LineCells {
     std::vector<T> hp, hm, srho, un, ut, H, speed;
 };
 
+// `par`: spread the cells over the OpenMP threads (a single long line; the cells are
+// independent, so the results do not depend on it).
 template <class T>
-void line_cells(const Problem& P, const T* Ul, int64_t np, int nv, T alpha, LineCells<T>& lc) {
+void line_cells(const Problem& P, const T* Ul, int64_t np, int nv, T alpha, LineCells<T>& lc, bool par = false) {
     lc.hp.resize(np * nv); lc.hm.resize(np * nv);
     if (P.system == SYS_ADV1D) {
         const T a = T(P.adv_speed);
+#pragma omp parallel for schedule(static) if (par && np > 4096)
         for (int64_t p = 0; p < np; ++p) {
             T f = a * Ul[p];
             lc.hp[p] = cst<T>(1, 2) * (f + alpha * Ul[p]);
@@ -378,6 +381,7 @@ void line_cells(const Problem& P, const T* Ul, int64_t np, int nv, T alpha, Line
     }
     const T gamma = T(P.gamma);
     lc.srho.resize(np); lc.un.resize(np); lc.ut.resize(np); lc.H.resize(np); lc.speed.resize(np);
+#pragma omp parallel for schedule(static) if (par && np > 4096)
     for (int64_t p = 0; p < np; ++p) {
         const T* U = &Ul[p * nv];
         Prim<T> w = primitives(U, nv, gamma);
@@ -474,17 +478,39 @@ void interface_flux(const Problem& P, const LineCells<T>& lc, int nv, int64_t i,
 
 // Largest |u_n| + c over the interior (one LF alpha per direction); dir 0 = x, 1 = y.
 template <class T>
+T cell_speed(const Problem& P, const T* U, int64_t nc, int64_t c, int dir) {
+    const int nv = nvar_of(P.system);
+    T s[4];
+    for (int k = 0; k < nv; ++k) s[k] = U[k * nc + c];
+    if (dir == 1) std::swap(s[1], s[2]);
+    Prim<T> w = primitives(s, nv, T(P.gamma));
+    return tabs(w.un) + sound_speed(w, T(P.gamma));
+}
+
+template <class T>
 T max_wavespeed(const Problem& P, const T* U, int dir) {
     if (P.system == SYS_ADV1D) return tabs(T(P.adv_speed));
-    const int nv = nvar_of(P.system);
     const int64_t nc = int64_t(P.nx) * P.ny;
     T best = T(0);
-    for (int64_t c = 0; c < nc; ++c) {
-        T s[4];
-        for (int k = 0; k < nv; ++k) s[k] = U[k * nc + c];
-        if (dir == 1) std::swap(s[1], s[2]);
-        Prim<T> w = primitives(s, nv, T(P.gamma));
-        best = tmax(best, tabs(w.un) + sound_speed(w, T(P.gamma)));
+    for (int64_t c = 0; c < nc; ++c) best = tmax(best, cell_speed(P, U, nc, c, dir));
+    return best;
+}
+
+// In double the maximum is exact and independent of the order the cells are visited in, so
+// the cells can be spread over the OpenMP threads (the other scalars keep the serial scan:
+// a dual number's maximum also picks the derivative of the first maximal cell).
+template <>
+double max_wavespeed<double>(const Problem& P, const double* U, int dir) {
+    if (P.system == SYS_ADV1D) return std::fabs(P.adv_speed);
+    const int64_t nc = int64_t(P.nx) * P.ny;
+    double best = 0.0;
+#pragma omp parallel if (nc > 8192)
+    {
+        double mine = 0.0;
+#pragma omp for schedule(static) nowait
+        for (int64_t c = 0; c < nc; ++c) mine = tmax(mine, cell_speed(P, U, nc, c, dir));
+#pragma omp critical
+        best = tmax(best, mine);
     }
     return best;
 }
@@ -531,9 +557,9 @@ template <class T>
 void rhs_with_speeds(const Problem& P, const T* U, T* Lout, const Speeds<T>& a) {
     const int nv = nvar_of(P.system);
     const int64_t nx = P.nx, ny = P.ny, nc = nx * ny;
-    // x-sweep, one grid row at a time
-#pragma omp parallel for schedule(static) if (nc > 4096)
-    for (int64_t j = 0; j < ny; ++j) {
+    // x-sweep, one grid row at a time; the rows are spread over the OpenMP threads, or, for a
+    // single row (1D), its cells and interfaces are
+    auto x_row = [&](int64_t j, bool par) {
         std::vector<T> line((nx + 6) * nv), flux((nx + 1) * nv);
         LineCells<T> lc;
         for (int64_t p = 0; p < nx + 6; ++p) {
@@ -541,12 +567,19 @@ void rhs_with_speeds(const Problem& P, const T* U, T* Lout, const Speeds<T>& a) 
             for (int k = 0; k < nv; ++k) line[p * nv + k] = U[k * nc + j * nx + src];
             if (nv > 1 && ghost_mirrored(p - 3, nx, P.bc_x)) line[p * nv + 1] = -line[p * nv + 1];
         }
-        line_cells(P, line.data(), nx + 6, nv, a.ax, lc);
+        line_cells(P, line.data(), nx + 6, nv, a.ax, lc, par);
+#pragma omp parallel for schedule(static) if (par && nx > 4096)
         for (int64_t f = 0; f <= nx; ++f)   // interface f - 1/2, between padded cells f+2, f+3
             interface_flux(P, lc, nv, f + 2, &flux[f * nv], a.fx);
         for (int64_t i = 0; i < nx; ++i)
             for (int k = 0; k < nv; ++k)
                 Lout[k * nc + j * nx + i] = -((flux[(i + 1) * nv + k] - flux[i * nv + k]) / T(P.dx));
+    };
+    if (ny == 1) {
+        x_row(0, true);
+    } else {
+#pragma omp parallel for schedule(static) if (nc > 4096)
+        for (int64_t j = 0; j < ny; ++j) x_row(j, false);
     }
     if (P.system != SYS_EULER2D) return;
     // y-sweep, one grid column at a time, state permuted to (rho, rho v, rho u, E)
@@ -591,10 +624,13 @@ template <class RhsFn>
 void ssp_rk3(int64_t n, double* U, double dt, RhsFn L) {
     std::vector<double> U0(U, U + n), U1(n), U2(n), K(n);
     L(U0.data(), K.data());
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (int64_t c = 0; c < n; ++c) U1[c] = U0[c] + dt * K[c];
     L(U1.data(), K.data());
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (int64_t c = 0; c < n; ++c) U2[c] = 0.75 * U0[c] + 0.25 * (U1[c] + dt * K[c]);
     L(U2.data(), K.data());
+#pragma omp parallel for schedule(static) if (n > 65536)
     for (int64_t c = 0; c < n; ++c) U[c] = U0[c] / 3.0 + 2.0 / 3.0 * (U2[c] + dt * K[c]);
 }
 

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libwenozn.so")
-SOURCES = ("flux_kernels.cu", "update_kernels.cu", "api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu", "adjoint_kernels.cu", "adjoint_api.cu")
+SOURCES = ("flux_kernels.cu", "update_kernels.cu", "api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu",
+           "adjoint_kernels.cu", "adjoint_api.cu", "diag.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -204,6 +204,58 @@ wenozn_status wenozn_rk3_step(const wenozn_problem* p, double* U, double dt, dou
     return WENOZN_OK;
 }
 
+wenozn_status wenozn_rk3_step_host(const wenozn_problem* p, const double* U_host_in, double* U_host_out,
+                                   double* U_dev, double dt, double t_remaining, double* dt_out, void* ws,
+                                   size_t ws_bytes, void* stream) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!U_host_in || !U_host_out || !U_dev || !ws || std::isnan(dt) || std::isnan(t_remaining) || std::isinf(dt))
+        return WENOZN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    const Layout lay = layout_of(*p);
+    if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = size_t(nvar_of(p->system)) * size_t(p->nx) * size_t(p->ny) * sizeof(double);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    double* u1 = reinterpret_cast<double*>(ws_base(ws) + lay.u1);
+    double* u2 = reinterpret_cast<double*>(ws_base(ws) + lay.u2);
+    note_status(stream, &ctrl->status);
+    cudaError_t e = cudaMemcpyAsync(U_dev, U_host_in, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = rk3_stages(*p, lay, ws, U_dev, U_dev, u1, u2, dt, t_remaining, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(U_host_out, U_dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dt_out) {
+        e = cudaMemcpyAsync(dt_out, &ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return cuda_status(e);
+}
+
+wenozn_status wenozn_cfl_dt(const wenozn_problem* p, const double* U, double* dt_out, void* ws, size_t ws_bytes,
+                            void* stream) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (!U || !ws) return WENOZN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    const Layout lay = layout_of(*p);
+    if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl);
+    note_status(stream, &ctrl->status);
+    cudaError_t e = clear_speeds(ctrl, s);
+    if (e == cudaSuccess)
+        e = launch_max_wavespeed(p->system, U, int64_t(p->nx) * p->ny, p->gamma, p->adv_speed, ctrl->alpha[0],
+                                 &ctrl->status, s);
+    if (e == cudaSuccess) {
+        UpdateArgs u = update_args(*p, ctrl, nullptr, nullptr);
+        e = launch_cfl_dt(p->system, u, s);
+    }
+    if (e == cudaSuccess && dt_out) {
+        e = cudaMemcpyAsync(dt_out, &ctrl->dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return cuda_status(e);
+}
+
 wenozn_status wenozn_rk3_run(const wenozn_problem* p, double* U, int64_t nsteps, double dt, void* ws,
                              size_t ws_bytes, void* stream) {
     wenozn_status st = check_problem(p);
@@ -301,17 +353,6 @@ wenozn_status wenozn_last_error(void* stream, int32_t* device_status) {
     if (e != cudaSuccess) return WENOZN_ECUDA;
     *device_status = host;
     return WENOZN_OK;
-}
-
-wenozn_status wenozn_check_reciprocal(const double* d, int64_t n, double* fast, double* ieee,
-                                      void* stream) {
-    if (!d || !fast || !ieee || n < 1 || n > (int64_t(1) << 31)) return WENOZN_EINVAL;
-    return cuda_status(launch_rcp_check(d, n, fast, ieee, static_cast<cudaStream_t>(stream)));
-}
-
-wenozn_status wenozn_fp64_fma_rate(int64_t fmas_per_thread, double* gflops, void* stream) {
-    if (!gflops || fmas_per_thread < 4 || fmas_per_thread > (int64_t(1) << 32)) return WENOZN_EINVAL;
-    return cuda_status(measure_fma_rate(fmas_per_thread, gflops, static_cast<cudaStream_t>(stream)));
 }
 
 const char* wenozn_status_string(wenozn_status s) {

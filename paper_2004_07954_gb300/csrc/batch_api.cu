@@ -1,6 +1,9 @@
 // C ABI of the batched 1D Euler path (declarations and contracts in include/wenozn.h).
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "../../include/wenozn.h"
 #include "launch.h"
@@ -54,6 +57,43 @@ wenozn_status check_batch(const wenozn_batch_params* bp, const int64_t* offsets,
 }
 
 int default_shape() { return 3; }   // 512 interfaces x 256 threads
+
+// Process-wide tuning table: the tile shape the tuner found fastest, keyed by what decides
+// it (the device, the boundary's ghost map, and the binary orders of magnitude of the mean
+// instance size and of the batch's total cell count; every batch is 1D Euler).  A step with
+// shape = -1 uses the entry of its key, so a batch of a size class already tuned in this
+// process is not timed again.
+struct TuneKey {
+    int dev, bc, mean_log2, total_log2;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, bc, mean_log2, total_log2) < std::tie(o.dev, o.bc, o.mean_log2, o.total_log2);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+int floor_log2(int64_t v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+TuneKey key_of(const wenozn_batch_params* bp, int64_t cells) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    return TuneKey{dev, bp->bc, floor_log2(cells / bp->nbatch), floor_log2(cells)};
+}
+
+// The shape a step uses: the caller's, else the table's entry for this batch, else the default.
+int resolve_shape(const wenozn_batch_params* bp, int64_t cells) {
+    if (bp->shape >= 0) return bp->shape;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key_of(bp, cells));
+    return it != g_tuned.end() ? it->second : default_shape();
+}
 
 struct TileSizes { int v[kNumBatchShapes]; };
 
@@ -209,7 +249,7 @@ wenozn_status wenozn_batch_rk3_step(const wenozn_batch_params* bp, const int64_t
     if (!U || !ws || reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
     const BatchLayout L = batch_layout(bp->nbatch, cells);
     if (ws_bytes < L.total) return WENOZN_ENOMEM_WS;
-    const int shape = bp->shape < 0 ? default_shape() : bp->shape;
+    const int shape = resolve_shape(bp, cells);
     const Ptrs bptr = ptrs_of(ws, L);
     note_status(stream, &bptr.ctrl->status);
     cudaError_t e = step_launches(bp, bptr, cells, U, shape, static_cast<cudaStream_t>(stream));
@@ -221,9 +261,21 @@ wenozn_status wenozn_batch_tune(wenozn_batch_params* bp, const int64_t* offsets,
     int64_t cells = 0;
     wenozn_status st = check_batch(bp, offsets, &cells);
     if (st != WENOZN_OK) return st;
-    if (!U || !ws || steps < 1 || reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    if (!U || !ws || steps < 0 || reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
     const BatchLayout L = batch_layout(bp->nbatch, cells);
     if (ws_bytes < L.total) return WENOZN_ENOMEM_WS;
+    const TuneKey key = key_of(bp, cells);
+    if (steps == 0) {            // the table's entry for this size class, if there is one
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            bp->shape = it->second;
+            if (ms_per_step)
+                for (int i = 0; i < kNumBatchShapes; ++i) ms_per_step[i] = 0.0f;
+            return WENOZN_OK;
+        }
+    }
+    if (steps == 0) steps = 2;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Ptrs p = ptrs_of(ws, L);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -253,6 +305,17 @@ wenozn_status wenozn_batch_tune(wenozn_batch_params* bp, const int64_t* offsets,
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return WENOZN_ECUDA;
     bp->shape = best;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    return WENOZN_OK;
+}
+
+wenozn_status wenozn_batch_resolved_shape(const wenozn_batch_params* bp, const int64_t* offsets, int32_t* shape) {
+    int64_t cells = 0;
+    wenozn_status st = check_batch(bp, offsets, &cells);
+    if (st != WENOZN_OK) return st;
+    if (!shape) return WENOZN_EINVAL;
+    *shape = resolve_shape(bp, cells);
     return WENOZN_OK;
 }
 

@@ -68,6 +68,9 @@ struct UpdateArgs {
     double dt_fixed, t_remaining, cfl, dx, dy, gamma, adv_speed;
 };
 cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s);
+// ctrl->dt = the CFL step of the LF speeds in ctrl->alpha[0] (a.dt_fixed <= 0, no clipping
+// unless a.t_remaining > 0), in the update kernel's operation order.
+cudaError_t launch_cfl_dt(int system, const UpdateArgs& a, cudaStream_t s);
 
 // Global LF speeds of U folded into dst[0..1] (bit-pattern max; dst must start at 0) and,
 // when dst_f is not null, the per-field speeds into dst_f[dir][3] (|u-c|, |u|, |u+c|).
@@ -127,11 +130,6 @@ cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
 // Remembers the device status word the most recent stepping call on `stream` wrote to
 // (read back by wenozn_last_error).
 void note_status(void* stream, int32_t* status_dev);
-
-// Times sm_count x 2 blocks of 256 threads, each thread fmas_per_thread independent FP64
-// FMAs (four chains), after one warm-up launch; writes the achieved GFLOP/s (2 per FMA).
-cudaError_t measure_fma_rate(int64_t fmas_per_thread, double* gflops, cudaStream_t s);
-cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s);
 
 cudaError_t launch_fill_ghosts(int nv, int nx, int ny, int bc_x, int bc_y, int two_d,
                                double* U_padded, cudaStream_t s);

@@ -1,6 +1,6 @@
 // Cell-wise kernels: flux difference + SSP-RK3 stage update (with the next stage's LF
-// speeds folded in), the standalone LF-speed reduction, the single-line reconstruction, the
-// ghost-cell fill, and the FP64 rate probe behind wenozn_fp64_fma_rate.
+// speeds folded in), the standalone LF-speed reduction, the single-line reconstruction and
+// the ghost-cell fill.
 #include "launch.h"
 #include "speed_screen.cuh"
 
@@ -175,6 +175,11 @@ __global__ void __launch_bounds__(T, T >= 256 ? 4 : 1) update_kernel(UpdateArgs 
     }
 }
 
+// The CFL step of the LF speeds in slot 0 (one thread), the step the first RK stage takes.
+__global__ void __launch_bounds__(32) cfl_dt_kernel(UpdateArgs a, int system) {
+    if (threadIdx.x == 0) a.ctrl->dt = step_dt(a, system);
+}
+
 template <int NV, int T>
 __global__ void __launch_bounds__(T) max_wavespeed_kernel(const double* U, int64_t nc, double gamma,
                                                           unsigned long long* dst, int32_t* status,
@@ -250,14 +255,6 @@ __global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, 
                        : zn_flux_w(s[5], s[4], s[3], s[2], s[1], eps4, kappa, weights);
 }
 
-__global__ void __launch_bounds__(kThreads) rcp_check_kernel(const double* d, int64_t n, double* fast,
-                                                              double* ieee) {
-    const int64_t i = blockIdx.x * int64_t(kThreads) + threadIdx.x;
-    if (i >= n) return;
-    fast[i] = rcp_nr(d[i]);
-    ieee[i] = 1.0 / d[i];
-}
-
 // x-ghosts of the interior rows (phase 0) or y-ghosts of every padded column (phase 1).
 __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int nx, int ny, int bc_x,
                                                           int bc_y, int two_d, int phase) {
@@ -285,24 +282,6 @@ __global__ void __launch_bounds__(kThreads) ghost_kernel(double* U, int nv, int 
         const double val = plane[int64_t(ghost_src(gj, ny, bc_y) + 3) * px + col];
         plane[int64_t(gj + 3) * px + col] = (k == 2 && ghost_mirrored(gj, ny, bc_y)) ? -val : val;
     }
-}
-
-// FP64 FMA rate probe: four independent FMA chains per thread and no memory traffic in the
-// loop; every thread stores its sum through a pointer argument (into a static buffer for up
-// to kProbeBlocks blocks).  Measured on GB300: a conditional store, or a store to the
-// device symbol itself, made the same loop run at 0.84 of this rate.
-constexpr int kProbeBlocks = 512;
-__device__ double g_fma_out[kProbeBlocks * kThreads];
-
-__global__ void __launch_bounds__(kThreads) fma_probe_kernel(double* out, int iters, double a, double b) {
-    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
-    for (int it = 0; it < iters; ++it) {
-        x0 = fma(x0, a, b);
-        x1 = fma(x1, a, b);
-        x2 = fma(x2, a, b);
-        x3 = fma(x3, a, b);
-    }
-    out[blockIdx.x * kThreads + threadIdx.x] = (x0 + x1) + (x2 + x3);
 }
 
 unsigned grid_for(int64_t items, int cap, int threads = kThreads) {
@@ -364,6 +343,11 @@ cudaError_t launch_update(int system, const UpdateArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_cfl_dt(int system, const UpdateArgs& a, cudaStream_t s) {
+    cfl_dt_kernel<<<1, 32, 0, s>>>(a, system);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, double gamma,
                                  double adv_speed, unsigned long long* dst, int32_t* status,
                                  cudaStream_t s, unsigned long long* dst_f) {
@@ -380,37 +364,6 @@ cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, 
                                double eps, double A, cudaStream_t s, int weights) {
     const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
     reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A), weights);
-    return cudaGetLastError();
-}
-
-cudaError_t measure_fma_rate(int64_t fmas_per_thread, double* gflops, cudaStream_t s) {
-    const int grid = 2 * sm_count() < kProbeBlocks ? 2 * sm_count() : kProbeBlocks;
-    const int iters = int(fmas_per_thread / 4);
-    double* out = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&out), g_fma_out);
-    if (e == cudaSuccess) e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    if (e == cudaSuccess) {
-        fma_probe_kernel<<<grid, kThreads, 0, s>>>(out, iters, 0.999999, 1e-7);     // warm-up
-        e = cudaEventRecord(e0, s);
-    }
-    if (e == cudaSuccess) {
-        fma_probe_kernel<<<grid, kThreads, 0, s>>>(out, iters, 0.999999, 1e-7);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (e == cudaSuccess) *gflops = ms > 0.0f ? 2.0 * 4.0 * double(iters) * grid * kThreads / (ms * 1e6) : 0.0;
-    return e;
-}
-
-cudaError_t launch_rcp_check(const double* d, int64_t n, double* fast, double* ieee, cudaStream_t s) {
-    rcp_check_kernel<<<unsigned((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, n, fast, ieee);
     return cudaGetLastError();
 }
 

@@ -68,8 +68,7 @@ def rollout(U0: torch.Tensor, p: W.wenozn_problem, dt: float, steps: int, checkp
     return WenoZNRollout.apply(U0, p, float(dt), int(steps), int(checkpoint_every), ws)
 
 
-def cfl_step(p: W.wenozn_problem, U: torch.Tensor) -> float:
-    """cfl dx / max(|u| + c) of U (1D), evaluated on the device by the library."""
-    a = torch.zeros(2, dtype=torch.float64, device=U.device)
-    W.wenozn_max_wavespeed(p, U, a)
-    return p.cfl * p.dx / float(a[0].item())
+def cfl_step(p: W.wenozn_problem, U: torch.Tensor, ws: torch.Tensor | None = None) -> float:
+    """The CFL step of U (cfl dx / max(|u| + c) in 1D), computed by the library on the device
+    (wenozn_cfl_dt); ws is any workspace of p (a fresh one if None)."""
+    return W.wenozn_cfl_dt(p, U, W.workspace(p, U.device) if ws is None else ws)

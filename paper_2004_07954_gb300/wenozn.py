@@ -71,6 +71,9 @@ _SIGNATURES = {
     "wenozn_rhs_noalloc": [_P, _VP, _VP, _VP],
     "wenozn_rk3_step": [_P, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                         _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_step_host": [_P, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                             _VP, ctypes.c_size_t, _VP],
+    "wenozn_cfl_dt": [_P, _VP, ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
     "wenozn_last_error": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
@@ -91,6 +94,7 @@ _SIGNATURES = {
     "wenozn_batch_rk3_step": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, ctypes.c_size_t, _VP],
     "wenozn_batch_tune": [ctypes.POINTER(wenozn_batch_params), _VP, _VP, _VP, ctypes.c_size_t, ctypes.c_int32,
                           ctypes.POINTER(ctypes.c_float), _VP],
+    "wenozn_batch_resolved_shape": [ctypes.POINTER(wenozn_batch_params), _VP, ctypes.POINTER(ctypes.c_int32)],
     "wenozn_batch_state": [_VP, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                            ctypes.POINTER(ctypes.c_void_p)],
 }
@@ -254,6 +258,39 @@ def wenozn_rk3_step(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, dt: fl
                                  ws.numel() * ws.element_size(), _stream(stream))
     _check("wenozn_rk3_step", code)
     return out.value if return_dt else None
+
+
+def _host_ptr(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 host tensor (pinned for asynchronous copies)")
+    return t.data_ptr()
+
+
+def wenozn_rk3_step_host(p: wenozn_problem, U_host_in: torch.Tensor, U_host_out: torch.Tensor,
+                         U_dev: torch.Tensor, ws: torch.Tensor, dt: float = 0.0, t_remaining: float = 0.0,
+                         return_dt: bool = False, stream=None):
+    """One RK3 step of a host-resident state through the device buffer U_dev (copies and
+    step enqueued on `stream`)."""
+    for t, name in ((U_host_in, "U_host_in"), (U_host_out, "U_host_out"), (U_dev, "U_dev")):
+        if t.numel() != p.nvar * p.nx * p.ny:
+            raise ValueError(f"{name}: expected {p.nvar * p.nx * p.ny} values")
+    out = ctypes.c_double(0.0)
+    code = lib().wenozn_rk3_step_host(ctypes.byref(p), _host_ptr(U_host_in, "U_host_in"),
+                                      _host_ptr(U_host_out, "U_host_out"), _dev_ptr(U_dev, "U_dev"), float(dt),
+                                      float(t_remaining), ctypes.byref(out) if return_dt else None, _ws_ptr(ws),
+                                      ws.numel() * ws.element_size(), _stream(stream))
+    _check("wenozn_rk3_step_host", code)
+    return out.value if return_dt else None
+
+
+def wenozn_cfl_dt(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, stream=None) -> float:
+    """The CFL step of U (the step wenozn_rk3_step would take), computed on the device."""
+    out = ctypes.c_double(0.0)
+    _check("wenozn_cfl_dt", lib().wenozn_cfl_dt(ctypes.byref(p), _dev_ptr(U, "U"), ctypes.byref(out), _ws_ptr(ws),
+                                                ws.numel() * ws.element_size(), _stream(stream)))
+    return out.value
 
 
 def wenozn_last_error(stream=None) -> int:
@@ -456,9 +493,18 @@ class Batch:
             ctypes.byref(self.bp), self.offsets.ctypes.data, _dev_ptr(U, "U"), self.ws.data_ptr(),
             self.ws.numel(), _stream(stream)))
 
+    def shape_in_use(self) -> int:
+        """The tile shape a step of this batch uses (its own, the tuning table's or the default)."""
+        sh = ctypes.c_int32(0)
+        _check("wenozn_batch_resolved_shape", lib().wenozn_batch_resolved_shape(
+            ctypes.byref(self.bp), self.offsets.ctypes.data, ctypes.byref(sh)))
+        return sh.value
+
     def tune(self, U_scratch: torch.Tensor, steps: int = 2, stream=None):
         """Times every compiled tile shape on U_scratch (advanced by the trials) and keeps the
-        fastest; returns the per-shape milliseconds per step."""
+        fastest, also in the process-wide table of this batch's size class; steps = 0 reuses
+        the table's entry without timing when there is one.  Returns the per-shape
+        milliseconds per step (zeros when nothing was timed)."""
         ms = (ctypes.c_float * wenozn_batch_num_shapes())()
         _check("wenozn_batch_tune", lib().wenozn_batch_tune(
             ctypes.byref(self.bp), self.offsets.ctypes.data, _dev_ptr(U_scratch, "U"), self.ws.data_ptr(),

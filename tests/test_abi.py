@@ -109,6 +109,15 @@ def test_newer_entry_points_reject_bad_arguments_on_host(wz):
     # the constant A of Eq. (function) outside [1e-6, 1e6]
     for a in (0.0, 1e-7, 1e7):
         assert L.wenozn_reconstruct(A, 10, A, 1, 1e-40, a, None) == wz.WENOZN_EINVAL
+    # host-buffer step and CFL step: no state, no staging buffer, no workspace
+    h = (ctypes.c_double * 64)()
+    assert L.wenozn_rk3_step_host(ctypes.byref(p1), None, h, A, 0.0, 0.0, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_step_host(ctypes.byref(p1), h, h, None, 0.0, 0.0, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_step_host(ctypes.byref(p1), h, h, A, float("nan"), 0.0, None, A, 1 << 30, None) == \
+        wz.WENOZN_EINVAL
+    assert L.wenozn_rk3_step_host(ctypes.byref(p1), h, h, A, 0.0, 0.0, None, A, 16, None) == wz.WENOZN_ENOMEM_WS
+    assert L.wenozn_cfl_dt(ctypes.byref(p1), None, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_cfl_dt(ctypes.byref(p1), A, None, ctypes.c_void_p(257), 1 << 30, None) == wz.WENOZN_EINVAL
     # FP64 rate probe: sizes outside [4, 2^32], no result pointer
     g = ctypes.c_double(0.0)
     for bad in (0, 3, (1 << 32) + 1):

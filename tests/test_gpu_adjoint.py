@@ -166,10 +166,8 @@ def test_chained_keep_and_reverse_equal_the_single_steps(wz):
 
 
 def test_chained_reverse_is_repeatable_at_the_benchmark_size(wz):
-    """N = 8192, 150 steps: inside a chain the interface kernels start before the previous
-    gather has finished (only lam-free work runs before their wait).  Three runs of the
-    chained reverse and the step-by-step reverse (each step's first stage waits first) agree
-    bit for bit."""
+    """N = 8192, 150 steps: three runs of the chained reverse (one call, programmatically
+    dependent launches) and the step-by-step reverse agree bit for bit."""
     n, m = 8192, 150
     p = wz.wenozn_problem_init(1, n, 1, 10.0 / n, 1.0, bc_x=0)
     U0 = dev(inputs.adjoint_ic(n, seed=3))

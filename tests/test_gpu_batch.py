@@ -144,3 +144,30 @@ def test_batch_full_size_sampled(wz, orc):
         w = u[:, 0, :]
         assert np.abs(got[:, offsets[b]:offsets[b + 1]] - w).max() <= STEP_TOL * np.abs(w).max(), b
     assert bt.status() == 0
+
+
+def test_batch_tuning_table_is_consulted(wz):
+    """A tuned size class is remembered for the process: another batch of the same class (same
+    boundary and instance sizes, other data) steps with the tuned shape and, asked to tune with
+    steps = 0, takes it without timing; a batch of another class keeps the default."""
+    sizes, offsets, dx, U0 = _batch(40, seed=21, n_min=100, n_max=900)
+    periodic = wz.WENOZN_BC_PERIODIC
+    U = torch.from_numpy(U0.copy()).cuda()
+    a = wz.Batch(offsets, dx, U, bc=periodic)
+    assert a.shape_in_use() == 3                      # the default: nothing tuned for this class yet
+    a.tune(U.clone(), steps=1)
+    chosen = a.bp.shape
+    other = np.concatenate([inputs.euler1d_ic(int(n), 500 + b)[:, 0, :] for b, n in enumerate(sizes)], axis=1)
+    V = torch.from_numpy(other).cuda()
+    b = wz.Batch(offsets, dx, V, bc=periodic)
+    assert b.bp.shape == -1 and b.shape_in_use() == chosen
+    ms = b.tune(V.clone(), steps=0)
+    assert b.bp.shape == chosen and all(m == 0.0 for m in ms)
+    W = V.clone()
+    b.bp.shape = -1
+    b.step(V)                                         # the table's shape ...
+    c = wz.Batch(offsets, dx, W, bc=periodic, shape=chosen)
+    c.step(W)                                         # ... is the explicit one
+    assert torch.equal(V, W)
+    d = wz.Batch(offsets, dx, W.clone(), bc=wz.WENOZN_BC_OUTFLOW)
+    assert d.shape_in_use() == 3

@@ -1,0 +1,209 @@
+"""Final-time parity at the configurations' own lengths, and the advection convergence orders
+on the GPU.
+
+One rule decides every case (every seed of a family, every instance of a batch), with no
+case picked by hand: the GPU state must lie within FINAL_TOL = 1e-9 (relative to the largest
+value) of the oracle's.  Where it does not, the oracle is run again from its initial data
+moved by one unit in the last place (two seeded sign patterns).  The cells where that
+response comes within a factor 4 of FINAL_TOL, widened by 10 cells in every direction, form
+the case's ill-conditioned region; outside it every cell must still meet FINAL_TOL, inside it
+every cell must lie within four times the largest response in the region, which is how far
+rounding alone moves this solution there.  Such a case is ill-conditioned in FP64, not wrong:
+with eps = 1e-40 the weights respond to rounding-level differences, so where the solution
+develops grid-scale structure (a shock running through the entropy waves, fluid at rest at
+rounding-noise velocity beside an outflow boundary) one-ulp changes of the data grow by many
+orders of magnitude, in the oracle as on the GPU.
+
+Sizes: the advection orders at N = 40..320 (Sec. 4.2); 1D Euler (seeded Shu-Osher family,
+Sec. 4.3.1) to t = 1.8 for seeds 0..9 at N = 200 and 1000 and for seed 0 at N = 2^14; 2D Euler
+(seeded four-quadrant problems, Sec. 4.4) over 200 CFL steps for seeds 0..4 at 256^2; 200
+batched instances of sizes 128..2048 to t_final = 1.8."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle_pool
+from paper_2004_07954_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FINAL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def wz():
+    from paper_2004_07954_gb300 import build, wenozn
+    build.build()
+    assert torch.cuda.is_available(), "CUDA device required"
+    return wenozn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _dilate(mask: np.ndarray, w: int) -> np.ndarray:
+    """mask widened by w cells in every direction of a [ny][nx] array (edges clamped)."""
+    out = mask.copy()
+    for axis in (0, 1):
+        base = out.copy()
+        n = base.shape[axis]
+        for s in range(1, w + 1):
+            out |= np.take(base, np.clip(np.arange(n) - s, 0, n - 1), axis=axis)
+            out |= np.take(base, np.clip(np.arange(n) + s, 0, n - 1), axis=axis)
+    return out
+
+
+def assert_final_parity(got, want, perturbed, label):
+    """The rule above.  `perturbed()` returns the oracle's results from the initial data moved
+    by one ulp with the sign patterns 0 and 1 (called only when needed).  Returns the number
+    of cells in the ill-conditioned region (0 when the case meets FINAL_TOL everywhere)."""
+    bar = FINAL_TOL * np.abs(want).max()
+    diff = np.abs(got - want).reshape(want.shape[0], -1, want.shape[-1]).max(axis=0)    # [ny][nx]
+    if diff.max() <= bar:
+        return 0
+    resp = np.zeros_like(diff)
+    for res in perturbed():
+        d = np.abs(res - want).reshape(want.shape[0], -1, want.shape[-1]).max(axis=0)
+        resp = np.maximum(resp, d)
+    region = _dilate(resp > bar / 4.0, 10)
+    inside = max(bar, 4.0 * resp[region].max(initial=0.0))
+    out_worst = diff[~region].max(initial=0.0) / bar
+    in_worst = diff[region].max(initial=0.0) / inside
+    assert out_worst <= 1.0, f"{label}: {out_worst:.3g} x FINAL_TOL outside the ill-conditioned region"
+    assert in_worst <= 1.0, f"{label}: {in_worst:.3g} x the bar inside it (response {resp.max() / bar:.3g} x FINAL_TOL)"
+    return int(region.sum())
+
+
+# ------------------------------------------------------------------ advection orders (Sec. 4.2)
+@pytest.mark.parametrize("which", ["sin", "critical"])
+def test_advection_orders_on_gpu(wz, orc, which):
+    """u_t + u_x = 0 on [-1, 1], periodic, u0 = sin(pi x) and sin(pi x - sin(pi x)/pi) (a
+    first-order critical point), N = 40, 80, 160, 320 to T = 2 with the step of R14: every N
+    within 1e-9 of the oracle, the GPU's own L1 and Linf errors against the exact solution
+    falling at fifth order (between successive N: 4.7 <= order <= 5.3), and within 10 % of
+    the linear fifth-order scheme (WENO-ZN's weights reduce to it on smooth data) at N >= 80."""
+    T = 2.0
+    errs, lin = [], []
+    for n in (40, 80, 160, 320):
+        _, dx = inputs.advection_grid(n)
+        dt, steps = inputs.advection_dt(n, T)
+        U0 = inputs.advection_ic(n, which)
+        exact = inputs.advection_exact(n, which, T)
+        res = {}
+        for weights in (wz.WENOZN_WEIGHTS_ZN, wz.WENOZN_WEIGHTS_LINEAR):
+            p = wz.wenozn_problem_init(wz.WENOZN_ADVECTION_1D, n, 1, dx, 1.0, bc_x=wz.WENOZN_BC_PERIODIC,
+                                       weights=weights)
+            S = wz.Solver(p)
+            t = dev(U0)
+            S.steps(t, steps - 1, dt)                     # chained fixed steps
+            S.step(t, dt=T - (steps - 1) * dt)            # the last one lands on T
+            res[weights] = t.cpu().numpy()
+        got = res[wz.WENOZN_WEIGHTS_ZN]
+        P = orc.problem(orc.ADV1D, n, 1, dx=dx, bc_x=orc.PERIODIC)
+        want, nsteps = orc.run(P, U0, T, dt)
+        assert nsteps == steps
+        assert np.abs(got - want).max() <= FINAL_TOL * np.abs(want).max(), n
+        e = np.abs(got - exact).ravel()
+        el = np.abs(res[wz.WENOZN_WEIGHTS_LINEAR] - exact).ravel()
+        errs.append((e.mean(), e.max()))
+        lin.append((el.mean(), el.max()))
+    for (l1a, lia), (l1b, lib) in zip(errs, errs[1:]):
+        assert 4.7 <= math.log2(l1a / l1b) <= 5.3
+        assert 4.7 <= math.log2(lia / lib) <= 5.3
+    for (z1, zi), (l1, li) in list(zip(errs, lin))[1:]:
+        assert z1 <= 1.1 * l1 and zi <= 1.1 * li
+
+
+# ------------------------------------------------------------------ 1D Euler to t = 1.8 (Sec. 4.3.1)
+CASES_1D = [(200, s) for s in range(10)] + [(1000, s) for s in range(10)] + [(1 << 14, 0)]
+
+
+@pytest.mark.parametrize("n,seed", CASES_1D)
+def test_euler1d_final_time(wz, orc, n, seed):
+    T = 1.8
+    U0 = inputs.euler1d_ic(n, seed)
+    _, dx = inputs.euler1d_grid(n)
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, n, 1, dx, 1.0)
+    S = wz.Solver(p)
+    t = dev(U0)
+    steps = S.run(t, T)
+    assert S.status() == 0
+    got = t.cpu().numpy()
+    P = orc.problem(orc.EULER1D, n, 1, dx=dx)
+    want, steps_o = orc.run(P, U0, T)
+    assert steps == steps_o
+
+    def perturbed():
+        if n <= 4096:
+            return [orc.run(P, oracle_pool.one_ulp(U0, draw), T)[0] for draw in (0, 1)]
+        # the two long runs side by side, each on half the cores
+        half = max(1, (os.cpu_count() or 2) // 2)
+        jobs = [(n, dx, 1, oracle_pool.one_ulp(U0, draw), T) for draw in (0, 1)]
+        return [u for u, _ in oracle_pool.run_1d_many(jobs, workers=2, threads=half)]
+
+    assert_final_parity(got, want, perturbed, f"1D n={n} seed={seed}")
+
+
+# ------------------------------------------------------------------ 2D Euler, 200 steps (Sec. 4.4)
+@pytest.mark.parametrize("seed", range(5))
+def test_euler2d_200_steps(wz, orc, seed):
+    n, K = 256, 200
+    U0 = inputs.euler2d_ic(n, n, seed)
+    p = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, n, n, 1.0 / n, 1.0 / n)
+    S = wz.Solver(p)
+    t = dev(U0)
+    S.steps(t, K)                                          # the chained call the benchmark times
+    dt_gpu = wz.wenozn_workspace_dt(S.ws).item()
+    assert S.status() == 0
+    got = t.cpu().numpy()
+    P = orc.problem(orc.EULER2D, n, n, dx=1.0 / n, dy=1.0 / n)
+
+    def oracle_run(U):
+        dt = 0.0
+        for _ in range(K):
+            U, dt = orc.rk3_step(P, U)
+        return U, dt
+
+    want, dt_o = oracle_run(U0)
+    assert dt_gpu == pytest.approx(dt_o, rel=1e-12)
+    assert_final_parity(got, want, lambda: [oracle_run(oracle_pool.one_ulp(U0, d))[0] for d in (0, 1)],
+                        f"2D seed={seed}")
+
+
+# ------------------------------------------------------------------ batched instances to t_final
+def test_batch_to_t_final(wz):
+    """200 instances of the 1D Euler family, sizes log-uniform in [128, 2048], each advanced
+    with its own CFL step to t_final = 1.8 by the batched kernel (steps repeated until every
+    instance is done), against the oracle run on every instance separately (spawned pool)."""
+    T, B = 1.8, 200
+    sizes, offsets, U0 = inputs.euler1d_batch(B, 5, 128, 2048)
+    dx = 10.0 / sizes
+    U = dev(U0)
+    bt = wz.Batch(offsets, dx, U, t_final=T)
+    steps = 0
+    while True:
+        for _ in range(50):
+            bt.step(U)
+        steps += 50
+        if bt.times().min().item() >= T or steps > 200000:
+            break
+    assert bt.status() == 0
+    assert np.all(bt.times().cpu().numpy() == T)
+    got = U.cpu().numpy()
+    jobs = [(int(sizes[b]), float(dx[b]), 1, U0[:, offsets[b]:offsets[b + 1]].reshape(3, 1, -1).copy(), T)
+            for b in range(B)]
+    want = [u for u, _ in oracle_pool.run_1d_many(jobs)]
+    mine = [got[:, offsets[b]:offsets[b + 1]].reshape(3, 1, -1) for b in range(B)]
+    # the one-ulp runs of the instances that miss FINAL_TOL, all at once on the pool
+    miss = [b for b in range(B) if np.abs(mine[b] - want[b]).max() > FINAL_TOL * np.abs(want[b]).max()]
+    pert_jobs = [(n, d, bc, oracle_pool.one_ulp(u0, draw), tt)
+                 for b in miss for draw in (0, 1) for (n, d, bc, u0, tt) in [jobs[b]]]
+    pert = dict(zip([(b, draw) for b in miss for draw in (0, 1)],
+                    [u for u, _ in oracle_pool.run_1d_many(pert_jobs)] if pert_jobs else []))
+    for b in range(B):
+        assert_final_parity(mine[b], want[b], lambda b=b: [pert[(b, 0)], pert[(b, 1)]],
+                            f"batch instance {b} (n={sizes[b]})")

@@ -5,8 +5,6 @@ Tolerances: relative L-infinity <= 1e-12 for one RHS evaluation or one RK3 step 
 compared bit for bit (a maximum is exact and both sides evaluate the per-cell speed in the
 same IEEE operation order).
 """
-import math
-
 import numpy as np
 import pytest
 import torch
@@ -243,8 +241,8 @@ def test_large_1d_step_parity(wz, orc, bc):
 
 
 def test_2d_chained_steps_repeatable_at_the_benchmark_size(wz):
-    """4096^2, six chained steps (the y sweep of each stage starts beside the x sweep and
-    waits for it before it ends), three times: bit-identical states and steps."""
+    """4096^2, six chained steps (programmatically dependent launches), three times:
+    bit-identical states and steps."""
     n = 4096
     p = gpu_problem(wz, 2, n, n, dx=1.0 / n, dy=1.0 / n)
     U0 = dev(inputs.euler2d_ic(n, n, seed=0))
@@ -259,6 +257,51 @@ def test_2d_chained_steps_repeatable_at_the_benchmark_size(wz):
         else:
             assert torch.equal(U, ref) and dt == dts
     assert S.status() == 0
+
+
+@pytest.mark.parametrize("system,nx,ny,split", [(0, 300, 1, 0), (1, 1000, 1, 0), (1, 700, 1, 1), (2, 77, 53, 0),
+                                                 (2, 40, 33, 1)])
+def test_cfl_dt_bit_exact(wz, orc, system, nx, ny, split):
+    """wenozn_cfl_dt equals the oracle's CFL step (Sec. 4.3 / 4.4) and the step the RK3 call
+    takes, bit for bit."""
+    U = (inputs.advection_ic(nx, "sin") if system == 0 else
+         inputs.euler1d_ic(nx, 6) if system == 1 else inputs.euler2d_ic(nx, ny, 6))
+    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / ny, split=split)
+    S = wz.Solver(p)
+    dt = wz.wenozn_cfl_dt(p, dev(U), S.ws)
+    assert dt == orc.cfl_dt(orc_problem(orc, p), U)
+    assert dt == S.step(dev(U), return_dt=True)
+    assert S.status() == 0
+
+
+@pytest.mark.parametrize("system,nx,ny", [(1, 5000, 1), (2, 200, 150)])
+def test_rk3_step_host_equals_device_step(wz, system, nx, ny):
+    """The host-buffer step (copy in, step, copy out in one call) gives the device step's
+    state and time step bit for bit: pinned and pageable buffers, separate and shared in/out
+    buffers, CFL, fixed and clipped steps, three steps chained through host memory."""
+    U0 = inputs.euler1d_ic(nx, 3) if system == 1 else inputs.euler2d_ic(nx, ny, 3)
+    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / ny)
+    A, B = wz.Solver(p), wz.Solver(p)
+    U_dev = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+    for dt, trem in ((0.0, 0.0), (1e-4, 0.0), (0.0, 1e-5)):
+        for pinned in (True, False):
+            a = dev(U0)
+            want_dt = A.step(a, dt=dt, t_remaining=trem, return_dt=True)
+            h_in = torch.from_numpy(U0.copy())
+            h_out = torch.empty_like(h_in)
+            if pinned:
+                h_in, h_out = h_in.pin_memory(), h_out.pin_memory()
+            got_dt = wz.wenozn_rk3_step_host(p, h_in, h_out, U_dev, B.ws, dt, trem, return_dt=True)
+            assert got_dt == want_dt
+            assert torch.equal(h_out, a.cpu())
+    a = dev(U0)
+    h = torch.from_numpy(U0.copy()).pin_memory()
+    for _ in range(3):
+        A.step(a)
+        wz.wenozn_rk3_step_host(p, h, h, U_dev, B.ws)
+    torch.cuda.synchronize()
+    assert torch.equal(h, a.cpu())
+    assert A.status() == 0 and B.status() == 0
 
 
 def test_rk3_fixed_and_clipped_dt(wz, orc):
@@ -276,83 +319,8 @@ def test_rk3_fixed_and_clipped_dt(wz, orc):
 
 
 # ------------------------------------------------------------------ final time
-def test_advection_final_time(wz, orc):
-    n = 160
-    _, dx = inputs.advection_grid(n)
-    dt, steps = inputs.advection_dt(n, 2.0)
-    for which in ("sin", "critical"):
-        U0 = inputs.advection_ic(n, which)
-        p = gpu_problem(wz, 0, n, dx=dx, bc=0)
-        S = wz.Solver(p)
-        t = dev(U0)
-        assert S.run(t, 2.0, dt) == steps
-        want, _ = orc.run(orc_problem(orc, p), U0, 2.0, dt)
-        assert rel_linf(host(t), want) <= FINAL_TOL
-        err = np.abs(host(t) - inputs.advection_exact(n, which, 2.0)).max()
-        assert err < {"sin": 2e-8, "critical": 5e-7}[which]   # oracle: 9.8e-9, 2.05e-7
-
-
-@pytest.mark.parametrize("seed", [0, 2, 3])
-def test_euler1d_final_time(wz, orc, seed):
-    """Seeded Shu-Osher-type problem, N = 200, outflow, CFL 0.5 to t = 1.8."""
-    n = 200
-    U0 = inputs.euler1d_ic(n, seed)
-    _, dx = inputs.euler1d_grid(n)
-    p = gpu_problem(wz, 1, n, dx=dx)
-    S = wz.Solver(p)
-    t = dev(U0)
-    steps = S.run(t, 1.8)
-    want, steps_o = orc.run(orc_problem(orc, p), U0, 1.8)
-    assert steps == steps_o
-    assert rel_linf(host(t), want) <= FINAL_TOL
-    assert S.status() == 0
-
-
-def test_euler1d_final_time_ill_conditioned(wz, orc):
-    """Seed 1 at t = 1.8 is ill-conditioned in FP64: next to the right outflow boundary the
-    fluid is at rest (u at rounding-noise level) and, with eps = 1e-40, the weights of the
-    acoustic characteristic fields there are set by that noise.  A 1-ulp perturbation of
-    the initial data moves the oracle's own result by 1e-8 - 3e-8 relative in cells 185..199,
-    while the rest of the grid agrees to 1e-13.  So: the 1e-9 bar on cells 0..184, and on
-    the boundary cells a distance within 4x the oracle's own 1-ulp response."""
-    n, seed, T = 200, 1, 1.8
-    U0 = inputs.euler1d_ic(n, seed)
-    _, dx = inputs.euler1d_grid(n)
-    p = gpu_problem(wz, 1, n, dx=dx)
-    P = orc_problem(orc, p)
-    S = wz.Solver(p)
-    t = dev(U0)
-    S.run(t, T)
-    got = host(t)
-    want, _ = orc.run(P, U0, T)
-    scale = np.abs(want).max()
-    sens = 0.0
-    for draw in range(3):
-        sign = np.random.default_rng(draw).choice([-1.0, 1.0], size=U0.shape)
-        pert, _ = orc.run(P, U0 * (1 + 2.0 ** -52 * sign), T)
-        sens = max(sens, np.abs(pert - want).max() / scale)
-        assert np.abs(pert - want)[:, :, :185].max() / scale <= FINAL_TOL
-    assert sens > FINAL_TOL                     # the case really is ill-conditioned
-    diff = np.abs(got - want) / scale
-    assert diff[:, :, :185].max() <= FINAL_TOL
-    assert diff.max() <= 4 * sens
-    assert S.status() == 0
-
-
-def test_euler2d_final_time(wz, orc):
-    n = 48
-    U0 = inputs.euler2d_ic(n, n, seed=0)
-    p = gpu_problem(wz, 2, n, n, dx=1.0 / n, dy=1.0 / n)
-    S = wz.Solver(p)
-    t = dev(U0)
-    P = orc_problem(orc, p)
-    want = U0
-    for _ in range(25):
-        dt = S.step(t, return_dt=True)
-        want, dt_o = orc.rk3_step(P, want)
-        assert dt == pytest.approx(dt_o, rel=1e-9)
-    assert rel_linf(host(t), want) <= FINAL_TOL
-    assert S.status() == 0
+# (advection orders, 1D Euler to t = 1.8, 2D Euler over 200 steps and batched instances to
+# their final time, all under one parity rule: tests/test_gpu_final_time.py)
 
 
 # ------------------------------------------------------------------ full sizes
