@@ -40,9 +40,9 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "bf926e69f14cafd5", "n": 4096, "bytes": 965.7e6, "capture_n": 2560,
+TRAFFIC_CAPTURE = {"sha256_16": "944ffbaca9a378ad", "n": 4096, "bytes": 967.2e6, "capture_n": 2560,
                    "profile": "profiles/flux_kernel_euler2d_2560.md",
-                   "fp64_pipe": {"x": 0.888, "y": 0.889}}   # ncu FP64-pipe busy, same capture
+                   "fp64_pipe": {"x": 0.894, "y": 0.895}}   # ncu FP64-pipe busy, same capture
 
 
 def hbm_peak() -> tuple:
@@ -508,14 +508,16 @@ def run_reference(args, rank: int):
     from paper_2004_07954_gb300 import inputs
     O.build()
     cores = O.num_threads()
-    # size the per-step sample so that warmup + steps finish in about two minutes
-    m = 128
+    # the benchmark's own grid when warmup + steps fit in about three minutes (a 4096^2 step
+    # takes about 3 s on 16 cores), else the largest square sample that does; the rate is
+    # calibrated on one 512^2 step
+    m = min(512, args.n)
     U = inputs.euler2d_ic(m, m, args.seed)
     P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
     t0 = time.perf_counter()
     O.rk3_step(P, U)
     per_cell = (time.perf_counter() - t0) / (m * m)
-    budget = 120.0 / max(1, args.steps + args.warmup)
+    budget = 200.0 / max(1, args.steps + args.warmup)
     m = max(64, min(args.n, int(math.sqrt(budget / max(per_cell, 1e-9)))))
     U = inputs.euler2d_ic(m, m, args.seed)
     P = O.problem(O.EULER2D, m, m, dx=1.0 / m, dy=1.0 / m)
@@ -527,7 +529,9 @@ def run_reference(args, rank: int):
     el = time.perf_counter() - t0
     value = args.steps * m * m / el
     sample = (f"each step: one SSP-RK3 step of the seeded four-quadrant 2D Euler problem on a {m}x{m} "
-              f"grid (bounded sample of the {args.n}x{args.n} workload), plain FP64 C++ oracle")
+              + ("grid (the whole workload)" if m == args.n else
+                 f"grid (bounded sample of the {args.n}x{args.n} workload)")
+              + f", plain FP64 C++ oracle on {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -658,28 +662,21 @@ def main():
                     "frac": round(traffic / (kern[0] / 1e3) / 1e9 / hbm_gbs, 5), "peak_source": hbm_src}}
 
     # ---- end to end: host buffers, copies inside the timed region --------------------
-    # Every step goes through the library's host-buffer call (wenozn_rk3_step_host): it copies
-    # the step's input from pinned host memory to a device staging buffer, takes one RK3 step
-    # and copies the result back, all on its stream.  Steps alternate between two streams,
-    # each with its own staging buffer and workspace, so one step's copies overlap the other
-    # stream's computation.
+    # One library call (wenozn_rk3_stream_host) takes the K steps' states from pinned host
+    # memory and returns their results to pinned host memory: each state is uploaded on an
+    # upload stream into one of two device staging buffers, stepped on the compute stream and
+    # downloaded on a download stream, so the copies of one state overlap the step of the
+    # next; the call is ordered after the work on the compute stream and before what follows.
     host_in = torch.from_numpy(U0).pin_memory()
     host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
     bufs = [torch.empty_like(U) for _ in range(2)]
-    solvers = [S, wenozn.Solver(p)]
-    streams = [stream, torch.cuda.Stream()]
+    up_s, down_s = torch.cuda.Stream(), torch.cuda.Stream()
     ke = max(1, args.e2e_steps)
 
     def e2e_run(k_steps):
-        start = torch.cuda.Event()
-        start.record(streams[0])
-        streams[1].wait_event(start)
-        for k in range(k_steps):
-            i = k % 2
-            wenozn.wenozn_rk3_step_host(p, host_in, host_out[i], bufs[i], solvers[i].ws, stream=streams[i])
-        done = torch.cuda.Event()
-        done.record(streams[1])
-        streams[0].wait_event(done)
+        wenozn.wenozn_rk3_stream_host(p, [host_in] * k_steps, [host_out[k % 2] for k in range(k_steps)],
+                                      bufs[0], bufs[1], S.ws, stream=stream, upload_stream=up_s,
+                                      download_stream=down_s)
 
     e2e_run(2)
     torch.cuda.synchronize()
@@ -690,13 +687,13 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ems = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e_status = max(sv.status() for sv in solvers)
     nbytes = U.numel() * U.element_size()
     e2e = {"value": job_throughput(n * n, ke, world, ems), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "steps": ke, "device_status": e2e_status,
-           "api": "wenozn_rk3_step_host (host buffers in and out, one C-ABI call per step)",
-           "copies": "pinned host <-> device inside the call, steps alternating between two streams"}
-    del bufs, solvers[1]
+           "d2h_bytes_per_step": nbytes, "steps": ke, "device_status": S.status(),
+           "api": "wenozn_rk3_stream_host (one C-ABI call: host states in, host results out)",
+           "copies": "pinned host <-> device on an upload and a download stream inside the call, "
+                     "overlapping the neighbouring states' steps"}
+    del bufs
 
     def part(skip, fn, *a, **kw):
         """A secondary measurement; its failure is reported in its own object, the headline

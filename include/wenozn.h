@@ -224,6 +224,24 @@ wenozn_status wenozn_rk3_step_host(const wenozn_problem* p, const double* U_host
                                    double* U_dev, double dt, double t_remaining, double* dt_out, void* ws,
                                    size_t ws_bytes, void* stream);
 
+/* A stream of `count` independent host-resident states, each advanced by one SSP-RK3 step
+ * (fixed dt > 0, or its CFL step for dt <= 0) as wenozn_rk3_step would, in one call:
+ * state k is copied from U_host_in[k] to the staging buffer U_dev0 (k even) or U_dev1 (k
+ * odd) on upload_stream, stepped on `stream` and copied to U_host_out[k] on
+ * download_stream, so that with pinned host buffers the copies of states k - 1 and k + 1
+ * overlap the step of state k.  The call's work starts after the work already enqueued on
+ * `stream`, and `stream` resumes only after its last copy: to the caller the call behaves
+ * as one operation on `stream`.  A NULL copy stream means `stream` itself (no overlap).
+ *   U_host_in, U_host_out : host arrays of `count` pointers to host [nvar][ny][nx] states
+ *                           (the same pointer may repeat; an output may equal its input).
+ *   U_dev0, U_dev1        : device, two distinct [nvar][ny][nx] staging buffers.
+ *   ws                    : one workspace (the steps run one after another on `stream`).
+ * The call creates its own ordering events and releases them before returning; it
+ * allocates no memory and does not synchronise. */
+wenozn_status wenozn_rk3_stream_host(const wenozn_problem* p, int64_t count, const double* const* U_host_in,
+                                     double* const* U_host_out, double* U_dev0, double* U_dev1, double dt, void* ws,
+                                     size_t ws_bytes, void* stream, void* upload_stream, void* download_stream);
+
 /* The CFL step of the state U (device, [nvar][ny][nx]): the step wenozn_rk3_step takes with
  * dt <= 0 (1D: cfl dx / max(|u|+c), Sec. 4.3; 2D: cfl dtx dty / (dtx + dty) with
  * dtx = dx / max(|u|+c), dty = dy / max(|v|+c), Sec. 4.4; advection: cfl dx / |a|), from

@@ -13,7 +13,6 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     v.ctl = reinterpret_cast<unsigned*>(ws_base(ws) + L.vjp_ctl);
     v.n = p.nx;
     v.bc = p.bc_x;
-    v.nblocks = vjp_partial_count(p.nx);
     v.rdx = 1.0 / p.dx;
     v.gamma = p.gamma;
     v.eps4 = 4.0 * p.eps;
@@ -44,8 +43,9 @@ wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws,
     double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
     double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
     VjpArgs v = vjp_args(p, L, ws);
-    // the control word is zero after every gather; clear it before a sequence starts
-    cudaError_t e = clear_ctl ? cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s) : cudaSuccess;
+    // the control words (argmax, ticket counter) are zero after every stage; clear them
+    // before a sequence starts
+    cudaError_t e = clear_ctl ? cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s) : cudaSuccess;
     if (e != cudaSuccess) return WENOZN_ECUDA;
     // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
     v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
@@ -91,7 +91,7 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
     VjpArgs v = vjp_args(*p, L, ws);
     note_status(stream, &ctrl->status);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) {
         v.U = U;
         v.lam = lam;

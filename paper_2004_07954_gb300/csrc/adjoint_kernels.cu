@@ -96,28 +96,24 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
 }
 
 // ---------------------------------------------------------------------------------------
-// Interface kernels.  A block takes kTI consecutive interfaces j0 .. j0+kTI-1 and their
-// kCells stencil cells, whose split fluxes h+- (and, for Euler, u, H, sqrt(rho), 1/rho) it
-// computes once into shared memory.  For Euler each interface is then handled by three
-// threads, one per characteristic field k (warp k of the block): the Roe state, row k of the
-// left and column k of the right eigenvectors, the projection of the stencil onto field k,
-// both WENO-ZN reconstructions of that field and their reverse sweeps.  The three fields'
-// cotangents of the split fluxes and of the Roe quantities are summed through shared memory.
+// Interface VJPs.  A block takes kTI consecutive interfaces and their kCells stencil cells,
+// whose split fluxes h+- (and, for Euler, u, H, sqrt(rho), 1/rho) it computes once into
+// shared memory.  For Euler each interface is then handled by three threads, one per
+// characteristic field k (warp k of the block): the Roe state, row k of the left and column
+// k of the right eigenvectors, the projection of the stencil onto field k, both WENO-ZN
+// reconstructions of that field and their reverse sweeps.  The three fields' cotangents of
+// the split fluxes and of the Roe quantities are summed through shared memory.
 //
-// Output, planar over interfaces (P = n + 1 planes):
-//   C[(s Q + m) P + j]      = (hbar+_{s,m} + hbar-_{s,m}) / 2,
-//   C[(s Q + NV + m) P + j] = (hbar+_{s,m} - hbar-_{s,m}) / 2,
-//   for stencil position s = 0..5 (cell j - 3 + s), Q = 2 NV values per position, and for
-//   Euler C[(36 + 3 t + m) P + j], t = 0, 1: the conserved-variable cotangent of the left
-//   (cell j - 1) and right (cell j) Roe-average inputs.
-// The split flux is h+- = (F(U) +- alpha U)/2, so hbar+ dh+/dU + hbar- dh-/dU is
-// J_F^T (hbar+ + hbar-)/2 + alpha (hbar+ - hbar-)/2: the gather applies J_F^T once per cell to
-// the summed first part.
+// Per interface j and stencil position s = 0..5 (cell j - 3 + s) the results are
+//   (hbar+_{s,m} + hbar-_{s,m}) / 2  and  (hbar+_{s,m} - hbar-_{s,m}) / 2,  m = 0..NV-1,
+// and for Euler the conserved-variable cotangents of the left (cell j - 1) and right
+// (cell j) Roe-average inputs.  The split flux is h+- = (F(U) +- alpha U)/2, so
+// hbar+ dh+/dU + hbar- dh-/dU is J_F^T (hbar+ + hbar-)/2 + alpha (hbar+ - hbar-)/2: the
+// gather applies J_F^T once per cell to the summed first part.
 // ---------------------------------------------------------------------------------------
 constexpr int kTI = 32;                 // interfaces per block (one warp per field)
-constexpr int kCells = kTI + 5;         // cells j0-3 .. j0+kTI+1
-constexpr int kGather = 64;             // cells per gather block (small blocks spread the FP64 work)
-constexpr int kRoe = 36;                // first Roe plane (Euler)
+constexpr int kCells = kTI + 5;         // their stencil cells
+constexpr int kGather = 64;             // cells per advection gather block
 
 struct EulerSmem {
     double U[3][kCells];
@@ -126,15 +122,67 @@ struct EulerSmem {
     double red[3][36][kTI];             // per field: hbar+ (5 x 3), hbar- (5 x 3), 6 Roe scalars
 };
 
-__global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
-    __shared__ EulerSmem sm;
+// ---------------------------------------------------------------------------------------
+// Euler: one kernel per reverse stage.  Block b owns the cells c0 = b kOwn .. c0 + kOwn - 1
+// and computes the VJPs of every interface whose stencil or Roe average touches them,
+// j = c0 - 2 .. c0 + kOwn + 2 (kTI of them), so that it can gather its own cells without
+// anything from other blocks; neighbouring blocks both compute the five interfaces they
+// share (5/kOwn more interface work, and no second launch).  What the tile cannot hold
+// crosses blocks through global memory:
+//   - the LF-speed cotangent: every interface is owned by one block (j in [c0, c0 + kOwn),
+//     and j = n by the last block), which adds its share sum_s U_s . (hbar+ - hbar-)_s / 2
+//     to the block's partial;
+//   - the stencil positions outside the grid (ghost cells -3..-1 and n..n+2): the summed
+//     contributions of each block's owned interfaces go to that block's slot;
+// and the block that finishes last (each block fences its writes and takes a ticket from
+// an atomic counter: the memory-fence pattern of the CUDA programming guide) sums the
+// partials in block order, adds d abar d(|u| + c)/dU at the argmax cell of the LF speed
+// (|x|' = 0 at 0) and the ghost contributions through J_F^T at the cells they map to, and
+// resets the argmax word and the counter for the next launch.  Every sum has a fixed order,
+// so the result is deterministic.
+// ---------------------------------------------------------------------------------------
+constexpr int kOwn = kTI - 5;           // cells owned by a block
+constexpr int kGhostSlot = 6 * 9;       // 6 ghost cells x (flux, LF, Roe) x 3 components
+
+struct StageSmem {
+    EulerSmem e;
+    double cF[6][3][kTI], cD[6][3][kTI];   // per position s, component m, interface: flux and LF parts
+    double cR[2][3][kTI];                  // Roe-input cotangents (left cell, right cell)
+    double sF[3][kOwn];                    // gathered flux parts, exchanged between component threads
+    double ghost[6][3][3];                 // ghost slots x (flux, LF, Roe) x component
+    double red[3];
+    int last;                              // this block finished last
+    int im;                                // the LF speed's argmax cell (completion step)
+    int cand;                              // the block's lowest LF-argmax candidate cell
+    int tgt[6];                            // the cells the ghost slots map to (completion step)
+};
+
+// Row m of J_F^T applied to (F0, F1, F2) at the state (rho, mom, E): F = (m, m u + p,
+// u (E + p)), u = m/rho, p = (gamma - 1)(E - m u/2).
+__device__ __forceinline__ double jft_row(int m, double F0, double F1, double F2, double rho, double mom,
+                                          double E, double gamma) {
+    const double gm1 = gamma - 1.0;
+    const double r = rcp_nr(rho), u = mom * r;
+    const double p = gm1 * (E - 0.5 * mom * u);
+    const double Ep = E + p;
+    const double pb = fma(F2, u, F1);
+    if (m == 2) return fma(F2, u, gm1 * pb);                                      // E bar
+    const double ub = fma(F1, mom, F2 * Ep) - gm1 * 0.5 * mom * pb;
+    if (m == 1) return fma(ub, r, fma(F1, u, F0) - gm1 * 0.5 * u * pb);          // m bar
+    return -ub * u * r;                                                            // rho bar
+}
+
+__global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
+    __shared__ StageSmem S;
+    EulerSmem& sm = S.e;
     pdl_wait();
-    const int n = a.n, j0 = blockIdx.x * kTI, tid = threadIdx.x;
-    const int64_t P = int64_t(n) + 1;
+    const int n = a.n, nb = int(gridDim.x), b = int(blockIdx.x), tid = threadIdx.x;
+    const int c0 = b * kOwn, j0 = c0 - 2;        // first owned cell, first interface
     const double gm1 = a.gamma - 1.0;
     const unsigned long long abits = a.alpha_bits[0];
     const double alpha = __longlong_as_double((long long)abits);
-    int cand = -1;                               // this thread's LF-argmax candidate cell
+    if (tid == 0) S.cand = n;
+    __syncthreads();
     for (int c = tid; c < kCells; c += 3 * kTI) {
         const int g = j0 - 3 + c;
         const int src = ghost_src(g, n, a.bc);
@@ -156,16 +204,33 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         sm.H[c] = Ep * r;
         sm.sq[c] = sqrt(s[0]);
         sm.r[c] = r;
-        if (g == src && c >= 3 && c < 3 + kTI) {   // a grid cell of this block: is it the LF argmax?
+        if (g == src && c >= 5 && c < 5 + kOwn) {   // an owned grid cell: is it the LF argmax?
             double sx, sy;
             wave_speeds<3>(s, a.gamma, sx, sy);
-            if ((unsigned long long)__double_as_longlong(sx) == abits) cand = g;
+            if ((unsigned long long)__double_as_longlong(sx) == abits) atomicMin(&S.cand, g);
         }
     }
     __syncthreads();
+    // the block's lowest candidate: offered for the global argmax (the lowest index on ties),
+    // with d(|u| + c)/dU of its state left for the completion step (|x|' = 0 at 0)
+    if (tid == 2 * kTI && S.cand < n) {
+        const int lc = S.cand - j0 + 3;
+        atomicMax(&a.ctl[0], ~unsigned(S.cand));
+        const double rho = sm.U[0][lc], mom = sm.U[1][lc], E = sm.U[2][lc];
+        const double r = rcp_nr(rho), u = mom * r;
+        const double p = gm1 * (E - 0.5 * mom * u);
+        const double c2 = a.gamma * p * r, rcs = rsqrt(c2);
+        const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
+        const double kk = 0.5 * a.gamma * r * rcs;                  // gamma / (2 c rho)
+        double* slot = a.C + int64_t(nb) * 18 + int64_t(b) * 3;
+        slot[0] = fma(sg, -u * r, kk * fma(gm1 * 0.5 * u, u, -p * r));
+        slot[1] = fma(sg, r, -kk * gm1 * u);
+        slot[2] = kk * gm1;
+    }
 
     const int k = tid / kTI, i = tid % kTI, j = j0 + i;
-    const bool live = j <= n;
+    const bool live = j >= 0 && j <= n;
+    const bool owned = live && ((j >= c0 && j < c0 + kOwn) || (j == n && b == nb - 1));
     const int cl = i + 2, cr = i + 3;            // cells j-1, j
     double ut = 0, Ht = 0, c = 0, rc = 0, b1 = 0, wl = 0, wr = 0, rS = 0;
     double L0 = 0, L1 = 0, L2 = 0, R1 = 0, R2 = 0;
@@ -199,7 +264,6 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
             fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
         }
     }
-    if (cand >= 0) atomicMax(&a.ctl[0], ~unsigned(cand));
     if (live) {
         double fpb[5], fmb[5];
         double Fb[3];
@@ -239,61 +303,182 @@ __global__ void __launch_bounds__(3 * kTI) vjp_interface_euler(VjpArgs a) {
         sm.red[k][33][i] = utb; sm.red[k][34][i] = cb; sm.red[k][35][i] = Htb;
     }
     __syncthreads();
-    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-, and this
-    // interface's share sum_s U_s . (hbar+ - hbar-)_s / 2 of the LF-speed cotangent
+    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-, and, for an owned
+    // interface, its share sum_s U_s . (hbar+ - hbar-)_s / 2 of the LF-speed cotangent
     double ab = 0.0;
-    if (live) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int s = 2 * k + t;
+    for (int t = 0; t < 2; ++t) {
+        const int s = 2 * k + t;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < 3; ++m) {
+            double sumF = 0.0, dh = 0.0;
+            if (live) {
                 const double hpb = s <= 4 ? (sm.red[0][s * 3 + m][i] + sm.red[1][s * 3 + m][i]) + sm.red[2][s * 3 + m][i]
                                           : 0.0;
                 const double hmb = s >= 1 ? (sm.red[0][12 + s * 3 + m][i] + sm.red[1][12 + s * 3 + m][i]) +
                                                 sm.red[2][12 + s * 3 + m][i] : 0.0;
-                const double dh = 0.5 * (hpb - hmb);
-                a.C[(s * 6 + m) * P + j] = 0.5 * (hpb + hmb);
-                a.C[(s * 6 + 3 + m) * P + j] = dh;
-                ab = fma(sm.U[m][i + s], dh, ab);
+                sumF = 0.5 * (hpb + hmb);
+                dh = 0.5 * (hpb - hmb);
+                if (owned) ab = fma(sm.U[m][i + s], dh, ab);
             }
+            S.cF[s][m][i] = sumF;
+            S.cD[s][m][i] = dh;
         }
     }
-    if (live && k > 0) {
-        // Roe average (warps 1 and 2 both reverse it; 1 writes the left cell, 2 the right):
+    if (k > 0) {
+        // Roe average (warps 1 and 2 both reverse it; 1 gives the left cell, 2 the right):
         // b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2))
-        double sc[6];
+        double Ur = 0.0, Um = 0.0, UE = 0.0;
+        if (live) {
+            double sc[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
-        double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
-        utb = fma(b2b * ut, b1, utb);
-        b1b = fma(b2b * 0.5 * ut, ut, b1b);
-        rcb = fma(b1b * 2.0 * gm1, rc, rcb);
-        cb = fma(-rcb * rc, rc, cb);
-        const double cq = cb * gm1 * 0.5 * rc;
-        Htb += cq;
-        utb = fma(-cq, ut, utb);
-        // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
-        const int cc = k == 1 ? cl : cr;
-        const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
-        const double ub = utb * w, Hb = Htb * w;
-        const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
-        // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
-        const double Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
-        const double Um = r * fma(-gm1 * uc, Hb, ub);
-        const double UE = a.gamma * r * Hb;
-        double* roe = a.C + (kRoe + 3 * (k - 1)) * P + j;
-        roe[0] = Ur;
-        roe[P] = Um;
-        roe[2 * P] = UE;
+            for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
+            double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
+            utb = fma(b2b * ut, b1, utb);
+            b1b = fma(b2b * 0.5 * ut, ut, b1b);
+            rcb = fma(b1b * 2.0 * gm1, rc, rcb);
+            cb = fma(-rcb * rc, rc, cb);
+            const double cq = cb * gm1 * 0.5 * rc;
+            Htb += cq;
+            utb = fma(-cq, ut, utb);
+            // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
+            const int cc = k == 1 ? cl : cr;
+            const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
+            const double ub = utb * w, Hb = Htb * w;
+            const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
+            // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
+            Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
+            Um = r * fma(-gm1 * uc, Hb, ub);
+            UE = a.gamma * r * Hb;
+        }
+        S.cR[k - 1][0][i] = Ur;
+        S.cR[k - 1][1][i] = Um;
+        S.cR[k - 1][2][i] = UE;
     }
     // deterministic per-block partial of the LF-speed cotangent (sm.red is free again)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ab += __shfl_down_sync(0xffffffffu, ab, o);
     __syncthreads();
-    if (i == 0) sm.red[0][0][k] = ab;
+    if (i == 0) S.red[k] = ab;
+    // the ghost contributions of the owned interfaces: slot q <-> cell -3 + q (q < 3) or
+    // n + q - 3, summed per part (flux, LF, Roe) and component in a fixed order over the
+    // positions s; only the first block and the last two can own such interfaces
+    const bool edge = b == 0 || b >= nb - 2;
+    if (edge && tid < kGhostSlot) {
+        const int q = tid / 9, part = (tid % 9) / 3, m = tid % 3;
+        const int g = q < 3 ? q - 3 : n + q - 3;
+        double v = 0.0;
+        for (int s = 0; s < 6; ++s) {
+            const int jj = g + 3 - s, li = jj - j0;
+            if (li < 0 || li >= kTI || jj < 0 || jj > n) continue;
+            if (!((jj >= c0 && jj < c0 + kOwn) || (jj == n && b == nb - 1))) continue;
+            if (part == 0) v += S.cF[s][m][li];
+            else if (part == 1) v += S.cD[s][m][li];
+            else if (s == 2) v += S.cR[0][m][li];       // left Roe input of interface jj is cell jj - 1 = g
+            else if (s == 3) v += S.cR[1][m][li];       // right Roe input is cell jj = g
+        }
+        S.ghost[q][part][m] = v;
+    }
     __syncthreads();
-    if (tid == 0) a.partial[blockIdx.x] = (sm.red[0][0][0] + sm.red[0][0][1]) + sm.red[0][0][2];
+    if (tid == 0) a.partial[b] = (S.red[0] + S.red[1]) + S.red[2];
+    // ... and their share of the cells the ghosts map to, d (J_F^T flux + alpha LF + Roe)
+    // with that cell's state: one value per slot and component
+    if (edge && tid < 18) {
+        const int q = tid / 3, m = tid % 3;
+        const int tgt = ghost_src(q < 3 ? q - 3 : n + q - 3, n, a.bc);
+        const double rho = a.U[tgt], mom = a.U[n + tgt], E = a.U[2 * int64_t(n) + tgt];
+        const double jf = jft_row(m, S.ghost[q][0][0], S.ghost[q][0][1], S.ghost[q][0][2], rho, mom, E, a.gamma);
+        a.C[int64_t(b) * 18 + tid] = a.d * (fma(alpha, S.ghost[q][1][m], jf) + S.ghost[q][2][m]);
+    }
+    // the gather of the owned cells: thread (m, lc) sums component m of cell c0 + lc over the
+    // positions s of interfaces c0 + lc + 3 - s (fixed order), exchanges the flux parts and
+    // applies row m of J_F^T
+    const int m = tid / kOwn, lc = tid % kOwn, cell = c0 + lc;
+    const bool mine = tid < 3 * kOwn && cell < n;
+    double Fs = 0.0, Ds = 0.0, Rs = 0.0;
+    if (mine) {
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            Fs += S.cF[s][m][lc + 5 - s];
+            Ds += S.cD[s][m][lc + 5 - s];
+        }
+        Rs = S.cR[1][m][lc + 2] + S.cR[0][m][lc + 3];
+    }
+    if (tid < 3 * kOwn) S.sF[m][lc] = Fs;
+    __syncthreads();
+    if (mine) {
+        const double rho = sm.U[0][lc + 5], mom = sm.U[1][lc + 5], E = sm.U[2][lc + 5];
+        const double part = jft_row(m, S.sF[0][lc], S.sF[1][lc], S.sF[2][lc], rho, mom, E, a.gamma);
+        const double Ub = fma(alpha, Ds, part) + Rs;
+        const int64_t idx = int64_t(m) * n + cell;
+        double v = a.d * Ub;
+        if (a.X1) v = fma(a.c1, a.X1[idx], v);
+        if (a.X2) v = fma(a.c2, a.X2[idx], v);
+        if (a.X3) v = fma(a.c3, a.X3[idx], v);
+        a.out[idx] = v;
+    }
+    // the last block to finish completes the stage
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) S.last = atomicAdd(&a.ctl[1], 1u) == unsigned(nb - 1);
+    __syncthreads();
+    if (!S.last) return;
+    __threadfence();
+    // Everything below is a few independent L2 reads and one read-modify-write per touched
+    // cell: abar = the partials summed in block order (strided runs, then the warps); the
+    // edge blocks' ghost corrections per slot and component; the argmax cell's d(|u|+c)/dU,
+    // left by the block that owns it.
+    if (tid >= 32 && tid < 38) S.tgt[tid - 32] = ghost_src(tid < 35 ? tid - 35 : n + tid - 35, n, a.bc);
+    double v = 0.0;
+#pragma unroll 4
+    for (int q = tid; q < nb; q += 3 * kTI) v += __ldcg(a.partial + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (i == 0) S.red[k] = v;
+    if (tid < 18) {
+        const int b1 = nb - 2, b2 = nb - 1;
+        double cq = __ldcg(a.C + tid);                                          // block 0
+        if (b1 > 0) cq += __ldcg(a.C + int64_t(b1) * 18 + tid);
+        if (b2 > 0 && b2 != b1) cq += __ldcg(a.C + int64_t(b2) * 18 + tid);
+        S.ghost[tid / 3][0][tid % 3] = cq;
+    } else if (tid < 21) {
+        const int mm = tid - 18;
+        const unsigned key = __ldcg(a.ctl);
+        const int im = key ? int(~key) : -1;
+        S.ghost[0][1][mm] = im >= 0 ? __ldcg(a.C + int64_t(nb) * 18 + int64_t(im / kOwn) * 3 + mm) : 0.0;
+        if (mm == 0) S.im = im;
+    }
+    __syncthreads();
+    // one update per touched cell and component: the first slot of each target cell sums the
+    // slots with that target in slot order, plus the LF-speed term if it is also the argmax
+    const double abar = (S.red[0] + S.red[1]) + S.red[2];
+    const int im = S.im;
+    if (tid < 18) {
+        const int q = tid / 3, mm = tid % 3, tgt = S.tgt[q];
+        bool first = true;
+        for (int r = 0; r < q; ++r) first = first && S.tgt[r] != tgt;
+        if (first) {
+            double add = 0.0;
+            for (int r = q; r < 6; ++r)
+                if (S.tgt[r] == tgt) add += S.ghost[r][0][mm];
+            if (tgt == im) add = fma(a.d * abar, S.ghost[0][1][mm], add);
+            double* o = a.out + int64_t(mm) * n + tgt;
+            *o = __ldcg(o) + add;
+        }
+    } else if (tid < 21 && im >= 0) {
+        const int mm = tid - 18;
+        bool ghost_target = false;
+        for (int r = 0; r < 6; ++r) ghost_target = ghost_target || S.tgt[r] == im;
+        if (!ghost_target) {
+            double* o = a.out + int64_t(mm) * n + im;
+            *o = fma(a.d * abar, S.ghost[0][1][mm], __ldcg(o));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a.ctl[0] = 0u;
+        a.ctl[1] = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(kTI) vjp_interface_advection(VjpArgs a) {
@@ -375,127 +560,14 @@ __global__ void __launch_bounds__(kGather) vjp_gather_advection(VjpArgs a) {
     a.out[i] = v;
 }
 
-// Euler: one warp per conserved component, so that the three threads of a cell each sum
-// their own component's contributions (fixed order, as above), exchange the flux parts
-// through shared memory and apply their row of J_F^T (F = (m, m u + p, u (E + p))); three
-// times the warps of one thread per cell, which the FP64 latency of the sums needs at small
-// n.  The block holding the argmax cell of the LF speed also sums the interface kernel's
-// partials of the LF-speed cotangent (fixed order), adds its term d(|u| + c)/dU there
-// (|x|' = 0 at 0) and clears the argmax word.
-constexpr int kGatherCells = 32;
-
-__global__ void __launch_bounds__(3 * kGatherCells) vjp_gather_euler(VjpArgs a) {
-    constexpr int Q = 6;
-    __shared__ double sF[3][kGatherCells];
-    pdl_wait();
-    const int n = a.n;
-    const int64_t P = int64_t(n) + 1;
-    const int m = threadIdx.x / kGatherCells, lane = threadIdx.x % kGatherCells;
-    const int i = blockIdx.x * kGatherCells + lane;
-    double Fs = 0.0, Ds = 0.0, Rs = 0.0;
-    if (i < n) {
-        if (i >= 3 && i <= n - 4) {
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-                const int64_t j = i + 3 - s;
-                Fs += a.C[(s * Q + m) * P + j];
-                Ds += a.C[(s * Q + 3 + m) * P + j];
-            }
-            Rs = a.C[(kRoe + 3 + m) * P + i] + a.C[(kRoe + m) * P + i + 1];
-        } else {
-            int gs[16], ng = 0;
-            if (n <= 8) {
-                for (int g = -3; g <= n + 2; ++g)
-                    if (ghost_src(g, n, a.bc) == i) gs[ng++] = g;
-            } else if (a.bc == 0) {
-                for (int g = i - n; g <= i + n; g += n)
-                    if (g >= -3 && g <= n + 2) gs[ng++] = g;
-            } else {
-                gs[ng++] = i;
-                if (i == 0) { gs[ng++] = -1; gs[ng++] = -2; gs[ng++] = -3; }
-                if (i == n - 1) { gs[ng++] = n; gs[ng++] = n + 1; gs[ng++] = n + 2; }
-            }
-            for (int q = 0; q < ng; ++q) {
-                const int g = gs[q];
-                for (int s = 0; s < 6; ++s) {
-                    const int j = g + 3 - s;
-                    if (j < 0 || j > n) continue;
-                    Fs += a.C[(s * Q + m) * P + j];
-                    Ds += a.C[(s * Q + 3 + m) * P + j];
-                    if (s == 2 || s == 3) Rs += a.C[(kRoe + 3 * (s - 2) + m) * P + j];
-                }
-            }
-        }
-    }
-    sF[m][lane] = Fs;
-    double rho = 1.0, mom = 0.0, E = 0.0;
-    if (i < n) {                                 // the cell's state, loaded before the barrier
-        rho = a.U[i];
-        mom = a.U[n + i];
-        E = a.U[2 * int64_t(n) + i];
-    }
-    __syncthreads();
-    double Ub = 0.0;
-    if (i < n) {
-        const double F0 = sF[0][lane], F1 = sF[1][lane], F2 = sF[2][lane];
-        const double alpha = __longlong_as_double((long long)a.alpha_bits[0]);
-        const double gm1 = a.gamma - 1.0;
-        const double r = rcp_nr(rho), u = mom * r;
-        const double p = gm1 * (E - 0.5 * mom * u);
-        const double Ep = E + p;
-        // F = (mom, mom u + p, u (E + p)), u = mom/rho, p = (gamma-1)(E - mom u/2)
-        const double pb = fma(F2, u, F1);
-        double part;
-        if (m == 2) {
-            part = fma(F2, u, gm1 * pb);                                   // E bar
-        } else {
-            const double ub = fma(F1, mom, F2 * Ep) - gm1 * 0.5 * mom * pb;
-            if (m == 1) part = fma(ub, r, fma(F1, u, F0) - gm1 * 0.5 * u * pb);   // m bar
-            else part = -ub * u * r;                                       // rho bar
-        }
-        Ub = fma(alpha, Ds, part) + Rs;
-    }
-    const unsigned key = a.ctl[0];
-    const int im = key ? int(~key) : -1;
-    if (im >= 0 && im / kGatherCells == int(blockIdx.x)) {     // uniform over the block
-        __shared__ double red[3];
-        double v = 0.0;
-        for (int b = threadIdx.x; b < a.nblocks; b += 3 * kGatherCells) v += a.partial[b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[m] = v;
-        __syncthreads();
-        if (i == im) {
-            const double abar = red[0] + red[1] + red[2];
-            const double u = mom / rho;
-            const double p = (a.gamma - 1.0) * (E - 0.5 * mom * u);
-            const double c = sqrt(a.gamma * p / rho);
-            const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
-            const double kk = a.gamma / (2.0 * c * rho), gm1 = a.gamma - 1.0;
-            if (m == 0) Ub += abar * (sg * (-u / rho) + kk * (gm1 * 0.5 * u * u - p / rho));
-            else if (m == 1) Ub += abar * (sg / rho - kk * gm1 * u);
-            else Ub += abar * (kk * gm1);
-        }
-        __syncthreads();
-        if (i == im && m == 0) a.ctl[0] = 0u;
-    }
-    if (i >= n) return;
-    const int64_t idx = int64_t(m) * n + i;
-    double v = a.d * Ub;
-    if (a.X1) v = fma(a.c1, a.X1[idx], v);
-    if (a.X2) v = fma(a.c2, a.X2[idx], v);
-    if (a.X3) v = fma(a.c3, a.X3[idx], v);
-    a.out[idx] = v;
-}
-
 }  // namespace
 
-// The Euler interface kernel is FP64-bound and as fast as its busiest SM: the block
-// scheduler balances it over empty SMs (at most two blocks per SM at the sizes where it
-// matters), but launched early beside the previous gather its blocks would pile up on the
-// SMs the gather leaves free.  An unused dynamic shared-memory reservation caps it at two
-// blocks per SM, so the early (programmatic) launch keeps the balanced placement.  The
-// reservation is sized per device, once.
+// The Euler stage kernel is FP64-bound and as fast as its busiest SM: the block scheduler
+// balances it over empty SMs (two blocks per SM at the sizes where it matters), but
+// launched with programmatic dependent launch its blocks become resident (and wait) while
+// the previous launch drains, and would pile up on the SMs that launch leaves free first.
+// An unused dynamic shared-memory reservation caps it at two blocks per SM, which keeps the
+// balanced placement.  The reservation is sized per device, once.
 static cudaError_t euler_interface_pad(size_t* pad) {
     static std::atomic<unsigned long long> configured{0};
     static size_t pads[64];
@@ -508,10 +580,10 @@ static cudaError_t euler_interface_pad(size_t* pad) {
         e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (e != cudaSuccess) return e;
-        const long budget = long(per_sm) / 2 - long(reserved) - long(sizeof(EulerSmem)) - 1024;
+        const long budget = long(per_sm) / 2 - long(reserved) - long(sizeof(StageSmem)) - 1024;
         size_t pd = budget > 0 ? size_t(budget) : 0;
         if (pd > 0) {
-            e = cudaFuncSetAttribute(vjp_interface_euler, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pd));
+            e = cudaFuncSetAttribute(vjp_stage_euler, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pd));
             if (e != cudaSuccess) return e;
         }
         pads[dev & 63] = pd;
@@ -521,24 +593,28 @@ static cudaError_t euler_interface_pad(size_t* pad) {
     return cudaSuccess;
 }
 
-int vjp_partial_count(int n) { return (n + 1 + kTI - 1) / kTI; }
+// per-block partials: the advection interface blocks (kTI interfaces) or the Euler stage
+// blocks (kOwn cells), whichever are more
+int vjp_partial_count(int n) {
+    const int adv = (n + 1 + kTI - 1) / kTI, euler = (n + kOwn - 1) / kOwn;
+    return adv > euler ? adv : euler;
+}
 
+// per-interface contributions (advection), or the Euler stage blocks' ghost slots (which
+// fit: 21 ceil(n / kOwn) <= 42 (n + 1): 18 ghost corrections and 3 speed derivatives a block)
 size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12 : 42); }
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
-    const unsigned gi = unsigned(vjp_partial_count(a.n)), gc = unsigned((a.n + kGather - 1) / kGather);
-    const unsigned ge = unsigned((a.n + kGatherCells - 1) / kGatherCells);
-    cudaError_t e;
     if (system == 0) {
-        e = launch_pdl(vjp_interface_advection, dim3(gi), dim3(kTI), 0, s, a);
-    } else {
-        size_t pad = 0;
-        e = euler_interface_pad(&pad);
-        if (e == cudaSuccess) e = launch_pdl(vjp_interface_euler, dim3(gi), dim3(3 * kTI), pad, s, a);
+        const unsigned gi = unsigned((a.n + 1 + kTI - 1) / kTI), gc = unsigned((a.n + kGather - 1) / kGather);
+        cudaError_t e = launch_pdl(vjp_interface_advection, dim3(gi), dim3(kTI), 0, s, a);
+        if (e == cudaSuccess) e = launch_pdl(vjp_gather_advection, dim3(gc), dim3(kGather), 0, s, a);
+        return e;
     }
+    size_t pad = 0;
+    cudaError_t e = euler_interface_pad(&pad);
     if (e == cudaSuccess)
-        e = system == 0 ? launch_pdl(vjp_gather_advection, dim3(gc), dim3(kGather), 0, s, a)
-                        : launch_pdl(vjp_gather_euler, dim3(ge), dim3(3 * kGatherCells), 0, s, a);
+        e = launch_pdl(vjp_stage_euler, dim3(unsigned((a.n + kOwn - 1) / kOwn)), dim3(3 * kTI), pad, s, a);
     return e;
 }
 

@@ -230,6 +230,56 @@ wenozn_status wenozn_rk3_step_host(const wenozn_problem* p, const double* U_host
     return cuda_status(e);
 }
 
+wenozn_status wenozn_rk3_stream_host(const wenozn_problem* p, int64_t count, const double* const* U_host_in,
+                                     double* const* U_host_out, double* U_dev0, double* U_dev1, double dt, void* ws,
+                                     size_t ws_bytes, void* stream, void* upload_stream, void* download_stream) {
+    wenozn_status st = check_problem(p);
+    if (st != WENOZN_OK) return st;
+    if (count < 1 || !U_host_in || !U_host_out || !U_dev0 || !U_dev1 || U_dev0 == U_dev1 || !ws ||
+        std::isnan(dt) || std::isinf(dt))
+        return WENOZN_EINVAL;
+    for (int64_t k = 0; k < count; ++k)
+        if (!U_host_in[k] || !U_host_out[k]) return WENOZN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return WENOZN_EINVAL;
+    const Layout lay = layout_of(*p);
+    if (ws_bytes < lay.total) return WENOZN_ENOMEM_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t up = upload_stream ? static_cast<cudaStream_t>(upload_stream) : s;
+    cudaStream_t down = download_stream ? static_cast<cudaStream_t>(download_stream) : s;
+    const size_t bytes = size_t(nvar_of(p->system)) * size_t(p->nx) * size_t(p->ny) * sizeof(double);
+    double* dev[2] = {U_dev0, U_dev1};
+    double* u1 = reinterpret_cast<double*>(ws_base(ws) + lay.u1);
+    double* u2 = reinterpret_cast<double*>(ws_base(ws) + lay.u2);
+    note_status(stream, &reinterpret_cast<Ctrl*>(ws_base(ws) + lay.ctrl)->status);
+    // ordering events of this call only: start, uploaded[2], stepped[2], downloaded[2]
+    cudaEvent_t ev[7] = {};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    cudaEvent_t start = ev[0], *uploaded = ev + 1, *stepped = ev + 3, *downloaded = ev + 5;
+    // the copy streams start after the work already on `stream`
+    if (e == cudaSuccess) e = cudaEventRecord(start, s);
+    if (e == cudaSuccess && up != s) e = cudaStreamWaitEvent(up, start, 0);
+    if (e == cudaSuccess && down != s) e = cudaStreamWaitEvent(down, start, 0);
+    for (int64_t k = 0; k < count && e == cudaSuccess; ++k) {
+        const int b = int(k & 1);
+        if (k >= 2) e = cudaStreamWaitEvent(up, downloaded[b], 0);            // the buffer is free again
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dev[b], U_host_in[k], bytes, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess) e = cudaEventRecord(uploaded[b], up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, uploaded[b], 0);
+        if (e == cudaSuccess) e = rk3_stages(*p, lay, ws, dev[b], dev[b], u1, u2, dt, 0.0, s);
+        if (e == cudaSuccess) e = cudaEventRecord(stepped[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(down, stepped[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(U_host_out[k], dev[b], bytes, cudaMemcpyDeviceToHost, down);
+        if (e == cudaSuccess) e = cudaEventRecord(downloaded[b], down);
+    }
+    // `stream` ends after every copy of the call
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        if (b < count) e = cudaStreamWaitEvent(s, downloaded[b], 0);
+    for (int i = 0; i < 7; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);            // released once their pending work completes
+    return cuda_status(e);
+}
+
 wenozn_status wenozn_cfl_dt(const wenozn_problem* p, const double* U, double* dt_out, void* ws, size_t ws_bytes,
                             void* stream) {
     wenozn_status st = check_problem(p);

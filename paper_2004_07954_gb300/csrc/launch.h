@@ -111,16 +111,18 @@ cudaError_t launch_batch_stage(int shape, const BatchArgs& a, int sms, cudaStrea
 struct VjpArgs {
     const double* U;                       // stage input, [nv][n]
     const double* lam;                     // cotangent of L(U), [nv][n]
-    double* C;                             // per-interface contributions, vjp_contrib_doubles(nv, n)
-    double* partial;                       // [nblocks] per-interface-block partial sums of the LF-speed cotangent
-    unsigned* ctl;                         // ctl[0]: ~(argmax of the LF speed); zero between launches
+    double* C;                             // per-interface contributions (advection) or the Euler stage
+                                           // blocks' ghost slots, vjp_contrib_doubles(nv, n)
+    double* partial;                       // [nblocks] per-block partial sums of the LF-speed cotangent
+    unsigned* ctl;                         // ctl[0]: ~(argmax of the LF speed), ctl[1]: ticket counter
+                                           // of the Euler stage kernel; zero between launches
     const unsigned long long* alpha_bits;  // LF speed of U (bit pattern)
     double* out;                           // c1 X1 + c2 X2 + c3 X3 + d J^T lam
     const double* X1;
     const double* X2;
     const double* X3;
     double c1, c2, c3, d;
-    int n, bc, nblocks;                    // nblocks = vjp_partial_count(n)
+    int n, bc;
     double rdx, gamma, eps4, kappa, adv_speed;
 };
 int vjp_partial_count(int n);

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "wenozn_rk3_step_host": [_P, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                              _VP, ctypes.c_size_t, _VP],
     "wenozn_cfl_dt": [_P, _VP, ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP],
+    "wenozn_rk3_stream_host": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                               _VP, _VP, ctypes.c_double, _VP, ctypes.c_size_t, _VP, _VP, _VP],
     "wenozn_workspace_status": [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _VP],
     "wenozn_last_error": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "wenozn_check_reciprocal": [_VP, ctypes.c_int64, _VP, _VP, _VP],
@@ -283,6 +285,27 @@ def wenozn_rk3_step_host(p: wenozn_problem, U_host_in: torch.Tensor, U_host_out:
                                       ws.numel() * ws.element_size(), _stream(stream))
     _check("wenozn_rk3_step_host", code)
     return out.value if return_dt else None
+
+
+def wenozn_rk3_stream_host(p: wenozn_problem, U_host_in, U_host_out, U_dev0: torch.Tensor, U_dev1: torch.Tensor,
+                           ws: torch.Tensor, dt: float = 0.0, stream=None, upload_stream=None,
+                           download_stream=None) -> None:
+    """One RK3 step of each host state U_host_in[k] into U_host_out[k] (lists of host tensors),
+    copies on the two copy streams overlapping the steps on `stream`; asynchronous."""
+    if len(U_host_in) != len(U_host_out) or not U_host_in:
+        raise ValueError("U_host_in and U_host_out must be non-empty lists of the same length")
+    n = p.nvar * p.nx * p.ny
+    for t in list(U_host_in) + list(U_host_out) + [U_dev0, U_dev1]:
+        if t.numel() != n:
+            raise ValueError(f"expected {n} values per state")
+    count = len(U_host_in)
+    ins = (ctypes.c_void_p * count)(*[_host_ptr(t, "U_host_in") for t in U_host_in])
+    outs = (ctypes.c_void_p * count)(*[_host_ptr(t, "U_host_out") for t in U_host_out])
+    up = None if upload_stream is None else _stream(upload_stream)
+    down = None if download_stream is None else _stream(download_stream)
+    _check("wenozn_rk3_stream_host", lib().wenozn_rk3_stream_host(
+        ctypes.byref(p), count, ins, outs, _dev_ptr(U_dev0, "U_dev0"), _dev_ptr(U_dev1, "U_dev1"), float(dt),
+        _ws_ptr(ws), ws.numel() * ws.element_size(), _stream(stream), up, down))
 
 
 def wenozn_cfl_dt(p: wenozn_problem, U: torch.Tensor, ws: torch.Tensor, stream=None) -> float:

@@ -117,6 +117,12 @@ def test_newer_entry_points_reject_bad_arguments_on_host(wz):
         wz.WENOZN_EINVAL
     assert L.wenozn_rk3_step_host(ctypes.byref(p1), h, h, A, 0.0, 0.0, None, A, 16, None) == wz.WENOZN_ENOMEM_WS
     assert L.wenozn_cfl_dt(ctypes.byref(p1), None, None, A, 1 << 30, None) == wz.WENOZN_EINVAL
+    hp = (ctypes.c_void_p * 2)(ctypes.cast(h, ctypes.c_void_p), None)
+    ok = (ctypes.c_void_p * 2)(ctypes.cast(h, ctypes.c_void_p), ctypes.cast(h, ctypes.c_void_p))
+    B_ = ctypes.c_void_p(512)
+    for count, ins, d0, d1 in ((0, ok, A, B_), (2, hp, A, B_), (2, ok, A, A), (2, ok, None, B_)):
+        assert L.wenozn_rk3_stream_host(ctypes.byref(p1), count, ins, ok, d0, d1, 0.0, A, 1 << 30, None, None,
+                                        None) == wz.WENOZN_EINVAL
     assert L.wenozn_cfl_dt(ctypes.byref(p1), A, None, ctypes.c_void_p(257), 1 << 30, None) == wz.WENOZN_EINVAL
     # FP64 rate probe: sizes outside [4, 2^32], no result pointer
     g = ctypes.c_double(0.0)

@@ -50,7 +50,11 @@ def test_rhs_vjp_elementwise_against_oracle_jacobian(wz, orc, system, bc, n):
     ws = wz.vjp_workspace(p)
     wz.wenozn_rhs_vjp(p, dev(U), dev(lam), out, ws)
     want = (J.T @ lam.ravel()).reshape(U.shape)
-    assert np.abs(out.cpu().numpy() - want).max() <= 1e-10 * np.abs(want).max()
+    # relative to the scale of the summed terms (lam / dx times O(1) flux derivatives): on
+    # one cell both interfaces see the same stencil, the RHS vanishes identically and only
+    # the cancellation residue of those terms remains
+    scale = max(np.abs(want).max(), np.abs(lam).max() / 0.1)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-10 * scale
 
 
 @pytest.mark.parametrize("system,n,bc", [(1, 300, 1), (1, 257, 0), (0, 500, 0), (1, 4099, 1)])

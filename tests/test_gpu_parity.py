@@ -280,7 +280,8 @@ def test_rk3_step_host_equals_device_step(wz, system, nx, ny):
     state and time step bit for bit: pinned and pageable buffers, separate and shared in/out
     buffers, CFL, fixed and clipped steps, three steps chained through host memory."""
     U0 = inputs.euler1d_ic(nx, 3) if system == 1 else inputs.euler2d_ic(nx, ny, 3)
-    p = wz.wenozn_problem_init(system, nx, ny, 1.0 / nx, 1.0 / ny)
+    dx = 10.0 / nx if system == 1 else 1.0 / nx        # the families' domains: the fixed step is stable
+    p = wz.wenozn_problem_init(system, nx, ny, dx, 1.0 / ny)
     A, B = wz.Solver(p), wz.Solver(p)
     U_dev = torch.empty(p.shape, dtype=torch.float64, device="cuda")
     for dt, trem in ((0.0, 0.0), (1e-4, 0.0), (0.0, 1e-5)):
@@ -301,6 +302,32 @@ def test_rk3_step_host_equals_device_step(wz, system, nx, ny):
         wz.wenozn_rk3_step_host(p, h, h, U_dev, B.ws)
     torch.cuda.synchronize()
     assert torch.equal(h, a.cpu())
+    assert A.status() == 0 and B.status() == 0
+
+
+@pytest.mark.parametrize("copy_streams", [True, False])
+def test_rk3_stream_host_equals_device_steps(wz, copy_streams):
+    """The streaming host-buffer call gives, for each of its states, the device step's result
+    bit for bit: five different states (CFL and fixed steps), outputs distinct or equal to the
+    inputs, with and without separate copy streams, and the call ordered on its stream."""
+    nx, ny = 160, 120
+    p = wz.wenozn_problem_init(2, nx, ny, 1.0 / nx, 1.0 / ny)
+    states = [inputs.euler2d_ic(nx, ny, 20 + k) for k in range(5)]
+    A, B = wz.Solver(p), wz.Solver(p)
+    for dt in (0.0, 2e-4):
+        want = []
+        for U0 in states:
+            a = dev(U0)
+            A.step(a, dt=dt)
+            want.append(a.cpu())
+        ins = [torch.from_numpy(U0.copy()).pin_memory() for U0 in states]
+        outs = [torch.empty_like(x).pin_memory() for x in ins[:3]] + ins[3:]     # the last two in place
+        d0, d1 = (torch.empty(p.shape, dtype=torch.float64, device="cuda") for _ in range(2))
+        kw = {"upload_stream": torch.cuda.Stream(), "download_stream": torch.cuda.Stream()} if copy_streams else {}
+        wz.wenozn_rk3_stream_host(p, ins, outs, d0, d1, B.ws, dt, **kw)
+        torch.cuda.current_stream().synchronize()          # the call is ordered on its stream
+        for k in range(5):
+            assert torch.equal(outs[k], want[k]), (dt, k)
     assert A.status() == 0 and B.status() == 0
 
 
