@@ -299,10 +299,12 @@ wenozn_status wenozn_last_error(void* stream, int32_t* device_status);
  * --------------------------------------------------------------------------------------- */
 
 /* Workspace bytes of wenozn_rhs_vjp / wenozn_rk3_step_vjp: the forward workspace of
- * wenozn_workspace_size followed by per-interface cotangent contributions (12 doubles per
- * interface for advection, 42 for Euler), per-block partial sums, two control words and two
- * state-sized cotangent vectors.  A workspace of
- * this size also serves wenozn_rhs and wenozn_rk3_step. */
+ * wenozn_workspace_size followed by per-interface cotangent contributions (advection: 12
+ * doubles per interface) or five correction records (Euler: about 4 doubles per 27 cells
+ * each: the per-block sums and boundary terms one VJP launch leaves to the launches that read
+ * its output), control words and two state-sized cotangent vectors.  A workspace of this
+ * size also serves wenozn_rhs and wenozn_rk3_step.  Calls sharing a workspace must not run
+ * concurrently. */
 wenozn_status wenozn_vjp_workspace_size(const wenozn_problem* p, size_t* bytes);
 
 /* out = J(U)^T lam with J the Jacobian of the RHS of Eq. (2) (LF splitting, Roe-averaged

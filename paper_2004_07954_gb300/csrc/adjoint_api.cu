@@ -9,8 +9,12 @@ VjpArgs vjp_args(const wenozn_problem& p, const Layout& L, void* ws) {
     VjpArgs v;
     std::memset(&v, 0, sizeof v);
     v.C = reinterpret_cast<double*>(ws_base(ws) + L.C);
-    v.partial = reinterpret_cast<double*>(ws_base(ws) + L.partial);
+    v.rec = v.C;
+    v.rec_stride = vjp_rec_stride(p.nx);
     v.ctl = reinterpret_cast<unsigned*>(ws_base(ws) + L.vjp_ctl);
+    v.prec[0] = v.prec[1] = v.prec[2] = -1;
+    v.lam_slot = -1;
+    v.x_slot[0] = v.x_slot[1] = v.x_slot[2] = -1;
     v.n = p.nx;
     v.bc = p.bc_x;
     v.rdx = 1.0 / p.dx;
@@ -34,32 +38,70 @@ wenozn_status check_vjp(const wenozn_problem* p, void* ws, size_t ws_bytes, Layo
     return WENOZN_OK;
 }
 
+// The state of a chain of Euler stage launches within one call: the launch count, the
+// record each of lam, Ub2 and Ub1 still has pending (-1: none), and each record's d.
+struct VjpChain {
+    int t = 0;
+    int lam_rec = -1, ub2_rec = -1, ub1_rec = -1;
+    double d[kVjpRecs] = {};
+};
+
+// Sets up launch v of the chain: it writes record t mod kVjpRecs; `lam_rec` and the X_k
+// records (-1: none; X_k == lam: read through lam's corrections) become pending slots.
+void chain_launch(VjpChain& ch, VjpArgs& v, int lam_rec, const int x_rec[3], bool complete) {
+    v.rec_out = ch.t % kVjpRecs;
+    v.prec[0] = v.prec[1] = v.prec[2] = -1;
+    int np = 0;
+    auto slot_of = [&](int r) {
+        if (r < 0) return -1;
+        for (int q = 0; q < np; ++q)
+            if (v.prec[q] == r) return q;
+        v.prec[np] = r;
+        return np++;
+    };
+    v.lam_slot = slot_of(lam_rec);
+    const double* X[3] = {v.X1, v.X2, v.X3};
+    for (int q = 0; q < 3; ++q) v.x_slot[q] = !X[q] ? -1 : (X[q] == v.lam ? -2 : slot_of(x_rec[q]));
+    v.complete = complete ? 1 : 0;
+    ch.d[v.rec_out] = v.d;
+    for (int r = 0; r < kVjpRecs; ++r) v.rec_d[r] = ch.d[r];
+    ++ch.t;
+}
+
 // Reverse of U3 = U0/3 + 2/3 (U2 + dt L(U2)), U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)),
-// U1 = U0 + dt L(U0), given the stage inputs and their LF speeds (bit patterns).
+// U1 = U0 + dt L(U0), given the stage inputs and their LF speeds (bit patterns).  `last`:
+// the call ends with this step, whose final launch completes in place.
 wenozn_status reverse_stages(const wenozn_problem& p, const Layout& L, void* ws, const double* U0,
                              const double* U1, const double* U2, const unsigned long long* a0,
                              const unsigned long long* a1, const unsigned long long* a2, double dt,
-                             double* lam, cudaStream_t s, bool clear_ctl = true) {
+                             double* lam, cudaStream_t s, VjpChain& ch, bool last) {
     double* ub2 = reinterpret_cast<double*>(ws_base(ws) + L.ub2);
     double* ub1 = reinterpret_cast<double*>(ws_base(ws) + L.ub1);
     VjpArgs v = vjp_args(p, L, ws);
-    // the control words (argmax, ticket counter) are zero after every stage; clear them
-    // before a sequence starts
-    cudaError_t e = clear_ctl ? cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s) : cudaSuccess;
+    // the control words (argmax words, ticket counter) are zero before a chain starts
+    cudaError_t e = ch.t == 0 ? cudaMemsetAsync(v.ctl, 0, (kVjpRecs + 1) * sizeof(unsigned), s) : cudaSuccess;
     if (e != cudaSuccess) return WENOZN_ECUDA;
     // Ub2 = 2/3 lam + 2/3 dt J(U2)^T lam
     v.U = U2; v.lam = lam; v.alpha_bits = a2; v.out = ub2;
     v.X1 = lam; v.c1 = 2.0 / 3.0; v.d = (2.0 / 3.0) * dt;
+    const int none[3] = {-1, -1, -1};
+    chain_launch(ch, v, ch.lam_rec, none, false);
     e = launch_vjp(p.system, v, s);
+    ch.ub2_rec = v.rec_out;
     if (e == cudaSuccess) {                 // Ub1 = 1/4 Ub2 + 1/4 dt J(U1)^T Ub2
         v.U = U1; v.lam = ub2; v.alpha_bits = a1; v.out = ub1;
         v.X1 = ub2; v.c1 = 0.25; v.d = 0.25 * dt;
+        chain_launch(ch, v, ch.ub2_rec, none, false);
         e = launch_vjp(p.system, v, s);
+        ch.ub1_rec = v.rec_out;
     }
     if (e == cudaSuccess) {                 // lam <- lam/3 + 3/4 Ub2 + Ub1 + dt J(U0)^T Ub1
         v.U = U0; v.lam = ub1; v.alpha_bits = a0; v.out = lam;
         v.X1 = lam; v.c1 = 1.0 / 3.0; v.X2 = ub2; v.c2 = 0.75; v.X3 = ub1; v.c3 = 1.0; v.d = dt;
+        const int xr[3] = {ch.lam_rec, ch.ub2_rec, -1};
+        chain_launch(ch, v, ch.ub1_rec, xr, last);
         e = launch_vjp(p.system, v, s);
+        ch.lam_rec = last ? -1 : v.rec_out;
     }
     return cuda_status(e);
 }
@@ -91,13 +133,16 @@ wenozn_status wenozn_rhs_vjp(const wenozn_problem* p, const double* U, const dou
         e = launch_max_wavespeed(p->system, U, p->nx, p->gamma, p->adv_speed, ctrl->alpha[0], &ctrl->status, s);
     VjpArgs v = vjp_args(*p, L, ws);
     note_status(stream, &ctrl->status);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.ctl, 0, (kVjpRecs + 1) * sizeof(unsigned), s);
     if (e == cudaSuccess) {
         v.U = U;
         v.lam = lam;
         v.alpha_bits = ctrl->alpha[0];
         v.out = out;
         v.d = 1.0;
+        VjpChain ch;
+        const int none[3] = {-1, -1, -1};
+        chain_launch(ch, v, -1, none, true);
         e = launch_vjp(p->system, v, s);
     }
     return cuda_status(e);
@@ -139,7 +184,8 @@ wenozn_status wenozn_rk3_step_vjp(const wenozn_problem* p, const double* U, doub
     }
     if (e != cudaSuccess) return WENOZN_ECUDA;
     const unsigned long long* a = &ctrl->alpha[0][0];
-    return reverse_stages(*p, L, ws, U, u1, u2, a, a + 2, a + 4, dt, lam, s);
+    VjpChain ch;
+    return reverse_stages(*p, L, ws, U, u1, u2, a, a + 2, a + 4, dt, lam, s, ch, true);
 }
 
 wenozn_status wenozn_rk3_step_vjp_stages(const wenozn_problem* p, const double* U, const double* U1,
@@ -151,7 +197,8 @@ wenozn_status wenozn_rk3_step_vjp_stages(const wenozn_problem* p, const double* 
     if (!U || !U1 || !U2 || !alphas || !lam || !(std::isfinite(dt) && dt > 0.0)) return WENOZN_EINVAL;
     if (lam == U || lam == U1 || lam == U2) return WENOZN_EINVAL;
     const unsigned long long* a = reinterpret_cast<const unsigned long long*>(alphas);
-    return reverse_stages(*p, L, ws, U, U1, U2, a, a + 1, a + 2, dt, lam, static_cast<cudaStream_t>(stream));
+    VjpChain ch;
+    return reverse_stages(*p, L, ws, U, U1, U2, a, a + 1, a + 2, dt, lam, static_cast<cudaStream_t>(stream), ch, true);
 }
 
 wenozn_status wenozn_workspace_stages(void* ws, const wenozn_problem* p, const double** U1, const double** U2,
@@ -212,9 +259,10 @@ wenozn_status wenozn_rk3_vjp_run(const wenozn_problem* p, const double* X, const
     const int64_t ns = int64_t(nvar_of(p->system)) * p->nx;
     const unsigned long long* A = reinterpret_cast<const unsigned long long*>(alphas);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VjpChain ch;
     for (int64_t k = nsteps - 1; k >= 0; --k) {
         st = reverse_stages(*p, L, ws, X + k * ns, S1 + k * ns, S2 + k * ns, A + 3 * k, A + 3 * k + 1,
-                            A + 3 * k + 2, dt, lam, s, k == nsteps - 1);
+                            A + 3 * k + 2, dt, lam, s, ch, k == 0);
         if (st != WENOZN_OK) return st;
     }
     return WENOZN_OK;

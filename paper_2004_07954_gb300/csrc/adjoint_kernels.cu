@@ -118,8 +118,9 @@ constexpr int kGather = 64;             // cells per advection gather block
 struct EulerSmem {
     double U[3][kCells];
     double hp[3][kCells], hm[3][kCells];
-    double u[kCells], H[kCells], sq[kCells], r[kCells];
-    double red[3][36][kTI];             // per field: hbar+ (5 x 3), hbar- (5 x 3), 6 Roe scalars
+    double u[kCells], H[kCells], sq[kCells], r[kCells], Ep[kCells];
+    double red[3][19][kTI];             // per field: cotangents of its projected h+ (5) and h- (5),
+                                        // half its left-eigenvector row (3), 6 Roe scalars
 };
 
 // ---------------------------------------------------------------------------------------
@@ -134,15 +135,27 @@ struct EulerSmem {
 //     to the block's partial;
 //   - the stencil positions outside the grid (ghost cells -3..-1 and n..n+2): the summed
 //     contributions of each block's owned interfaces go to that block's slot;
-// and the block that finishes last (each block fences its writes and takes a ticket from
-// an atomic counter: the memory-fence pattern of the CUDA programming guide) sums the
-// partials in block order, adds d abar d(|u| + c)/dU at the argmax cell of the LF speed
-// (|x|' = 0 at 0) and the ghost contributions through J_F^T at the cells they map to, and
-// resets the argmax word and the counter for the next launch.  Every sum has a fixed order,
-// so the result is deterministic.
+// A block that needs the result of every block (the sum of the partials times the speed
+// derivative at the argmax cell, and the ghost contributions mapped through J_F^T to the
+// cells they stand for) cannot have it before the launch ends.  So each launch leaves those
+// terms in a correction record (one of kVjpRecs, in a ring: the partials, the edge blocks'
+// ghost slots, the argmax candidates' speed derivatives and the argmax word), and leaves
+// the at most seven cells they touch uncorrected in its output.  The launches that read
+// that output later (as the cotangent input of the next stage, or as one of the RK
+// combination's terms up to three stages on) apply the pending corrections as they read:
+// a block resolves a record only if one of the cells it reads is a target, which only the
+// first and last blocks and the block holding the argmax cell do, and forms exactly the
+// value x + add (or fma(d abar, d(|u| + c)/dU, x)) that an in-place completion would have
+// stored.  The last launch of a call completes in place instead: each block fences its
+// writes and takes a ticket from an atomic counter (the memory-fence pattern of the CUDA
+// programming guide), and the block that finishes last applies the record to the output
+// and resets the argmax word and the counter.  Every sum has a fixed order, so the result
+// is deterministic and does not depend on which launches complete in place.
 // ---------------------------------------------------------------------------------------
 constexpr int kOwn = kTI - 5;           // cells owned by a block
 constexpr int kGhostSlot = 6 * 9;       // 6 ghost cells x (flux, LF, Roe) x 3 components
+constexpr int kWin = kTI + 1;           // cotangent window: cells j0 - 1 .. j0 + kTI - 1
+constexpr int kEnt = 7;                 // pending corrections of a record: 6 ghost targets + the argmax
 
 struct StageSmem {
     EulerSmem e;
@@ -151,25 +164,43 @@ struct StageSmem {
     double sF[3][kOwn];                    // gathered flux parts, exchanged between component threads
     double ghost[6][3][3];                 // ghost slots x (flux, LF, Roe) x component
     double red[3];
+    double lamw[3][kWin];                  // the cotangent input on the window, corrections applied
+    double pcq[kVjpPend][6][3];            // input records: ghost slots summed over the edge blocks,
+    double pds[kVjpPend][3];               //   the argmax cell's speed derivative,
+    double pred[kVjpPend][3];              //   per-warp sums of the partials,
+    double pa[kVjpPend][kEnt], pb[kVjpPend][kEnt][3];   // and their entries: x <- fma(pa, pb_m, x)
+    int pcell[kVjpPend][kEnt];                           //   at cell pcell (-1: none)
     int last;                              // this block finished last
     int im;                                // the LF speed's argmax cell (completion step)
     int cand;                              // the block's lowest LF-argmax candidate cell
     int tgt[6];                            // the cells the ghost slots map to (completion step)
 };
 
-// Row m of J_F^T applied to (F0, F1, F2) at the state (rho, mom, E): F = (m, m u + p,
-// u (E + p)), u = m/rho, p = (gamma - 1)(E - m u/2).
-__device__ __forceinline__ double jft_row(int m, double F0, double F1, double F2, double rho, double mom,
-                                          double E, double gamma) {
-    const double gm1 = gamma - 1.0;
-    const double r = rcp_nr(rho), u = mom * r;
-    const double p = gm1 * (E - 0.5 * mom * u);
-    const double Ep = E + p;
+// Record layout (doubles): partials [nb], ghost slots [3 edge blocks][18], candidates'
+// speed derivatives [nb][3], and abar once a later launch has summed the partials.
+__host__ __device__ inline int64_t rec_ghost(int nb) { return nb; }
+__host__ __device__ inline int64_t rec_dsdu(int nb) { return int64_t(nb) + 54; }
+__host__ __device__ inline int64_t rec_abar(int nb) { return 4 * int64_t(nb) + 54; }
+__device__ inline int edge_index(int b, int nb) { return b == 0 ? 0 : (b == nb - 1 ? 2 : 1); }
+
+// Row m of J_F^T applied to (F0, F1, F2) at a state with momentum mom, velocity u, 1/rho = r
+// and E + p = Ep: F = (m, m u + p, u (E + p)), u = m/rho, p = (gamma - 1)(E - m u/2).
+__device__ __forceinline__ double jft_row_q(int m, double F0, double F1, double F2, double mom, double u,
+                                            double r, double Ep, double gm1) {
     const double pb = fma(F2, u, F1);
     if (m == 2) return fma(F2, u, gm1 * pb);                                      // E bar
     const double ub = fma(F1, mom, F2 * Ep) - gm1 * 0.5 * mom * pb;
     if (m == 1) return fma(ub, r, fma(F1, u, F0) - gm1 * 0.5 * u * pb);          // m bar
     return -ub * u * r;                                                            // rho bar
+}
+
+// The same at the state (rho, mom, E).
+__device__ __forceinline__ double jft_row(int m, double F0, double F1, double F2, double rho, double mom,
+                                          double E, double gamma) {
+    const double gm1 = gamma - 1.0;
+    const double r = rcp_nr(rho), u = mom * r;
+    const double p = gm1 * (E - 0.5 * mom * u);
+    return jft_row_q(m, F0, F1, F2, mom, u, r, E + p, gm1);
 }
 
 __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
@@ -178,10 +209,65 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     pdl_wait();
     const int n = a.n, nb = int(gridDim.x), b = int(blockIdx.x), tid = threadIdx.x;
     const int c0 = b * kOwn, j0 = c0 - 2;        // first owned cell, first interface
+    const int w0 = j0 - 1;                       // first cell of the cotangent window
     const double gm1 = a.gamma - 1.0;
     const unsigned long long abits = a.alpha_bits[0];
-    const double alpha = __longlong_as_double((long long)abits);
+    const double alpha = __longlong_as_double((long long)abits), half_alpha = 0.5 * alpha;
+    // the record the next launch writes is no longer read by anyone: clear its argmax word
+    if (b == 0 && tid == 0) a.ctl[(a.rec_out + 1) % kVjpRecs] = 0u;
     if (tid == 0) S.cand = n;
+    // loads whose results are used after the cell phase: the cotangent window, the argmax
+    // words of the input records and, where a ghost target lies in the window, their ghost
+    // slots
+    const int lo = w0 > 0 ? w0 : 0, hi = (w0 + kWin < n ? w0 + kWin : n) - 1;     // grid cells of the window
+    int tg[6];
+    bool gwin = false;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        tg[q] = ghost_src(q < 3 ? q - 3 : n + q - 3, n, a.bc);
+        gwin = gwin || (tg[q] >= lo && tg[q] <= hi);
+    }
+    double lw[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int q = tid + t * 3 * kTI, m = q / kWin, g = w0 + q % kWin;
+        lw[t] = q < 3 * kWin && g >= 0 && g < n ? a.lam[int64_t(m) * n + g] : 0.0;
+    }
+    // the input records' argmax words (uniform loads); where the argmax cell lies in the
+    // window, its speed derivative and abar: the cotangent input's record sums its partials
+    // (the first 4 x 96 loaded now, used after the cell phase), the others were summed by
+    // the launch that read them as its cotangent input, which left abar in the record
+    int imp[kVjpPend];
+    bool need = false;
+#pragma unroll
+    for (int p = 0; p < kVjpPend; ++p) {
+        const unsigned key = a.prec[p] >= 0 ? __ldcg(a.ctl + a.prec[p]) : 0u;
+        imp[p] = key ? int(~key) : -1;
+        need = need || (a.prec[p] >= 0 && (gwin || (imp[p] >= lo && imp[p] <= hi)));
+    }
+    double gsl[kVjpPend][3], pv[4] = {0.0, 0.0, 0.0, 0.0}, ds[kVjpPend], abc[kVjpPend];
+#pragma unroll
+    for (int p = 0; p < kVjpPend; ++p) {
+        gsl[p][0] = gsl[p][1] = gsl[p][2] = 0.0;
+        ds[p] = abc[p] = 0.0;
+        if (a.prec[p] < 0) continue;
+        const double* R = a.rec + a.prec[p] * a.rec_stride;
+        if (gwin && tid < 18) {
+            gsl[p][0] = __ldcg(R + rec_ghost(nb) + tid);
+            if (nb >= 3) gsl[p][1] = __ldcg(R + rec_ghost(nb) + 18 + tid);
+            if (nb >= 2) gsl[p][2] = __ldcg(R + rec_ghost(nb) + 36 + tid);
+        }
+        if (imp[p] >= lo && imp[p] <= hi) {
+            if (p == a.lam_slot) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (tid + r * 3 * kTI < nb) pv[r] = __ldcg(R + tid + r * 3 * kTI);
+            } else {
+                abc[p] = __ldcg(R + rec_abar(nb));
+            }
+            if (tid >= 18 && tid < 21) ds[p] = __ldcg(R + rec_dsdu(nb) + int64_t(imp[p] / kOwn) * 3 + tid - 18);
+        }
+    }
     __syncthreads();
     for (int c = tid; c < kCells; c += 3 * kTI) {
         const int g = j0 - 3 + c;
@@ -191,17 +277,19 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             s[m] = a.U[int64_t(m) * n + src];
             sm.U[m][c] = s[m];
         }
-        const double r = 1.0 / s[0];
+        const double r = rcp_nr(s[0]);
         const double u = s[1] * r;
         const double p = gm1 * (s[2] - 0.5 * s[1] * u);
         const double Ep = s[2] + p;
         const double F[3] = {s[1], fma(s[1], u, p), u * Ep};
         for (int m = 0; m < 3; ++m) {
-            sm.hp[m][c] = 0.5 * fma(alpha, s[m], F[m]);
-            sm.hm[m][c] = 0.5 * fma(-alpha, s[m], F[m]);
+            const double hF = 0.5 * F[m];
+            sm.hp[m][c] = fma(half_alpha, s[m], hF);
+            sm.hm[m][c] = fma(-half_alpha, s[m], hF);
         }
         sm.u[c] = u;
         sm.H[c] = Ep * r;
+        sm.Ep[c] = Ep;
         sm.sq[c] = sqrt(s[0]);
         sm.r[c] = r;
         if (g == src && c >= 5 && c < 5 + kOwn) {   // an owned grid cell: is it the LF argmax?
@@ -210,25 +298,112 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             if ((unsigned long long)__double_as_longlong(sx) == abits) atomicMin(&S.cand, g);
         }
     }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int q = tid + t * 3 * kTI;
+        if (q < 3 * kWin) S.lamw[q / kWin][q % kWin] = lw[t];
+    }
+    if (need) {
+        // the pending records' inputs: ghost slots summed over the edge blocks, and abar =
+        // the partials summed in block order (strided runs, then the warps)
+        const int kw = tid / kTI;
+#pragma unroll
+        for (int p = 0; p < kVjpPend; ++p) {
+            if (a.prec[p] < 0) continue;
+            if (gwin && tid < 18) S.pcq[p][tid / 3][tid % 3] = (gsl[p][0] + gsl[p][1]) + gsl[p][2];
+            if (imp[p] >= lo && imp[p] <= hi) {
+                if (p == a.lam_slot) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (tid + r * 3 * kTI < nb) v += pv[r];
+                    const double* R = a.rec + a.prec[p] * a.rec_stride;
+                    for (int q = tid + 12 * kTI; q < nb; q += 3 * kTI) v += __ldcg(R + q);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    if ((tid & 31) == 0) S.pred[p][kw] = v;
+                } else if (tid == 0) {
+                    S.pred[p][0] = abc[p];
+                }
+                if (tid >= 18 && tid < 21) S.pds[p][tid - 18] = ds[p];
+            }
+        }
+    }
     __syncthreads();
     // the block's lowest candidate: offered for the global argmax (the lowest index on ties),
-    // with d(|u| + c)/dU of its state left for the completion step (|x|' = 0 at 0)
+    // with d(|u| + c)/dU of its state left in the record (|x|' = 0 at 0)
     if (tid == 2 * kTI && S.cand < n) {
         const int lc = S.cand - j0 + 3;
-        atomicMax(&a.ctl[0], ~unsigned(S.cand));
+        atomicMax(&a.ctl[a.rec_out], ~unsigned(S.cand));
         const double rho = sm.U[0][lc], mom = sm.U[1][lc], E = sm.U[2][lc];
         const double r = rcp_nr(rho), u = mom * r;
         const double p = gm1 * (E - 0.5 * mom * u);
         const double c2 = a.gamma * p * r, rcs = rsqrt(c2);
         const double sg = u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
         const double kk = 0.5 * a.gamma * r * rcs;                  // gamma / (2 c rho)
-        double* slot = a.C + int64_t(nb) * 18 + int64_t(b) * 3;
+        double* slot = a.rec + a.rec_out * a.rec_stride + rec_dsdu(nb) + int64_t(b) * 3;
         slot[0] = fma(sg, -u * r, kk * fma(gm1 * 0.5 * u, u, -p * r));
         slot[1] = fma(sg, r, -kk * gm1 * u);
         slot[2] = kk * gm1;
     }
 
     const int k = tid / kTI, i = tid % kTI, j = j0 + i;
+    // ---- the corrections pending on the inputs (block-uniform branches) ------------------
+    if (tid < kVjpPend * kEnt * 3) {
+        // entry e of record p, component mm: e < 6 the first ghost slot of a target cell in the
+        // window (its slots summed in slot order, plus the LF-speed term if the cell is also
+        // the argmax), e = 6 the argmax cell if it is no ghost target; the cotangent input's
+        // entries are applied to the window at once (distinct cells: no two threads meet)
+        const int p = tid / (kEnt * 3), e = (tid / 3) % kEnt, mm = tid % 3;
+        int cell = -1;
+        if (need && a.prec[p] >= 0) {
+            const int im = p == 0 ? imp[0] : (p == 1 ? imp[1] : imp[2]);
+            const bool im_in = im >= lo && im <= hi;
+            double abar = 0.0;
+            if (im_in) abar = p == a.lam_slot ? (S.pred[p][0] + S.pred[p][1]) + S.pred[p][2] : S.pred[p][0];
+            const double dabar = a.rec_d[a.prec[p]] * abar;
+            if (im_in && p == a.lam_slot && e == 0 && mm == 0)
+                a.rec[a.prec[p] * a.rec_stride + rec_abar(nb)] = abar;      // for the later readers
+            double pa = 1.0, pb = 0.0;
+            if (e < 6) {
+                int t = -1;
+                bool first = true;
+                double add = 0.0;
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+                    if (r == e) t = tg[r];
+                }
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+                    if (r < e && tg[r] == t) first = false;
+                    if (r >= e && tg[r] == t) add += S.pcq[p][r][mm];
+                }
+                if (first && t >= lo && t <= hi) {
+                    cell = t;
+                    pb = t == im ? fma(dabar, S.pds[p][mm], add) : add;
+                }
+            } else {
+                bool im_ghost = false;
+#pragma unroll
+                for (int r = 0; r < 6; ++r) im_ghost = im_ghost || tg[r] == im;
+                if (im_in && !im_ghost) {
+                    cell = im;
+                    pa = dabar;
+                    pb = S.pds[p][mm];
+                }
+            }
+            if (cell >= 0) {
+                S.pa[p][e] = pa;
+                S.pb[p][e][mm] = pb;
+                if (p == a.lam_slot) {
+                    double& x = S.lamw[mm][cell - w0];
+                    x = fma(pa, pb, x);
+                }
+            }
+        }
+        if (mm == 0) S.pcell[p][e] = cell;
+    }
+    if (need) __syncthreads();
     const bool live = j >= 0 && j <= n;
     const bool owned = live && ((j >= c0 && j < c0 + kOwn) || (j == n && b == nb - 1));
     const int cl = i + 2, cr = i + 3;            // cells j-1, j
@@ -267,26 +442,20 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     if (live) {
         double fpb[5], fmb[5];
         double Fb[3];
-        for (int m = 0; m < 3; ++m) {
-            const double right = j < n ? a.lam[int64_t(m) * n + j] : 0.0;
-            const double left = j > 0 ? a.lam[int64_t(m) * n + j - 1] : 0.0;
-            Fb[m] = (right - left) * a.rdx;
-        }
+        for (int m = 0; m < 3; ++m) Fb[m] = (S.lamw[m][i + 1] - S.lamw[m][i]) * a.rdx;   // cells j, j - 1
         const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
         const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, fpb) +
                           zn_vjp(fm, ghb, a.eps4, a.kappa, fmb);
         double Lb[3] = {0, 0, 0};
-        const double Lk[3] = {L0, L1, L2};
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             const double gpb = fpb[s], gmb = fmb[4 - s];     // cotangents of the projected h+_s, h-_{s+1}
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
-                sm.red[k][s * 3 + m][i] = gpb * Lk[m];
-                sm.red[k][15 + s * 3 + m][i] = gmb * Lk[m];
-            }
+            for (int m = 0; m < 3; ++m) Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
+            sm.red[k][s][i] = gpb;
+            sm.red[k][5 + s][i] = gmb;
         }
+        sm.red[k][10][i] = 0.5 * L0; sm.red[k][11][i] = 0.5 * L1; sm.red[k][12][i] = 0.5 * L2;
         const double Rb1 = Fb[1] * gh, Rb2 = Fb[2] * gh;
         double b2b, b1b, rcb, utb, cb, Htb;
         if (k == 0) {
@@ -299,28 +468,38 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             b2b = 0.5 * Lb[0]; b1b = 0.5 * fma(-ut, Lb[1], Lb[2]); rcb = 0.5 * fma(-ut, Lb[0], Lb[1]);
             utb = -0.5 * fma(rc, Lb[0], b1 * Lb[1]) + fma(c, Rb2, Rb1); cb = fma(ut, Rb2, Rb1); Htb = Rb2;
         }
-        sm.red[k][30][i] = b2b; sm.red[k][31][i] = b1b; sm.red[k][32][i] = rcb;
-        sm.red[k][33][i] = utb; sm.red[k][34][i] = cb; sm.red[k][35][i] = Htb;
+        sm.red[k][13][i] = b2b; sm.red[k][14][i] = b1b; sm.red[k][15][i] = rcb;
+        sm.red[k][16][i] = utb; sm.red[k][17][i] = cb; sm.red[k][18][i] = Htb;
     }
     __syncthreads();
-    // stencil positions 2k, 2k+1: sum the three fields' cotangents of h+-, and, for an owned
-    // interface, its share sum_s U_s . (hbar+ - hbar-)_s / 2 of the LF-speed cotangent
+    // stencil positions 2k, 2k+1: the cotangents of h+- there, (hbar+ +- hbar-)/2 summed over
+    // the three fields (row m of each field's left eigenvector times its projected cotangent),
+    // and, for an owned interface, its share sum_s U_s . (hbar+ - hbar-)_s / 2 of the
+    // LF-speed cotangent
     double ab = 0.0;
+    double hL[3][3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) hL[f][m] = live ? sm.red[f][10 + m][i] : 0.0;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int s = 2 * k + t;
+        double gp[3] = {0.0, 0.0, 0.0}, gm[3] = {0.0, 0.0, 0.0};
+        if (live) {
+            if (s <= 4)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) gp[f] = sm.red[f][s][i];
+            if (s >= 1)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) gm[f] = sm.red[f][4 + s][i];
+        }
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            double sumF = 0.0, dh = 0.0;
-            if (live) {
-                const double hpb = s <= 4 ? (sm.red[0][s * 3 + m][i] + sm.red[1][s * 3 + m][i]) + sm.red[2][s * 3 + m][i]
-                                          : 0.0;
-                const double hmb = s >= 1 ? (sm.red[0][12 + s * 3 + m][i] + sm.red[1][12 + s * 3 + m][i]) +
-                                                sm.red[2][12 + s * 3 + m][i] : 0.0;
-                sumF = 0.5 * (hpb + hmb);
-                dh = 0.5 * (hpb - hmb);
-                if (owned) ab = fma(sm.U[m][i + s], dh, ab);
-            }
+            const double hpb = fma(gp[2], hL[2][m], fma(gp[1], hL[1][m], gp[0] * hL[0][m]));
+            const double hmb = fma(gm[2], hL[2][m], fma(gm[1], hL[1][m], gm[0] * hL[0][m]));
+            const double sumF = hpb + hmb, dh = hpb - hmb;
+            if (owned) ab = fma(sm.U[m][i + s], dh, ab);
             S.cF[s][m][i] = sumF;
             S.cD[s][m][i] = dh;
         }
@@ -332,7 +511,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         if (live) {
             double sc[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][30 + q][i] + sm.red[1][30 + q][i]) + sm.red[2][30 + q][i];
+            for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][13 + q][i] + sm.red[1][13 + q][i]) + sm.red[2][13 + q][i];
             double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
             utb = fma(b2b * ut, b1, utb);
             b1b = fma(b2b * 0.5 * ut, ut, b1b);
@@ -347,7 +526,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             const double ub = utb * w, Hb = Htb * w;
             const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
             // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
-            Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, 0.5 * sqb / sm.sq[cc]));
+            Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, (0.5 * sqb) * (sm.sq[cc] * r)));
             Um = r * fma(-gm1 * uc, Hb, ub);
             UE = a.gamma * r * Hb;
         }
@@ -380,7 +559,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         S.ghost[q][part][m] = v;
     }
     __syncthreads();
-    if (tid == 0) a.partial[b] = (S.red[0] + S.red[1]) + S.red[2];
+    double* Rout = a.rec + a.rec_out * a.rec_stride;
+    if (tid == 0) Rout[b] = (S.red[0] + S.red[1]) + S.red[2];
     // ... and their share of the cells the ghosts map to, d (J_F^T flux + alpha LF + Roe)
     // with that cell's state: one value per slot and component
     if (edge && tid < 18) {
@@ -388,7 +568,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         const int tgt = ghost_src(q < 3 ? q - 3 : n + q - 3, n, a.bc);
         const double rho = a.U[tgt], mom = a.U[n + tgt], E = a.U[2 * int64_t(n) + tgt];
         const double jf = jft_row(m, S.ghost[q][0][0], S.ghost[q][0][1], S.ghost[q][0][2], rho, mom, E, a.gamma);
-        a.C[int64_t(b) * 18 + tid] = a.d * (fma(alpha, S.ghost[q][1][m], jf) + S.ghost[q][2][m]);
+        Rout[rec_ghost(nb) + edge_index(b, nb) * 18 + tid] = a.d * (fma(alpha, S.ghost[q][1][m], jf) + S.ghost[q][2][m]);
     }
     // the gather of the owned cells: thread (m, lc) sums component m of cell c0 + lc over the
     // positions s of interfaces c0 + lc + 3 - s (fixed order), exchanges the flux parts and
@@ -407,20 +587,36 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     if (tid < 3 * kOwn) S.sF[m][lc] = Fs;
     __syncthreads();
     if (mine) {
-        const double rho = sm.U[0][lc + 5], mom = sm.U[1][lc + 5], E = sm.U[2][lc + 5];
-        const double part = jft_row(m, S.sF[0][lc], S.sF[1][lc], S.sF[2][lc], rho, mom, E, a.gamma);
+        const int cc = lc + 5;
+        const double part = jft_row_q(m, S.sF[0][lc], S.sF[1][lc], S.sF[2][lc], sm.U[1][cc], sm.u[cc], sm.r[cc],
+                                      sm.Ep[cc], gm1);
         const double Ub = fma(alpha, Ds, part) + Rs;
         const int64_t idx = int64_t(m) * n + cell;
         double v = a.d * Ub;
-        if (a.X1) v = fma(a.c1, a.X1[idx], v);
-        if (a.X2) v = fma(a.c2, a.X2[idx], v);
-        if (a.X3) v = fma(a.c3, a.X3[idx], v);
+        const double* X[3] = {a.X1, a.X2, a.X3};
+        const double cx[3] = {a.c1, a.c2, a.c3};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (!X[t]) continue;
+            double x;
+            if (a.x_slot[t] == -2) {
+                x = S.lamw[m][lc + 3];                  // the cotangent input, corrected
+            } else {
+                x = X[t][idx];
+                const int p = a.x_slot[t];
+                if (p >= 0)
+                    for (int e = 0; e < kEnt; ++e)
+                        if (S.pcell[p][e] == cell) x = fma(S.pa[p][e], S.pb[p][e][m], x);
+            }
+            v = fma(cx[t], x, v);
+        }
         a.out[idx] = v;
     }
-    // the last block to finish completes the stage
+    if (!a.complete) return;
+    // the last launch of a call: the block that finishes last applies the record in place
     __threadfence();
     __syncthreads();
-    if (tid == 0) S.last = atomicAdd(&a.ctl[1], 1u) == unsigned(nb - 1);
+    if (tid == 0) S.last = atomicAdd(&a.ctl[kVjpRecs], 1u) == unsigned(nb - 1);
     __syncthreads();
     if (!S.last) return;
     __threadfence();
@@ -431,21 +627,21 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     if (tid >= 32 && tid < 38) S.tgt[tid - 32] = ghost_src(tid < 35 ? tid - 35 : n + tid - 35, n, a.bc);
     double v = 0.0;
 #pragma unroll 4
-    for (int q = tid; q < nb; q += 3 * kTI) v += __ldcg(a.partial + q);
+    for (int q = tid; q < nb; q += 3 * kTI) v += __ldcg(Rout + q);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (i == 0) S.red[k] = v;
     if (tid < 18) {
-        const int b1 = nb - 2, b2 = nb - 1;
-        double cq = __ldcg(a.C + tid);                                          // block 0
-        if (b1 > 0) cq += __ldcg(a.C + int64_t(b1) * 18 + tid);
-        if (b2 > 0 && b2 != b1) cq += __ldcg(a.C + int64_t(b2) * 18 + tid);
+        const double* G = Rout + rec_ghost(nb);             // blocks 0, nb - 2, nb - 1 (where distinct)
+        double cq = __ldcg(G + tid);
+        if (nb >= 3) cq += __ldcg(G + 18 + tid);
+        if (nb >= 2) cq += __ldcg(G + 36 + tid);
         S.ghost[tid / 3][0][tid % 3] = cq;
     } else if (tid < 21) {
         const int mm = tid - 18;
-        const unsigned key = __ldcg(a.ctl);
+        const unsigned key = __ldcg(a.ctl + a.rec_out);
         const int im = key ? int(~key) : -1;
-        S.ghost[0][1][mm] = im >= 0 ? __ldcg(a.C + int64_t(nb) * 18 + int64_t(im / kOwn) * 3 + mm) : 0.0;
+        S.ghost[0][1][mm] = im >= 0 ? __ldcg(Rout + rec_dsdu(nb) + int64_t(im / kOwn) * 3 + mm) : 0.0;
         if (mm == 0) S.im = im;
     }
     __syncthreads();
@@ -476,8 +672,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-        a.ctl[0] = 0u;
-        a.ctl[1] = 0u;
+        a.ctl[a.rec_out] = 0u;
+        a.ctl[kVjpRecs] = 0u;
     }
 }
 
@@ -593,16 +789,16 @@ static cudaError_t euler_interface_pad(size_t* pad) {
     return cudaSuccess;
 }
 
-// per-block partials: the advection interface blocks (kTI interfaces) or the Euler stage
-// blocks (kOwn cells), whichever are more
-int vjp_partial_count(int n) {
-    const int adv = (n + 1 + kTI - 1) / kTI, euler = (n + kOwn - 1) / kOwn;
-    return adv > euler ? adv : euler;
+// one correction record of the Euler stage kernel, in doubles (a multiple of 32)
+int64_t vjp_rec_stride(int n) {
+    const int64_t nb = (int64_t(n) + kOwn - 1) / kOwn;
+    return (rec_abar(int(nb)) + 1 + 31) / 32 * 32;
 }
 
-// per-interface contributions (advection), or the Euler stage blocks' ghost slots (which
-// fit: 21 ceil(n / kOwn) <= 42 (n + 1): 18 ghost corrections and 3 speed derivatives a block)
-size_t vjp_contrib_doubles(int nv, int n) { return size_t(n + 1) * (nv == 1 ? 12 : 42); }
+// per-interface contributions (advection), or the Euler stage kernel's correction records
+size_t vjp_contrib_doubles(int nv, int n) {
+    return nv == 1 ? size_t(n + 1) * 12 : size_t(kVjpRecs) * size_t(vjp_rec_stride(n));
+}
 
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
     if (system == 0) {

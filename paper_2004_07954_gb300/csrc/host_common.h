@@ -19,11 +19,11 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline int nvar_of(int system) { return system == WENOZN_ADVECTION_1D ? 1 : (system == WENOZN_EULER_1D ? 3 : 4); }
 
 // Workspace regions of wenozn_rhs / wenozn_rk3_step, followed by the extra regions the
-// adjoint entry points use (per-interface cotangent contributions, per-block partial sums,
-// two control words and two cotangent vectors).
+// adjoint entry points use (per-interface cotangent contributions for advection or the
+// Euler stage kernel's correction records, their control words and two cotangent vectors).
 struct Layout {
-    size_t ctrl, u1, u2, fx, gy, total;                 // forward
-    size_t C, partial, vjp_ctl, ub2, ub1, total_vjp;    // adjoint (1D only)
+    size_t ctrl, u1, u2, fx, gy, total;        // forward
+    size_t C, vjp_ctl, ub2, ub1, total_vjp;    // adjoint (1D only)
 };
 
 inline Layout layout_of(const wenozn_problem& p) {
@@ -37,8 +37,7 @@ inline Layout layout_of(const wenozn_problem& p) {
     L.gy = L.fx + align_up(nv * (nx + 1) * ny * sizeof(double));
     L.total = L.gy + (p.system == WENOZN_EULER_2D ? align_up(nv * nx * (ny + 1) * sizeof(double)) : 0);
     L.C = L.total;
-    L.partial = L.C + align_up(vjp_contrib_doubles(int(nv), int(nx)) * sizeof(double));
-    L.vjp_ctl = L.partial + align_up(size_t(vjp_partial_count(int(nx))) * sizeof(double));
+    L.vjp_ctl = L.C + align_up(vjp_contrib_doubles(int(nv), int(nx)) * sizeof(double));
     L.ub2 = L.vjp_ctl + kAlign;
     L.ub1 = L.ub2 + align_up(nv * nx * sizeof(double));
     L.total_vjp = L.ub1 + align_up(nv * nx * sizeof(double));

@@ -108,14 +108,20 @@ cudaError_t launch_batch_init(const BatchArgs& a, cudaStream_t s);
 cudaError_t launch_batch_stage(int shape, const BatchArgs& a, int sms, cudaStream_t s);
 
 // Adjoint of the 1D right-hand side (see adjoint_kernels.cu).
+// The Euler stage kernel's correction records: a ring of kVjpRecs (a launch's record is
+// read by the launches up to three stages later, and cleared by the one after those), and
+// at most kVjpPend records pending on one launch's inputs.
+constexpr int kVjpRecs = 5;
+constexpr int kVjpPend = 3;
+
 struct VjpArgs {
     const double* U;                       // stage input, [nv][n]
     const double* lam;                     // cotangent of L(U), [nv][n]
-    double* C;                             // per-interface contributions (advection) or the Euler stage
-                                           // blocks' ghost slots, vjp_contrib_doubles(nv, n)
-    double* partial;                       // [nblocks] per-block partial sums of the LF-speed cotangent
-    unsigned* ctl;                         // ctl[0]: ~(argmax of the LF speed), ctl[1]: ticket counter
-                                           // of the Euler stage kernel; zero between launches
+    double* C;                             // advection: per-interface contributions, vjp_contrib_doubles(1, n)
+    double* rec;                           // Euler: kVjpRecs correction records of rec_stride doubles
+    int64_t rec_stride;
+    unsigned* ctl;                         // ctl[r]: ~(argmax of the LF speed) of record r, ctl[kVjpRecs]:
+                                           // ticket counter of a completing launch; zero when unused
     const unsigned long long* alpha_bits;  // LF speed of U (bit pattern)
     double* out;                           // c1 X1 + c2 X2 + c3 X3 + d J^T lam
     const double* X1;
@@ -124,8 +130,14 @@ struct VjpArgs {
     double c1, c2, c3, d;
     int n, bc;
     double rdx, gamma, eps4, kappa, adv_speed;
+    int rec_out;                           // the record this launch writes
+    int prec[kVjpPend];                    // records with corrections pending on the inputs (-1: none)
+    int lam_slot;                          // index into prec of lam's record (-1: none)
+    int x_slot[3];                         // ... of X1..X3 (-1: none; -2: X_t is lam itself)
+    int complete;                          // apply this launch's own record in place (a call's last launch)
+    double rec_d[kVjpRecs];                // d of the launch that wrote each record
 };
-int vjp_partial_count(int n);
+int64_t vjp_rec_stride(int n);
 size_t vjp_contrib_doubles(int nv, int n);
 cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s);
 
