@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
     constexpr int CL = TI + 5;
     extern __shared__ double smem[];
     const CellPlanes<NV> sp(smem, CL);
-    double* sF = smem + CL * CellPlanes<NV>::kPerCell;        // [3][TI]
+    double* sF = smem + CL * CellPlanes<NV>::kPerCellDefault;  // [3][TI]
     __shared__ int s_inst;
     __shared__ float s_est[TI];                                // screened speed estimates
     __shared__ float s_red[THREADS / 32];
@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
             for (int k = 0; k < NV; ++k) Uc[k] = a.Us[k * a.total + o + g];
             split_cell<NV>(Uc, alpha, 0.0, gm1, sp, i);
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < CL - 1; i += THREADS) cell_diffs<NV>(sp, i, 1);
         __syncthreads();
         for (int jl = threadIdx.x; jl <= ncell; jl += THREADS) {     // interfaces c0 .. c0+ncell
             double Fh[NV];
@@ -186,14 +188,14 @@ __global__ void __launch_bounds__(256) batch_init_kernel(BatchArgs a) {
 
 template <int TI, int THREADS>
 cudaError_t launch_stage(const BatchArgs& a, int grid, cudaStream_t s) {
-    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCell + 3 * TI) * sizeof(double);
+    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCellDefault + 3 * TI) * sizeof(double);
     batch_stage_kernel<TI, THREADS><<<grid, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TI, int THREADS>
 cudaError_t configure_one() {
-    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCell + 3 * TI) * sizeof(double);
+    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCellDefault + 3 * TI) * sizeof(double);
     return cudaFuncSetAttribute(batch_stage_kernel<TI, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(smem));
 }
@@ -203,7 +205,7 @@ int resident_blocks() {
     // resident blocks per SM of this shape (same on every GB300; looked up once)
     static int cached = 0;
     if (cached > 0) return cached;
-    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCell + 3 * TI) * sizeof(double);
+    constexpr size_t smem = (size_t(TI + 5) * CellPlanes<3>::kPerCellDefault + 3 * TI) * sizeof(double);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<TI, THREADS>, THREADS, smem) !=
         cudaSuccess)

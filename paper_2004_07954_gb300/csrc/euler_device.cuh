@@ -9,11 +9,14 @@
 namespace wz {
 
 // Shared-memory planes of one tile of NC cells: split fluxes h+ and h- (NV planes each),
-// and for the Euler systems sqrt(rho), u_n, H (and u_t in 2D).
+// and for the Euler systems sqrt(rho), u_n, H (and u_t in 2D); the default Euler kernels
+// add the differences dh+-_c = h+-_c - h+-_{c+1} along the sweep (NV planes each), the
+// generic ones the cell's |u_n| + c.
 template <int NV>
 struct CellPlanes {
     static constexpr int kPerCell = NV == 1 ? 2 : 2 * NV + (NV == 4 ? 4 : 3);
     static constexpr int kPerCellGeneric = kPerCell + (NV == 1 ? 0 : 1);   // + |u_n| + c
+    static constexpr int kPerCellDefault = kPerCell + (NV == 1 ? 0 : 2 * NV);   // + dh+, dh-
     double* hp;
     double* hm;
     double* sr;
@@ -21,6 +24,8 @@ struct CellPlanes {
     double* H;
     double* ut;
     double* sp;          // generic kernels: the cell's |u_n| + c (local LF)
+    double* dp;          // default Euler kernels: dh+ and dh- (same storage as sp)
+    double* dm;
     int NC;
     __device__ __forceinline__ CellPlanes(double* base, int nc) : NC(nc) {
         hp = base;
@@ -30,8 +35,22 @@ struct CellPlanes {
         H = un + nc;
         ut = H + nc;
         sp = base + kPerCell * nc;
+        dp = sp;
+        dm = dp + NV * nc;
     }
 };
+
+// The split-flux differences of cell si and its neighbour si + stride along the sweep, once
+// per cell: the characteristic projection is linear, so the reconstructions' stencil
+// differences are projections of these (no cell difference is formed per interface and field).
+template <int NV>
+__device__ __forceinline__ void cell_diffs(const CellPlanes<NV>& s, int si, int stride) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        s.dp[k * s.NC + si] = s.hp[k * s.NC + si] - s.hp[k * s.NC + si + stride];
+        s.dm[k * s.NC + si] = s.hm[k * s.NC + si] - s.hm[k * s.NC + si + stride];
+    }
+}
 
 // One cell: Uc = (rho, m_n[, m_t], E) in the sweep direction's frame (or the scalar u with
 // the advection speed `a`), alpha the LF speed.  Writes h+- = (F +- alpha U)/2 and the Roe
@@ -147,8 +166,9 @@ __device__ __forceinline__ void split_cell_gen(const double* Uc, int split, doub
 }
 
 // Numerical flux F^ at the interface between the stencil's cells 2 and 3, the stencil being
-// the six cells base + k*stride, k = 0..5 (cells i-2 .. i+3 around x_{i+1/2}).
-// Fh is in the sweep direction's frame.
+// the six cells base + k*stride, k = 0..5 (cells i-2 .. i+3 around x_{i+1/2}); for the
+// Euler systems the planes dh+ of cells 0..3 and dh- of cells 1..4 must be filled
+// (cell_diffs).  Fh is in the sweep direction's frame.
 template <int NV>
 __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base, int stride,
                                                double gm1, double eps4, double kappa, double* Fh) {
@@ -184,27 +204,44 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
     // evaluated through their shared parts: with W = u h_1 + v h_2 - h_E,
     // Z = b2 h_0 - b1 W and B = (u h_0 - h_1)/(2c),
     //   l_u.h = h_0 - Z,  l_{u-+c}.h = Z/2 +- B,  l_shear.h = h_2 - v h_0.
-    auto project = [&](const double* hs, int i, double* g) {
-        const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
-        const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+    auto project = [&](const double* h, double* g) {
+        const double h0 = h[0], h1 = h[1], hE = h[NV - 1];
+        const double W = NV == 4 ? fma(u, h1, fma(v, h[2], -hE)) : fma(u, h1, -hE);
         const double Zh = fma(hb2, h0, -(hb1 * W));          // Z / 2
         const double Bi = fma(u, h0, -h1);                   // 2 c B
         g[0] = fma(hrc, Bi, Zh);
         g[1] = fma(-2.0, Zh, h0);
-        if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+        if (NV == 4) g[2] = fma(-v, h0, h[2]);
         g[NV - 1] = fma(-hrc, Bi, Zh);
     };
-    double gp[5][NV], gm[5][NV];
+    auto project_at = [&](const double* planes, int i, double* g) {
+        double h[NV];
 #pragma unroll
-    for (int st = 0; st < 5; ++st) {
-        project(s.hp, base + st * stride, gp[st]);
-        project(s.hm, base + (st + 1) * stride, gm[st]);
+        for (int k = 0; k < NV; ++k) h[k] = planes[k * NC + i];
+        project(h, g);
+    };
+    // Each field's reconstructions need only the first differences of its stencil and the
+    // centre value: plus side (g+ at cells 0..4) D_s = l.dh+ at cells s - 1, centre l.h+_2;
+    // minus side, the mirrored stencil of g- at cells 5..1, D_s = -l.dh- at cells 5 - s,
+    // centre l.h-_3; both centres at once as l.(h+_2 + h-_3).
+    double Dp[4][NV], Dm[4][NV], C[NV];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        project_at(s.dp, base + st * stride, Dp[st]);
+        project_at(s.dm, base + (st + 1) * stride, Dm[st]);
+    }
+    {
+        double hc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) hc[k] = s.hp[k * NC + base + 2 * stride] + s.hm[k * NC + base + 3 * stride];
+        project(hc, C);
     }
     double gh[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        gh[k] = zn_split_flux(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k],
-                              gm[0][k], gm[1][k], gm[2][k], gm[3][k], gm[4][k], eps4, kappa);
+    for (int k = 0; k < NV; ++k) {
+        const double fm = zn_flux_d(-Dm[3][k], -Dm[2][k], -Dm[1][k], -Dm[0][k], C[k], eps4, kappa);
+        gh[k] = zn_flux_d(Dp[0][k], Dp[1][k], Dp[2][k], Dp[3][k], fm, eps4, kappa);
+    }
     // back-projection F^ = R g^ with the right eigenvectors (columns)
     //   r_{u-c} = (1, u-c, [v,] H-uc), r_u = (1, u, [v,] q^2/2), r_shear = (0, 0, 1, v),
     //   r_{u+c} = (1, u+c, [v,] H+uc)

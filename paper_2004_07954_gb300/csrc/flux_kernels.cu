@@ -77,6 +77,15 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         else split_cell<NV>(Uc, alpha, a.adv_speed, gm1, sp, sidx(l, lc));
     }
     __syncthreads();
+    if (!GEN && NV > 1) {
+        // the split-flux differences of neighbouring cells along the sweep
+        for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
+            const int l = DIR == 0 ? idx / CL : idx % TA;
+            const int lc = DIR == 0 ? idx % CL : idx / TA;
+            if (lc < CL - 1) cell_diffs<NV>(sp, sidx(l, lc), kStride);
+        }
+        __syncthreads();
+    }
 
     // ---- interfaces ----------------------------------------------------------------
     const int nint = DIR == 0 ? a.nx + 1 : a.ny + 1;
@@ -113,7 +122,7 @@ cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int NC = (TI + 5) * TA;
     constexpr size_t smem =
-        size_t(NC) * (GEN ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCell) * sizeof(double);
+        size_t(NC) * (GEN ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCellDefault) * sizeof(double);
     // the dynamic shared-memory limit is a per-device function attribute
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;

@@ -219,13 +219,20 @@ __host__ __device__ __forceinline__ double zn_correction_rescaled(double D1, dou
 // f^ = c + num / den, with the rescaled evaluation when the fast one left the double range.
 // den is then a positive normal number (eps >= 1e-60 makes den >= 10 (4 eps)^5), so the
 // Newton reciprocal applies.
-__host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
-                                                   double eps4, double kappa) {
-    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+// base + (f^ - c) from the stencil's first differences D1..D4 (f^ - c depends on nothing
+// else), so that a caller holding the differences and several centre values adds them once.
+__host__ __device__ __forceinline__ double zn_flux_d(double D1, double D2, double D3, double D4, double base,
+                                                     double eps4, double kappa) {
     double num, den;
     zn_num_den(D1, D2, D3, D4, eps4, kappa, num, den);
-    if (zn_out_of_range(num, den, D1, D2, D3, D4)) return c + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, 0);
-    return fma(num, rcp_nr(den), c);
+    if (zn_out_of_range(num, den, D1, D2, D3, D4))
+        return base + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, 0);
+    return fma(num, rcp_nr(den), base);
+}
+
+__host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,
+                                                   double eps4, double kappa) {
+    return zn_flux_d(a - b, b - c, c - d, d - e, c, eps4, kappa);
 }
 
 // f^+ + f^- at one interface: plus side from (p0..p4) = h+_{i-2..i+2}, minus side from the
