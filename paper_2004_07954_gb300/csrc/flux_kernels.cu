@@ -44,6 +44,9 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     const int j0 = (DIR == 0 ? blockIdx.x : blockIdx.y) * TI;   // first interface of the tile
     const int l0 = (DIR == 0 ? blockIdx.y : blockIdx.x) * TA;   // first line of the tile
     const int64_t nc = int64_t(a.nx) * a.ny;
+    // cells this tile's interfaces use along the sweep (the last tile of a line may hold
+    // fewer than TI interfaces, e.g. only the boundary interface n)
+    const int cl_used = min(TI, n + 1 - j0) + 5;
 
     // cell (line l, along index lc) -> shared index; the fastest thread index runs along
     // the contiguous direction of global memory
@@ -60,6 +63,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
         const int l = DIR == 0 ? idx / CL : idx % TA;
         const int lc = DIR == 0 ? idx % CL : idx / TA;
+        if (lc >= cl_used) continue;
         const int line = min(l0 + l, nlines - 1);
         const int gi = j0 - 3 + lc;
         const int g = ghost_src(gi, n, a.bc);
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
             const int l = DIR == 0 ? idx / CL : idx % TA;
             const int lc = DIR == 0 ? idx % CL : idx / TA;
-            if (lc < CL - 1) cell_diffs<NV>(sp, sidx(l, lc), kStride);
+            if (lc < cl_used - 1) cell_diffs<NV>(sp, sidx(l, lc), kStride);
         }
         __syncthreads();
     }

@@ -196,6 +196,52 @@ def test_chained_reverse_is_repeatable_at_the_benchmark_size(wz):
     assert torch.equal(step, runs[0])
 
 
+def _wave_speeds(U, gamma=1.4):
+    rho, m, E = U[0, 0], U[1, 0], U[2, 0]
+    u = m / rho
+    return np.abs(u) + np.sqrt(gamma * (gamma - 1.0) * (E - 0.5 * m * u) / rho)
+
+
+@pytest.mark.parametrize("bc,target", [(1, 0), (1, 199), (1, 26), (1, 27), (1, 29), (0, 1), (0, 198), (0, 54)])
+def test_reverse_with_the_lf_argmax_at_a_correction_target(wz, orc, bc, target):
+    """The LF speed's argmax planted (a one-cell pressure spike that holds it through every
+    stage input) at a cell the deferred corrections touch: a ghost-cell target at either
+    boundary (outflow: cells 0, n-1; periodic: 0..2, n-3..n-1), or a cell in the windows of
+    two neighbouring blocks (27 owned cells each: 24..29 and 51..56 lie in two).  Two
+    reverse steps in one chained call (six stage launches: every pending slot is read)
+    against the oracle's binary128 forward-mode derivative, and bit for bit against the
+    step-by-step reverse (each call completing in place)."""
+    n, m = 200, 2
+    p, P = _problem(wz, orc, 1, n, 10.0 / n, bc)
+    W = inputs.adjoint_ic(n, seed=9)
+    rho, mom = W[0, 0], W[1, 0]
+    u = mom / rho
+    pr = 0.4 * (W[2, 0] - 0.5 * mom * u)
+    pr[target] *= 1.8
+    U0 = inputs.cons_from_prim(rho, u, pr).reshape(3, 1, n).copy()
+    dt = 0.1 * p.dx / orc.max_wavespeed(P, U0)
+    ws = wz.vjp_workspace(p)
+    X = torch.empty((m + 1,) + tuple(U0.shape), dtype=torch.float64, device="cuda")
+    S1, S2 = torch.empty_like(X[:m]), torch.empty_like(X[:m])
+    A = torch.empty(3 * m + 1, dtype=torch.float64, device="cuda")
+    X[0].copy_(dev(U0))
+    wz.wenozn_rk3_run_keep(p, X, S1, S2, A, m, dt, ws)
+    for k in range(m):                                    # the planted argmax holds
+        for st in (X[k], S1[k], S2[k]):
+            assert int(np.argmax(_wave_speeds(st.cpu().numpy()))) == target
+    g = np.random.default_rng(11)
+    for _ in range(2):
+        v, lam = g.normal(size=U0.shape), g.normal(size=U0.shape)
+        _, Jv = orc.rollout_jvp_quad(P, U0, v, dt, m)
+        l1, l2 = dev(lam), dev(lam)
+        wz.wenozn_rk3_vjp_run(p, X, S1, S2, A, m, dt, l1, ws)
+        for k in reversed(range(m)):
+            wz.wenozn_rk3_step_vjp_stages(p, X[k], S1[k], S2[k], A[3 * k:3 * k + 3], dt, l2, ws)
+        assert torch.equal(l1, l2)
+        a, b = float(np.sum(lam * Jv)), float(np.sum(l1.cpu().numpy() * v))
+        assert b == pytest.approx(a, rel=1e-10)
+
+
 def _loss_grad(wz, p, U0, dt, steps, target, every=1):
     from paper_2004_07954_gb300.rollout import rollout
     U = dev(U0).requires_grad_(True)
