@@ -289,7 +289,7 @@ def bench_euler1d(wenozn, inputs, seed: int, n: int = 1 << 20, K: int = 100) -> 
                         f"{K} chained SSP-RK3 steps",
             "metric": "cell-updates/s", "value": n / (ms_step / 1e3), "ms_per_step": round(ms_step, 4),
             "fp64_frac": round(OPS_1D_CELL_UPDATE * n / (ms_step / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
-            "flux_kernel": {"kernel": "flux_kernel<3,0> (512-interface tiles)", "ms": round(flux_ms, 4),
+            "flux_kernel": {"kernel": "flux_kernel<3,0> (507-interface tiles)", "ms": round(flux_ms, 4),
                             "frac": round(flux_flops / (flux_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "device_status": status}
 

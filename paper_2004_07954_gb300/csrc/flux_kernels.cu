@@ -19,11 +19,12 @@ namespace wz {
 namespace {
 
 // Tile shapes: TI interfaces along the sweep x TA lines across it, THREADS per block.
-// Long 1D lines use 512-interface tiles; short ones (fewer tiles than twice the SM count)
-// use 64-interface tiles of 64 threads so that every SM gets work.
+// Long 1D lines use 507-interface tiles (512 cells with the halo: two full rounds of the cell
+// and difference passes); short ones (fewer tiles than twice the SM count) use 64-interface
+// tiles of 64 threads so that every SM gets work.
 template <int NV, int DIR, bool SMALL = false> struct Tile;
-template <> struct Tile<1, 0, false> { static constexpr int TI = 512, TA = 1, THREADS = 256; };
-template <> struct Tile<3, 0, false> { static constexpr int TI = 512, TA = 1, THREADS = 256; };
+template <> struct Tile<1, 0, false> { static constexpr int TI = 507, TA = 1, THREADS = 256; };
+template <> struct Tile<3, 0, false> { static constexpr int TI = 507, TA = 1, THREADS = 256; };
 template <> struct Tile<1, 0, true> { static constexpr int TI = 64, TA = 1, THREADS = 64; };
 template <> struct Tile<3, 0, true> { static constexpr int TI = 64, TA = 1, THREADS = 64; };
 template <> struct Tile<4, 0, false> { static constexpr int TI = 128, TA = 4, THREADS = 256; };
@@ -161,7 +162,7 @@ template <bool GEN>
 cudaError_t launch_flux_t(int system, int dir, const FluxArgs& a, cudaStream_t s) {
     if (system != 2) {
         // 1D: short lines take the small tiles so that every SM has work
-        const int64_t big_tiles = (int64_t(a.nx) + 512) / 512 * a.ny;
+        const int64_t big_tiles = (int64_t(a.nx) + Tile<3, 0>::TI) / Tile<3, 0>::TI * a.ny;
         const bool small = big_tiles < 2 * sm_count_cached();
         if (system == 0) return small ? launch_one<1, 0, true, GEN>(a, s) : launch_one<1, 0, false, GEN>(a, s);
         return small ? launch_one<3, 0, true, GEN>(a, s) : launch_one<3, 0, false, GEN>(a, s);
