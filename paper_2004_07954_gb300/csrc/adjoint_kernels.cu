@@ -4,13 +4,14 @@
 // RHS: L_i = -(F^_{i+1/2} - F^_{i-1/2})/dx, F^ at interface j (x_{j-1/2}) depends on the six
 // cells j-3 .. j+2 and on the global LF speed alpha = max_i(|u_i| + c_i).  For a cotangent
 // lambda of L the interface cotangent is Fbar_j = (lambda_j - lambda_{j-1})/dx (lambda outside
-// the grid is 0).  The interface kernel recomputes the forward quantities of each interface
-// and sweeps them backwards, writing the cotangents of its six stencil cells' split fluxes
-// (and of its Roe-average inputs) to a buffer; a gather kernel then sums, for every cell, the
-// contributions of the stencil positions that map to it (ghost cells included) in a fixed
-// order and applies the cell's own derivatives once, so the result is deterministic.  alpha
-// is differentiated through its argmax cell (the lowest index on ties); d|x|/dx is taken as
-// 0 at x = 0.
+// the grid is 0).  Each interface's forward quantities are recomputed and swept backwards,
+// giving the cotangents of its six stencil cells' split fluxes (and, for Euler, of its
+// Roe-average inputs); every cell then sums the contributions of the stencil positions that
+// map to it (ghost cells included) in a fixed order and applies its own derivatives once, so
+// the result is deterministic.  Advection does the two parts in two kernels with a
+// contribution buffer between them, Euler in one kernel per RK stage (below).  alpha is
+// differentiated through its argmax cell (the lowest index on ties); d|x|/dx is taken as 0
+// at x = 0.
 #include <atomic>
 
 #include "launch.h"
@@ -101,8 +102,10 @@ __host__ __device__ __forceinline__ double zn_vjp(const double* f, double Wb, do
 // shared memory.  For Euler each interface is then handled by three threads, one per
 // characteristic field k (warp k of the block): the Roe state, row k of the left and column
 // k of the right eigenvectors, the projection of the stencil onto field k, both WENO-ZN
-// reconstructions of that field and their reverse sweeps.  The three fields' cotangents of
-// the split fluxes and of the Roe quantities are summed through shared memory.
+// reconstructions of that field and their reverse sweeps.  Each field leaves its projected
+// stencil's cotangents, half its left-eigenvector row and its Roe-quantity cotangents in
+// shared memory; the cotangents of the split fluxes are then the sums over the fields of
+// row m times the projected cotangents, and the Roe quantities' the sums of the fields'.
 //
 // Per interface j and stencil position s = 0..5 (cell j - 3 + s) the results are
 //   (hbar+_{s,m} + hbar-_{s,m}) / 2  and  (hbar+_{s,m} - hbar-_{s,m}) / 2,  m = 0..NV-1,
