@@ -9,23 +9,23 @@
 namespace wz {
 
 // Shared-memory planes of one tile of NC cells: split fluxes h+ and h- (NV planes each),
-// and for the Euler systems sqrt(rho), u_n, H (and u_t in 2D); the default Euler kernels
-// add the differences dh+-_c = h+-_c - h+-_{c+1} along the sweep (NV planes each), the
-// generic ones the cell's |u_n| + c.
+// and for the Euler systems sqrt(rho), u_n, H (and u_t in 2D), the differences
+// dh+-_c = h+-_c - h+-_{c+1} along the sweep (NV planes each) and, in the generic kernels,
+// the cell's |u_n| + c.
 template <int NV>
 struct CellPlanes {
     static constexpr int kPerCell = NV == 1 ? 2 : 2 * NV + (NV == 4 ? 4 : 3);
-    static constexpr int kPerCellGeneric = kPerCell + (NV == 1 ? 0 : 1);   // + |u_n| + c
     static constexpr int kPerCellDefault = kPerCell + (NV == 1 ? 0 : 2 * NV);   // + dh+, dh-
+    static constexpr int kPerCellGeneric = kPerCellDefault + (NV == 1 ? 0 : 1);   // + |u_n| + c
     double* hp;
     double* hm;
     double* sr;
     double* un;
     double* H;
     double* ut;
-    double* sp;          // generic kernels: the cell's |u_n| + c (local LF)
-    double* dp;          // default Euler kernels: dh+ and dh- (same storage as sp)
+    double* dp;          // Euler: dh+ and dh-
     double* dm;
+    double* sp;          // generic kernels: the cell's |u_n| + c (local LF)
     int NC;
     __device__ __forceinline__ CellPlanes(double* base, int nc) : NC(nc) {
         hp = base;
@@ -34,9 +34,9 @@ struct CellPlanes {
         un = sr + nc;
         H = un + nc;
         ut = H + nc;
-        sp = base + kPerCell * nc;
-        dp = sp;
+        dp = base + kPerCell * nc;
         dm = dp + NV * nc;
+        sp = base + kPerCellDefault * nc;
     }
 };
 
@@ -265,7 +265,7 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
 // project F/2 and U/2 of the six cells and split each field k with its speed alpha_k:
 // g+- = l_k.(F/2) +- alpha_k l_k.(U/2), alpha_k = alpha_f[kind of field k] (split 1; kinds
 // 0 u-c, 1 u, 2 u+c) or the largest |u_n| + c of the six cells (split 2).
-template <int NV>
+template <int NV, bool DIFF>
 __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int base, int stride, double gm1,
                                                    double eps4, double kappa, int weights, int split,
                                                    const double* alpha_f, double* Fh) {
@@ -295,24 +295,43 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
     const double hb1 = (0.5 * gm1) * (rc * rc);        // b1 / 2, b1 = (gamma - 1) / c^2
     const double hb2 = hq2 * hb1;                      // b2 / 2, b2 = q^2 b1 / 2
     // left eigenvectors through their shared parts, as in interface_flux
-    auto project = [&](const double* hs, int i, double* g) {
-        const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
-        const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+    auto project = [&](const double* h, double* g) {
+        const double h0 = h[0], h1 = h[1], hE = h[NV - 1];
+        const double W = NV == 4 ? fma(u, h1, fma(v, h[2], -hE)) : fma(u, h1, -hE);
         const double Zh = fma(hb2, h0, -(hb1 * W));          // Z / 2
         const double Bi = fma(u, h0, -h1);                   // 2 c B
         g[0] = fma(hrc, Bi, Zh);
         g[1] = fma(-2.0, Zh, h0);
-        if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+        if (NV == 4) g[2] = fma(-v, h0, h[2]);
         g[NV - 1] = fma(-hrc, Bi, Zh);
     };
-    double gp[5][NV], gm[5][NV];
-    if (split == 0 || split == 3) {
+    auto project_at = [&](const double* planes, int i, double* g) {
+        double h[NV];
 #pragma unroll
-        for (int st = 0; st < 5; ++st) {
-            project(s.hp, base + st * stride, gp[st]);
-            project(s.hm, base + (st + 1) * stride, gm[st]);
+        for (int k = 0; k < NV; ++k) h[k] = planes[k * NC + i];
+        project(h, g);
+    };
+    double gh[NV];
+    if (DIFF) {
+        // splits 0 and 3, split fluxes per cell: the stencil differences and both centre
+        // values projected as in interface_flux (the planes dh+- filled by cell_diffs)
+        double Dp[4][NV], Dm[4][NV], C[NV];
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            project_at(s.dp, base + st * stride, Dp[st]);
+            project_at(s.dm, base + (st + 1) * stride, Dm[st]);
+        }
+        double hc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) hc[k] = s.hp[k * NC + base + 2 * stride] + s.hm[k * NC + base + 3 * stride];
+        project(hc, C);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double fm = zn_flux_w_d(-Dm[3][k], -Dm[2][k], -Dm[1][k], -Dm[0][k], C[k], eps4, kappa, weights);
+            gh[k] = zn_flux_w_d(Dp[0][k], Dp[1][k], Dp[2][k], Dp[3][k], fm, eps4, kappa, weights);
         }
     } else {
+        double gp[5][NV], gm[5][NV];
         double ak[NV];
         if (split == 2) {
             double a = s.sp[base];
@@ -326,23 +345,32 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
             if (NV == 4) ak[2] = alpha_f[1];
             ak[NV - 1] = alpha_f[2];
         }
+        auto project_planes = [&](const double* hs, int i, double* g) {
+            const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
+            const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
+            const double Zh = fma(hb2, h0, -(hb1 * W));
+            const double Bi = fma(u, h0, -h1);
+            g[0] = fma(hrc, Bi, Zh);
+            g[1] = fma(-2.0, Zh, h0);
+            if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
+            g[NV - 1] = fma(-hrc, Bi, Zh);
+        };
 #pragma unroll
         for (int st = 0; st < 6; ++st) {
             double gF[NV], gU[NV];
-            project(s.hp, base + st * stride, gF);
-            project(s.hm, base + st * stride, gU);
+            project_planes(s.hp, base + st * stride, gF);
+            project_planes(s.hm, base + st * stride, gU);
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 if (st <= 4) gp[st][k] = fma(ak[k], gU[k], gF[k]);
                 if (st >= 1) gm[st - 1][k] = fma(-ak[k], gU[k], gF[k]);
             }
         }
-    }
-    double gh[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, kappa, weights) +
-                zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, kappa, weights);
+        for (int k = 0; k < NV; ++k)
+            gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, kappa, weights) +
+                    zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, kappa, weights);
+    }
     const double uc = u * c;
     if (NV == 3) {
         const double d20 = gh[2] - gh[0];

@@ -1,6 +1,8 @@
 // Interface-flux kernels: global Lax-Friedrichs splitting, Roe-averaged characteristic
 // projection and WENO-ZN reconstruction of both split parts, one thread per interface.
-// The generic instantiations (GEN) take the weight function and the flux splitting at run
+// The generic instantiations (GEN = 1: splittings that project the cell split fluxes, global
+// LF and Steger-Warming; GEN = 2: those that split per field after the projection, per-field
+// and local LF) take the weight function and the flux splitting at run
 // time (WENO-Z / linear / Jiang-Shu weights; per-field LF, local LF, Steger-Warming); the
 // default scheme keeps its own instantiations.
 //
@@ -30,7 +32,7 @@ template <> struct Tile<3, 0, true> { static constexpr int TI = 64, TA = 1, THRE
 template <> struct Tile<4, 0, false> { static constexpr int TI = 128, TA = 4, THREADS = 256; };
 template <> struct Tile<4, 1, false> { static constexpr int TI = 32, TA = 16, THREADS = 256; };
 
-template <int NV, int DIR, bool SMALL, bool GEN>
+template <int NV, int DIR, bool SMALL, int GEN>
 __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(FluxArgs a) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int kThreads = Tile<NV, DIR, SMALL>::THREADS;
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     const double alpha = NV == 1 ? fabs(a.adv_speed) : __longlong_as_double((long long)a.alpha_bits[DIR]);
     const double gm1 = a.gamma - 1.0;
     double alpha_f[3] = {0.0, 0.0, 0.0};           // per-field speeds of this direction
-    if (GEN && NV > 1 && a.split == 1)
+    if (GEN == 2 && NV > 1 && a.split == 1)
         for (int k = 0; k < 3; ++k) alpha_f[k] = __longlong_as_double((long long)a.alpha_f_bits[DIR * 3 + k]);
 
     // ---- per-cell quantities -------------------------------------------------------
@@ -78,11 +80,11 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
             Uc[NV - 1] = a.U[(NV - 1) * nc + cell];
             if (a.bc == 2 && ghost_mirrored(gi, n, a.bc)) Uc[1] = -Uc[1];   // wall mirror image
         }
-        if (GEN) split_cell_gen<NV>(Uc, a.split, alpha, a.adv_speed, a.gamma, sp, sidx(l, lc));
+        if (GEN != 0) split_cell_gen<NV>(Uc, a.split, alpha, a.adv_speed, a.gamma, sp, sidx(l, lc));
         else split_cell<NV>(Uc, alpha, a.adv_speed, gm1, sp, sidx(l, lc));
     }
     __syncthreads();
-    if (!GEN && NV > 1) {
+    if (NV > 1 && GEN != 2) {
         // the split-flux differences of neighbouring cells along the sweep
         for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
             const int l = DIR == 0 ? idx / CL : idx % TA;
@@ -100,9 +102,9 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         const int j = j0 + jl, line = l0 + l;
         if (j >= nint || line >= nlines) continue;
         double Fh[NV];
-        if (GEN)
-            interface_flux_gen<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.weights,
-                                   a.split, alpha_f, Fh);
+        if (GEN != 0)
+            interface_flux_gen<NV, GEN == 1>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, a.weights,
+                                             a.split, alpha_f, Fh);
         else
             interface_flux<NV>(sp, sidx(l, jl), kStride, gm1, a.eps4, a.kappa, Fh);
         // store, undoing the direction frame
@@ -122,12 +124,12 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
     }
 }
 
-template <int NV, int DIR, bool SMALL, bool GEN>
+template <int NV, int DIR, bool SMALL, int GEN>
 cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int NC = (TI + 5) * TA;
     constexpr size_t smem =
-        size_t(NC) * (GEN ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCellDefault) * sizeof(double);
+        size_t(NC) * (GEN != 0 ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCellDefault) * sizeof(double);
     // the dynamic shared-memory limit is a per-device function attribute
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;
@@ -158,7 +160,7 @@ int sm_count_cached() {
     return sms > 0 ? sms : 152;
 }
 
-template <bool GEN>
+template <int GEN>
 cudaError_t launch_flux_t(int system, int dir, const FluxArgs& a, cudaStream_t s) {
     if (system != 2) {
         // 1D: short lines take the small tiles so that every SM has work
@@ -173,8 +175,10 @@ cudaError_t launch_flux_t(int system, int dir, const FluxArgs& a, cudaStream_t s
 }  // namespace
 
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s) {
-    const bool generic = a.weights != 0 || (system != 0 && a.split != 0);
-    return generic ? launch_flux_t<true>(system, dir, a, s) : launch_flux_t<false>(system, dir, a, s);
+    if (a.weights == 0 && (system == 0 || a.split == 0)) return launch_flux_t<0>(system, dir, a, s);
+    // advection ignores the splitting
+    const bool diff = system == 0 || a.split == 0 || a.split == 3;
+    return diff ? launch_flux_t<1>(system, dir, a, s) : launch_flux_t<2>(system, dir, a, s);
 }
 
 }  // namespace wz

@@ -244,14 +244,19 @@ __device__ __forceinline__ double zn_split_flux(double p0, double p1, double p2,
     return zn_flux(p0, p1, p2, p3, p4, eps4, kappa) + zn_flux(m4, m3, m2, m1, m0, eps4, kappa);
 }
 
-__host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
-                                                     double eps4, double kappa, int weights) {
-    const double D1 = a - b, D2 = b - c, D3 = c - d, D4 = d - e;
+// zn_flux_d with the weight function chosen at run time
+__host__ __device__ __forceinline__ double zn_flux_w_d(double D1, double D2, double D3, double D4, double base,
+                                                       double eps4, double kappa, int weights) {
     double num, den;
     zn_num_den_w(D1, D2, D3, D4, eps4, kappa, weights, num, den);
     if (zn_out_of_range(num, den, D1, D2, D3, D4))
-        return c + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, weights);
-    return fma(num, rcp_nr(den), c);
+        return base + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, weights);
+    return fma(num, rcp_nr(den), base);
+}
+
+__host__ __device__ __forceinline__ double zn_flux_w(double a, double b, double c, double d, double e,
+                                                     double eps4, double kappa, int weights) {
+    return zn_flux_w_d(a - b, b - c, c - d, d - e, c, eps4, kappa, weights);
 }
 
 // ------------------------------------------------------------------------------------
