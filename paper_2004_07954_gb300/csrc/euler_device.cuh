@@ -261,10 +261,11 @@ __device__ __forceinline__ void interface_flux(const CellPlanes<NV>& s, int base
 }
 
 // The interface flux of the generic kernels: weights and splitting chosen at run time.
-// Splits 0 and 3 project the cell split fluxes h+- (5 + 5 stencil points); splits 1 and 2
-// project F/2 and U/2 of the six cells and split each field k with its speed alpha_k:
-// g+- = l_k.(F/2) +- alpha_k l_k.(U/2), alpha_k = alpha_f[kind of field k] (split 1; kinds
-// 0 u-c, 1 u, 2 u+c) or the largest |u_n| + c of the six cells (split 2).
+// Splits 0 and 3 (DIFF) project the cell split fluxes h+- (their differences and centres);
+// splits 1 and 2 project F/2 and U/2 of the six cells (their differences and centres) and
+// split each field k with its speed alpha_k: g+- = l_k.(F/2) +- alpha_k l_k.(U/2),
+// alpha_k = alpha_f[kind of field k] (split 1; kinds 0 u-c, 1 u, 2 u+c) or the largest
+// |u_n| + c of the six cells (split 2).  The planes dh+- must be filled (cell_diffs).
 template <int NV, bool DIFF>
 __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int base, int stride, double gm1,
                                                    double eps4, double kappa, int weights, int split,
@@ -331,7 +332,10 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
             gh[k] = zn_flux_w_d(Dp[0][k], Dp[1][k], Dp[2][k], Dp[3][k], fm, eps4, kappa, weights);
         }
     } else {
-        double gp[5][NV], gm[5][NV];
+        // splits 1 and 2: hp = F/2 and hm = U/2 per cell, each field split with its speed after
+        // the projection, g+-_c = l.F_c/2 +- a_k l.U_c/2; differences g+-_c - g+-_{c+1} =
+        // l.dF_c/2 +- a_k l.dU_c/2 (dh+- of cells 0..4), both centres at once as
+        // l.(F_2 + F_3)/2 + a_k l.(U_2 - U_3)/2
         double ak[NV];
         if (split == 2) {
             double a = s.sp[base];
@@ -345,31 +349,36 @@ __device__ __forceinline__ void interface_flux_gen(const CellPlanes<NV>& s, int 
             if (NV == 4) ak[2] = alpha_f[1];
             ak[NV - 1] = alpha_f[2];
         }
-        auto project_planes = [&](const double* hs, int i, double* g) {
-            const double h0 = hs[i], h1 = hs[NC + i], hE = hs[(NV - 1) * NC + i];
-            const double W = NV == 4 ? fma(u, h1, fma(v, hs[2 * NC + i], -hE)) : fma(u, h1, -hE);
-            const double Zh = fma(hb2, h0, -(hb1 * W));
-            const double Bi = fma(u, h0, -h1);
-            g[0] = fma(hrc, Bi, Zh);
-            g[1] = fma(-2.0, Zh, h0);
-            if (NV == 4) g[2] = fma(-v, h0, hs[2 * NC + i]);
-            g[NV - 1] = fma(-hrc, Bi, Zh);
-        };
+        // plus side D_s = g+_{s-1} - g+_s (cells 0..3 of dh), minus side the mirrored
+        // D_s = -(g-_{5-s} - g-_{6-s}) (cells 4..1), combined as each point is projected
+        double Dp[4][NV], Dm[4][NV], cF[NV], cU[NV];
 #pragma unroll
-        for (int st = 0; st < 6; ++st) {
+        for (int st = 0; st < 5; ++st) {
             double gF[NV], gU[NV];
-            project_planes(s.hp, base + st * stride, gF);
-            project_planes(s.hm, base + st * stride, gU);
+            project_at(s.dp, base + st * stride, gF);
+            project_at(s.dm, base + st * stride, gU);
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                if (st <= 4) gp[st][k] = fma(ak[k], gU[k], gF[k]);
-                if (st >= 1) gm[st - 1][k] = fma(-ak[k], gU[k], gF[k]);
+                if (st <= 3) Dp[st][k] = fma(ak[k], gU[k], gF[k]);
+                if (st >= 1) Dm[st - 1][k] = fma(ak[k], gU[k], -gF[k]);
             }
         }
+        {
+            double hf[NV], hu[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            gh[k] = zn_flux_w(gp[0][k], gp[1][k], gp[2][k], gp[3][k], gp[4][k], eps4, kappa, weights) +
-                    zn_flux_w(gm[4][k], gm[3][k], gm[2][k], gm[1][k], gm[0][k], eps4, kappa, weights);
+            for (int k = 0; k < NV; ++k) {
+                hf[k] = s.hp[k * NC + base + 2 * stride] + s.hp[k * NC + base + 3 * stride];
+                hu[k] = s.hm[k * NC + base + 2 * stride] - s.hm[k * NC + base + 3 * stride];
+            }
+            project(hf, cF);
+            project(hu, cU);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double C = fma(ak[k], cU[k], cF[k]);
+            const double fm = zn_flux_w_d(Dm[3][k], Dm[2][k], Dm[1][k], Dm[0][k], C, eps4, kappa, weights);
+            gh[k] = zn_flux_w_d(Dp[0][k], Dp[1][k], Dp[2][k], Dp[3][k], fm, eps4, kappa, weights);
+        }
     }
     const double uc = u * c;
     if (NV == 3) {

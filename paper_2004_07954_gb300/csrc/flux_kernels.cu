@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
         else split_cell<NV>(Uc, alpha, a.adv_speed, gm1, sp, sidx(l, lc));
     }
     __syncthreads();
-    if (NV > 1 && GEN != 2) {
+    if (NV > 1) {
         // the split-flux differences of neighbouring cells along the sweep
         for (int idx = threadIdx.x; idx < NC; idx += kThreads) {
             const int l = DIR == 0 ? idx / CL : idx % TA;
