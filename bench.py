@@ -98,7 +98,9 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-euler1d", action="store_true")
     ap.add_argument("--no-euler2d-1024", action="store_true")
-    ap.add_argument("--only", choices=["batched", "adjoint", "variants", "euler1d", "euler2d_1024"], default=None,
+    ap.add_argument("--no-reconstruct", action="store_true")
+    ap.add_argument("--only", choices=["batched", "adjoint", "variants", "euler1d", "euler2d_1024", "reconstruct"],
+                    default=None,
                     help="run only this part and print its object (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the baseline sample")
     return ap.parse_args()
@@ -118,6 +120,7 @@ OPS_2D = {  # (weights, split): per-unit counts, 2D Euler
 }
 OPS_1D_CELL_UPDATE = 2448.0     # 1D Euler, default scheme, per cell-update (large grid)
 OPS_1D = (755.0, 32.0, 11.0, 6.0)   # 1D Euler: interface, cell per sweep, LF speed, difference
+RECON_FLOPS = 85.0                   # one WENO-ZN reconstruction f^_{i+1/2} (wenozn_reconstruct, per point)
 
 
 def algorithmic_flops(nx: int, ny: int, weights: int = 0, split: int = 0) -> dict:
@@ -292,6 +295,36 @@ def bench_euler1d(wenozn, inputs, seed: int, n: int = 1 << 20, K: int = 100) -> 
             "flux_kernel": {"kernel": "flux_kernel<3,0> (507-interface tiles)", "ms": round(flux_ms, 4),
                             "frac": round(flux_flops / (flux_ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "device_status": status}
+
+
+def bench_reconstruct(wenozn, seed: int, n: int = 1 << 27, reps: int = 10) -> dict:
+    """The reconstruction entry point alone (wenozn_reconstruct) on n points of seeded data
+    with jumps (larger than L2: 1 GiB in, 1 GiB out at 2^27): both sides, CUDA events."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    f = torch.rand(n + 6, dtype=torch.float64, device="cuda", generator=g)
+    f += torch.floor(torch.linspace(0.0, 64.0, n + 6, dtype=torch.float64, device="cuda"))   # 64 steps
+    out = {}
+    for side in (1, -1):
+        fhat = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+        wenozn.wenozn_reconstruct(f, fhat, side)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            wenozn.wenozn_reconstruct(f, fhat, side)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        pts = (n + 1) / (ms / 1e3)
+        hbm, _ = hbm_peak()
+        out["plus" if side > 0 else "minus"] = {
+            "ms": round(ms, 4), "points_per_s": pts,
+            "fp64_frac": round(RECON_FLOPS * pts / 1e9 / FP64_PEAK_GFLOPS, 4),
+            "hbm_frac": round(16.0 * pts / 1e9 / hbm, 4) if hbm else None}
+        del fhat
+    return {"workload": f"wenozn_reconstruct on {n} points of seeded uniform data with 64 unit jumps, eps 1e-40, A 10",
+            "bound": "FP64 pipe (85 algorithmic flops against 16 bytes per point)", **out}
 
 
 def bench_euler2d(wenozn, inputs, seed: int, n: int, K: int, reps: int = 5) -> dict:
@@ -572,6 +605,8 @@ def main():
             part = bench_euler1d(wenozn, inputs, args.seed + rank)
         elif args.only == "euler2d_1024":
             part = bench_euler2d(wenozn, inputs, args.seed + rank, 1024, 100)
+        elif args.only == "reconstruct":
+            part = bench_reconstruct(wenozn, args.seed + rank)
         else:
             part = bench_adjoint(wenozn, inputs, args.seed + rank, steps=args.adjoint_steps,
                                  fd_dirs=args.adjoint_fd_dirs)
@@ -708,6 +743,7 @@ def main():
     batched = part(args.no_batched, bench_batched, wenozn, inputs, args.seed + rank, args.batched_steps)
     euler1d = part(args.no_euler1d, bench_euler1d, wenozn, inputs, args.seed + rank)
     euler2d_1024 = part(args.no_euler2d_1024, bench_euler2d, wenozn, inputs, args.seed + rank, 1024, 100)
+    reconstruct = part(args.no_reconstruct, bench_reconstruct, wenozn, args.seed + rank)
     variants = part(args.no_variants, bench_variants, wenozn, inputs, args.seed + rank, n)
     adjoint = part(args.no_adjoint, bench_adjoint, wenozn, inputs, args.seed + rank,
                    steps=args.adjoint_steps, fd_dirs=args.adjoint_fd_dirs)
@@ -726,7 +762,7 @@ def main():
                            "parallelism": f"{world} independent replica(s), one per GPU",
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "euler2d_1024": euler2d_1024, "variants": variants, "adjoint": adjoint,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "euler2d_1024": euler2d_1024, "reconstruct": reconstruct, "variants": variants, "adjoint": adjoint,
                 "gpu_launches": 9 * args.steps + 1, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -245,6 +245,40 @@ __global__ void __launch_bounds__(kThreads) abs_speed_kernel(double adv_speed, u
     }
 }
 
+// WENO-ZN weights, a tile of kThreads interfaces a block: the first differences
+// D_i = f_i - f_{i+1} and the second-difference part of the indicators,
+// S_i = (13/3)(D_i - D_{i+1})^2 + 4 eps, are shared by neighbouring interfaces (sub-stencil k of
+// interface j covers f_{j+k} .. f_{j+k+2}, mirrored for the minus side), so each is formed once
+// per point in shared memory; the one-sided parts of the indicators differ between the
+// sub-stencils and stay per interface.  The minus side's mirrored stencil has the negated
+// differences in reverse order.
+__global__ void __launch_bounds__(kThreads) reconstruct_zn_kernel(const double* f, int64_t n, double* fhat,
+                                                                   int side, double eps4, double kappa) {
+    __shared__ double sf[kThreads + 5], sD[kThreads + 4], sS[kThreads + 3];
+    const int64_t j0 = blockIdx.x * int64_t(kThreads);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < kThreads + 5; t += kThreads) {
+        const int64_t g = j0 + t;
+        sf[t] = g < n + 6 ? f[g] : 0.0;
+    }
+    __syncthreads();
+    for (int t = tid; t < kThreads + 4; t += kThreads) sD[t] = sf[t] - sf[t + 1];
+    __syncthreads();
+    const double k13_3 = 13.0 / 3.0;
+    for (int t = tid; t < kThreads + 3; t += kThreads) {
+        const double s2 = sD[t] - sD[t + 1];
+        sS[t] = fma(k13_3 * s2, s2, eps4);
+    }
+    __syncthreads();
+    const int64_t j = j0 + tid;
+    if (j > n) return;
+    const int i = tid;
+    fhat[j] = side > 0 ? zn_flux_ds(sD[i], sD[i + 1], sD[i + 2], sD[i + 3], sS[i], sS[i + 1], sS[i + 2], sf[i + 2],
+                                    eps4, kappa)
+                       : zn_flux_ds<true>(sD[i + 4], sD[i + 3], sD[i + 2], sD[i + 1], sS[i + 3], sS[i + 2],
+                                          sS[i + 1], sf[i + 3], eps4, kappa);   // the mirrored stencil
+}
+
 __global__ void __launch_bounds__(kThreads) reconstruct_kernel(const double* f, int64_t n, double* fhat,
                                                                 int side, double eps4, double kappa,
                                                                 int weights) {
@@ -363,7 +397,10 @@ cudaError_t launch_max_wavespeed(int system, const double* U, int64_t ncells, do
 cudaError_t launch_reconstruct(const double* f_padded, int64_t n, double* fhat, int side,
                                double eps, double A, cudaStream_t s, int weights) {
     const unsigned grid = unsigned((n + 1 + kThreads - 1) / kThreads);
-    reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A), weights);
+    if (weights == 0)
+        reconstruct_zn_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A));
+    else
+        reconstruct_kernel<<<grid, kThreads, 0, s>>>(f_padded, n, fhat, side, 4.0 * eps, zn_kappa(A), weights);
     return cudaGetLastError();
 }
 

@@ -74,6 +74,10 @@ __host__ __device__ __forceinline__ double rcp_nr(double d) {
 
 // WENO-ZN numerator and denominator of f^ - c from the first differences D1..D4 (the
 // evaluation described above).
+__host__ __device__ __forceinline__ void zn_num_den_tb(double D1, double D2, double D3, double D4, double t0,
+                                                       double t2, double b0, double b1, double b2, double eps4,
+                                                       double kappa, double& num, double& den);
+
 __host__ __device__ __forceinline__ void zn_num_den(double D1, double D2, double D3, double D4, double eps4,
                                                     double kappa, double& num, double& den) {
     // second (s_k) and one-sided (t_k) differences from the first: equal inputs give exact zeros
@@ -83,6 +87,14 @@ __host__ __device__ __forceinline__ void zn_num_den(double D1, double D2, double
     const double b0 = fma(k13_3 * s0, s0, fma(t0, t0, eps4));   // 4 (IS_0 + eps)
     const double b1 = fma(k13_3 * s1, s1, fma(t1, t1, eps4));
     const double b2 = fma(k13_3 * s2, s2, fma(t2, t2, eps4));
+    zn_num_den_tb(D1, D2, D3, D4, t0, t2, b0, b1, b2, eps4, kappa, num, den);
+}
+
+// The same from the scaled indicators b_k = 4 (IS_k + eps) and the one-sided differences
+// t_0, t_2 (callers that share parts of the indicators between neighbouring stencils).
+__host__ __device__ __forceinline__ void zn_num_den_tb(double D1, double D2, double D3, double D4, double t0,
+                                                       double t2, double b0, double b1, double b2, double eps4,
+                                                       double kappa, double& num, double& den) {
     const double d4 = t0 + t2;                                  // a - 4b + 6c - 4d + e
     // non-negative doubles order like their bit patterns: min/max on the integer pipe
 #ifdef __CUDA_ARCH__
@@ -228,6 +240,25 @@ __host__ __device__ __forceinline__ double zn_flux_d(double D1, double D2, doubl
     if (zn_out_of_range(num, den, D1, D2, D3, D4))
         return base + zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, 0);
     return fma(num, rcp_nr(den), base);
+}
+
+// zn_flux_d with the second-difference part of the indicators given, S_k = (13/3) s_k^2 + 4 eps
+// (s_k the second difference of sub-stencil k): b_k = t_k^2 + S_k.  NEG: base - (f^ - c) of
+// the differences D1..D4, which is base + (f^ - c) of the negated differences (f^ - c is odd
+// in them: the numerator changes sign, the denominator and the range guard do not).
+template <bool NEG = false>
+__host__ __device__ __forceinline__ double zn_flux_ds(double D1, double D2, double D3, double D4, double S0,
+                                                      double S1, double S2, double base, double eps4,
+                                                      double kappa) {
+    const double t0 = fma(-3.0, D2, D1), t1 = D2 + D3, t2 = fma(3.0, D3, -D4);
+    double num, den;
+    zn_num_den_tb(D1, D2, D3, D4, t0, t2, fma(t0, t0, S0), fma(t1, t1, S1), fma(t2, t2, S2), eps4, kappa, num,
+                  den);
+    if (zn_out_of_range(num, den, D1, D2, D3, D4)) {
+        const double corr = zn_correction_rescaled(D1, D2, D3, D4, eps4, kappa, 0);
+        return NEG ? base - corr : base + corr;
+    }
+    return fma(NEG ? -num : num, rcp_nr(den), base);
 }
 
 __host__ __device__ __forceinline__ double zn_flux(double a, double b, double c, double d, double e,

@@ -107,6 +107,7 @@ def test_bench_tables_follow_the_derivation():
     assert bench.OPS_2D[(0, 0)] == (interface(4), cell_split(4), speed(4), difference(4), rk3(4))
     assert bench.OPS_1D == (interface(3), cell_split(3), speed(3), difference(3))
     assert bench.OPS_1D_CELL_UPDATE == cell_update(3)
+    assert bench.RECON_FLOPS == reconstruction()
     fl = bench.algorithmic_flops(4096, 4096)
     assert fl["x_flux"] == interface(4) * 4097 * 4096 + cell_split(4) * 4096 * 4096
     assert fl["per_cell_update"] == pytest.approx(cell_update(4), rel=1e-3)    # plus the boundary interfaces
