@@ -48,7 +48,7 @@ def orc_problem(orc, p):
 
 
 # ------------------------------------------------------------------ reconstruction
-@pytest.mark.parametrize("n", [1, 2, 5, 64, 300, 1000, 4099])
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 255, 256, 300, 1000, 4099])
 @pytest.mark.parametrize("side", [1, -1])
 def test_reconstruct_random(wz, orc, n, side):
     g = np.random.default_rng(n * 7 + side)
