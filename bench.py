@@ -40,7 +40,7 @@ FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 # DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
 # profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
 # kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "8f5a2438affbbbd1", "n": 4096, "bytes": 963.2e6, "capture_n": 2560,
+TRAFFIC_CAPTURE = {"sha256_16": "3a2bac444ff487eb", "n": 4096, "bytes": 962.3e6, "capture_n": 2560,
                    "profile": "profiles/flux_kernel_euler2d_2560.md",
                    "fp64_pipe": {"x": 0.891, "y": 0.892}}   # ncu FP64-pipe busy, same capture
 
