@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             double abar = 0.0;
             if (im_in) abar = p == a.lam_slot ? (S.pred[p][0] + S.pred[p][1]) + S.pred[p][2] : S.pred[p][0];
             const double dabar = a.rec_d[a.prec[p]] * abar;
-            if (im_in && p == a.lam_slot && e == 0 && mm == 0)
-                a.rec[a.prec[p] * a.rec_stride + rec_abar(nb)] = abar;      // for the later readers
+            if (im_in && p == a.lam_slot && e == 0 && mm == 0 && im / kOwn == b)
+                a.rec[a.prec[p] * a.rec_stride + rec_abar(nb)] = abar;      // for the later readers (one writer: the owner of im)
             double pa = 1.0, pb = 0.0;
             if (e < 6) {
                 int t = -1;
