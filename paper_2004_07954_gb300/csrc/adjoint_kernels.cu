@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             s[m] = a.U[int64_t(m) * n + src];
             sm.U[m][c] = s[m];
         }
-        const double r = rcp_nr(s[0]);
+        const double rs = rsqrt(s[0]), r = rs * rs;   // 1/sqrt(rho) and 1/rho, as the forward cell phase
         const double u = s[1] * r;
         const double p = gm1 * (s[2] - 0.5 * s[1] * u);
         const double Ep = s[2] + p;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         sm.u[c] = u;
         sm.H[c] = Ep * r;
         sm.Ep[c] = Ep;
-        sm.sq[c] = sqrt(s[0]);
+        sm.sq[c] = s[0] * rs;
         sm.r[c] = r;
         if (g == src && c >= 5 && c < 5 + kOwn) {   // an owned grid cell: is it the LF argmax?
             double sx, sy;
@@ -499,8 +499,9 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         }
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            const double hpb = fma(gp[2], hL[2][m], fma(gp[1], hL[1][m], gp[0] * hL[0][m]));
-            const double hmb = fma(gm[2], hL[2][m], fma(gm[1], hL[1][m], gm[0] * hL[0][m]));
+            // (position 5 has no plus-side point, position 0 no minus-side one)
+            const double hpb = s <= 4 ? fma(gp[2], hL[2][m], fma(gp[1], hL[1][m], gp[0] * hL[0][m])) : 0.0;
+            const double hmb = s >= 1 ? fma(gm[2], hL[2][m], fma(gm[1], hL[1][m], gm[0] * hL[0][m])) : 0.0;
             const double sumF = hpb + hmb, dh = hpb - hmb;
             if (owned) ab = fma(sm.U[m][i + s], dh, ab);
             S.cF[s][m][i] = sumF;
