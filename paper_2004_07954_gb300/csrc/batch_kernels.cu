@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
         }
         const double alpha = bits2d(a.alpha[slot * a.B + b]);
 
-        for (int i = threadIdx.x; i < CL; i += THREADS) {
+        // the cells interfaces c0 .. c0 + ncell use (an instance's last tile may hold fewer)
+        const int cl_used = ncell + 6;
+        for (int i = threadIdx.x; i < cl_used; i += THREADS) {
             const int g = ghost_src(c0 - 3 + i, n, a.bc);
             double Uc[NV];
 #pragma unroll
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(THREADS, 2) batch_stage_kernel(BatchArgs a) {
             split_cell<NV>(Uc, alpha, 0.0, gm1, sp, i);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < CL - 1; i += THREADS) cell_diffs<NV>(sp, i, 1);
+        for (int i = threadIdx.x; i < cl_used - 1; i += THREADS) cell_diffs<NV>(sp, i, 1);
         __syncthreads();
         for (int jl = threadIdx.x; jl <= ncell; jl += THREADS) {     // interfaces c0 .. c0+ncell
             double Fh[NV];
