@@ -489,7 +489,49 @@ def bench_adjoint(wenozn, inputs, seed: int, n: int = 8192, steps: int = 2000, f
     return {"workload": f"1D Euler N={n}, seeded smooth periodic multi-wave state, {steps} SSP-RK3 steps of "
                         f"fixed dt (CFL 0.5 of U0), loss 1/2||rho(T) - rho_target||^2, rho_target from seed+1",
             "forward_s": round(t_fwd, 4), "store_all": res[1], "checkpoint_every_50": res[50],
-            "loss": float(loss.detach()), "fd_check": {"h": h, **checks}}
+            "loss": float(loss.detach()), "fd_check": {"h": h, **checks},
+            "reverse_scaling": adjoint_scaling(wenozn, inputs, seed)}
+
+
+def adjoint_scaling(wenozn, inputs, seed: int, sizes=(8192, 1 << 17, 1 << 20), steps: int = 10) -> list:
+    """Forward and reverse step times on lines of several lengths (the same seeded smooth
+    state, fixed dt): one chained forward call (wenozn_rk3_run), and the reverse of a kept
+    segment (wenozn_rk3_vjp_run); lines of 10240 cells and more take the
+    one-thread-per-interface stage kernel."""
+    import torch
+    out = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_us(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(3):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e3 / steps)
+        return best
+
+    for n in sizes:
+        p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_1D, n, 1, 10.0 / n, 1.0, bc_x=wenozn.WENOZN_BC_PERIODIC)
+        ws = wenozn.vjp_workspace(p)
+        U0 = torch.from_numpy(inputs.adjoint_ic(n, seed)).cuda()
+        dt = 0.5 * wenozn.wenozn_cfl_dt(p, U0, ws)
+        X = torch.empty((steps + 1,) + tuple(U0.shape), dtype=torch.float64, device="cuda")
+        S1, S2 = torch.empty_like(X[:steps]), torch.empty_like(X[:steps])
+        A = torch.empty(3 * steps + 1, dtype=torch.float64, device="cuda")
+        X[0].copy_(U0)
+        wenozn.wenozn_rk3_run_keep(p, X, S1, S2, A, steps, dt, ws)
+        U = U0.clone()
+        fwd = timed_us(lambda: wenozn.wenozn_rk3_run(p, U, steps, ws, dt))
+        lam = torch.ones_like(U0)
+        rev = timed_us(lambda: wenozn.wenozn_rk3_vjp_run(p, X, S1, S2, A, steps, dt, lam.clone(), ws))
+        out.append({"n": n, "forward_step_us": round(fwd, 1), "reverse_step_us": round(rev, 1),
+                    "reverse_over_forward": round(rev / fwd, 2)})
+        del X, S1, S2
+    return out
 
 
 def cpu_baseline(n_full: int, seed: int, target_s: float, steps: int = 1) -> dict:

@@ -118,12 +118,17 @@ constexpr int kTI = 32;                 // interfaces per block (one warp per fi
 constexpr int kCells = kTI + 5;         // their stencil cells
 constexpr int kGather = 64;             // cells per advection gather block
 
+// The Euler stage kernel's tile: TI interfaces and their TI + 5 stencil cells; WIDE: one
+// thread per interface (all three fields), else one per (interface, field).
+template <int TI, bool WIDE>
 struct EulerSmem {
-    double U[3][kCells];
-    double hp[3][kCells], hm[3][kCells];
-    double u[kCells], H[kCells], sq[kCells], r[kCells], Ep[kCells];
-    double red[3][19][kTI];             // per field: cotangents of its projected h+ (5) and h- (5),
-                                        // half its left-eigenvector row (3), 6 Roe scalars
+    static constexpr int NC = TI + 5;
+    double U[3][NC];
+    double hp[3][NC], hm[3][NC];
+    double u[NC], H[NC], sq[NC], r[NC], Ep[NC];
+    double red[WIDE ? 1 : 3][WIDE ? 1 : 19][WIDE ? 1 : TI];   // per field: cotangents of its projected
+                                        // h+ (5) and h- (5), half its left-eigenvector row (3), 6 Roe
+                                        // scalars (the per-field threads' exchange)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -131,7 +136,10 @@ struct EulerSmem {
 // and computes the VJPs of every interface whose stencil or Roe average touches them,
 // j = c0 - 2 .. c0 + kOwn + 2 (kTI of them), so that it can gather its own cells without
 // anything from other blocks; neighbouring blocks both compute the five interfaces they
-// share (5/kOwn more interface work, and no second launch).  What the tile cannot hold
+// share (5/kOwn more interface work, and no second launch).  Two forms: one thread per
+// (interface, characteristic field) with 32-interface tiles, which gives short lines three
+// times the warps, and one thread per interface with 64-interface tiles, which does less
+// work per interface and serves long lines (kWideMinCells).  What the tile cannot hold
 // crosses blocks through global memory:
 //   - the LF-speed cotangent: every interface is owned by one block (j in [c0, c0 + kOwn),
 //     and j = n by the last block), which adds its share sum_s U_s . (hbar+ - hbar-)_s / 2
@@ -155,19 +163,26 @@ struct EulerSmem {
 // and resets the argmax word and the counter.  Every sum has a fixed order, so the result
 // is deterministic and does not depend on which launches complete in place.
 // ---------------------------------------------------------------------------------------
-constexpr int kOwn = kTI - 5;           // cells owned by a block
+constexpr int kOwn = kTI - 5;           // cells owned by a block of the per-field kernel (the most blocks)
 constexpr int kGhostSlot = 6 * 9;       // 6 ghost cells x (flux, LF, Roe) x 3 components
-constexpr int kWin = kTI + 1;           // cotangent window: cells j0 - 1 .. j0 + kTI - 1
 constexpr int kEnt = 7;                 // pending corrections of a record: 6 ghost targets + the argmax
+constexpr int kTIWide = 64;             // interfaces a block of the one-thread-per-interface kernel
+// Lines of at least this many cells take the one-thread-per-interface kernel (fewer FP64
+// instructions: no per-field copies of the Roe state, the fields' cotangents summed in
+// registers, 5 of 64 interfaces computed twice instead of 5 of 32); shorter ones need the
+// per-field kernel's three times as many warps to occupy the GPU.  Measured crossover:
+// 8192 cells 105 (per field) against 154 us per reverse step, 12288 cells 196 against 165.
+constexpr int kWideMinCells = 10240;
 
+template <int TI, bool WIDE>
 struct StageSmem {
-    EulerSmem e;
-    double cF[6][3][kTI], cD[6][3][kTI];   // per position s, component m, interface: flux and LF parts
-    double cR[2][3][kTI];                  // Roe-input cotangents (left cell, right cell)
-    double sF[3][kOwn];                    // gathered flux parts, exchanged between component threads
+    EulerSmem<TI, WIDE> e;
+    double cF[6][3][TI], cD[6][3][TI];     // per position s, component m, interface: flux and LF parts
+    double cR[2][3][TI];                   // Roe-input cotangents (left cell, right cell)
+    double sF[3][TI - 5];                  // gathered flux parts, exchanged between component threads
     double ghost[6][3][3];                 // ghost slots x (flux, LF, Roe) x component
     double red[3];
-    double lamw[3][kWin];                  // the cotangent input on the window, corrections applied
+    double lamw[3][TI + 1];                // the cotangent input on the window, corrections applied
     double pcq[kVjpPend][6][3];            // input records: ghost slots summed over the edge blocks,
     double pds[kVjpPend][3];               //   the argmax cell's speed derivative,
     double pred[kVjpPend][3];              //   per-warp sums of the partials,
@@ -178,6 +193,15 @@ struct StageSmem {
     int cand;                              // the block's lowest LF-argmax candidate cell
     int tgt[6];                            // the cells the ghost slots map to (completion step)
 };
+
+// The per-warp partial sums in warp order, ((w0 + w1) + w2)
+template <int W>
+__device__ __forceinline__ double warp_sum(const double* w) {
+    double v = w[0];
+#pragma unroll
+    for (int q = 1; q < W; ++q) v += w[q];
+    return v;
+}
 
 // Record layout (doubles): partials [nb], ghost slots [3 edge blocks][18], candidates'
 // speed derivatives [nb][3], and abar once a later launch has summed the partials.
@@ -206,9 +230,70 @@ __device__ __forceinline__ double jft_row(int m, double F0, double F1, double F2
     return jft_row_q(m, F0, F1, F2, mom, u, r, E + p, gm1);
 }
 
-__global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
-    __shared__ StageSmem S;
-    EulerSmem& sm = S.e;
+// Row k of the left eigenvectors (L0, L1, L2) and column k of the right ones (1, R1, R2) at
+// the Roe state (u~, H~, c, 1/c, b1 = (gamma-1)/c^2, b2 = u~^2 b1 / 2).
+__device__ __forceinline__ void field_lr(int k, double ut, double Ht, double c, double rc, double b1, double b2,
+                                         double& L0, double& L1, double& L2, double& R1, double& R2) {
+    if (k == 0) {
+        L0 = 0.5 * fma(ut, rc, b2); L1 = -0.5 * fma(b1, ut, rc); L2 = 0.5 * b1;
+        R1 = ut - c; R2 = fma(-ut, c, Ht);
+    } else if (k == 1) {
+        L0 = 1.0 - b2; L1 = b1 * ut; L2 = -b1;
+        R1 = ut; R2 = 0.5 * ut * ut;
+    } else {
+        L0 = 0.5 * fma(-ut, rc, b2); L1 = -0.5 * fma(b1, ut, -rc); L2 = 0.5 * b1;
+        R1 = ut + c; R2 = fma(ut, c, Ht);
+    }
+}
+
+// The reverse of field_lr: from the cotangents of L0..L2 (Lb) and of R1, R2 (Rb1, Rb2), those
+// of b2, b1, 1/c, u~, c and H~ (q[0..5]).
+__device__ __forceinline__ void field_lr_reverse(int k, const double* Lb, double Rb1, double Rb2, double ut, double c,
+                                                 double rc, double b1, double* q) {
+    if (k == 0) {
+        q[0] = 0.5 * Lb[0]; q[1] = 0.5 * fma(-ut, Lb[1], Lb[2]); q[2] = 0.5 * fma(ut, Lb[0], -Lb[1]);
+        q[3] = 0.5 * fma(rc, Lb[0], -b1 * Lb[1]) + fma(-c, Rb2, Rb1); q[4] = fma(-ut, Rb2, -Rb1); q[5] = Rb2;
+    } else if (k == 1) {
+        q[0] = -Lb[0]; q[1] = fma(ut, Lb[1], -Lb[2]); q[2] = 0.0;
+        q[3] = fma(b1, Lb[1], fma(ut, Rb2, Rb1)); q[4] = 0.0; q[5] = 0.0;
+    } else {
+        q[0] = 0.5 * Lb[0]; q[1] = 0.5 * fma(-ut, Lb[1], Lb[2]); q[2] = 0.5 * fma(-ut, Lb[0], Lb[1]);
+        q[3] = -0.5 * fma(rc, Lb[0], b1 * Lb[1]) + fma(c, Rb2, Rb1); q[4] = fma(ut, Rb2, Rb1); q[5] = Rb2;
+    }
+}
+
+// The Roe average reversed to one of its input cells: from the cotangents of b2, b1, 1/c, u~,
+// c, H~ summed over the fields (sc), those of the conserved state of the cell with velocity
+// uc, enthalpy Hc, 1/rho = r, sqrt(rho) = sq and weight w (w_l or w_r):
+// b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2));
+// u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR));
+// u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho.
+__device__ __forceinline__ void roe_reverse_cell(const double* sc, double ut, double Ht, double rc, double b1,
+                                                 double rS, double gm1, double gamma, double w, double uc,
+                                                 double Hc, double r, double sq, double* Ub) {
+    double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
+    utb = fma(b2b * ut, b1, utb);
+    b1b = fma(b2b * 0.5 * ut, ut, b1b);
+    rcb = fma(b1b * 2.0 * gm1, rc, rcb);
+    cb = fma(-rcb * rc, rc, cb);
+    const double cq = cb * gm1 * 0.5 * rc;
+    Htb += cq;
+    utb = fma(-cq, ut, utb);
+    const double ub = utb * w, Hb = Htb * w;
+    const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
+    Ub[0] = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, (0.5 * sqb) * (sq * r)));
+    Ub[1] = r * fma(-gm1 * uc, Hb, ub);
+    Ub[2] = gamma * r * Hb;
+}
+
+template <int TI, bool WIDE>
+__global__ void __launch_bounds__(WIDE ? TI : 3 * TI) vjp_stage_euler(VjpArgs a) {
+    constexpr int kTI = TI, kOwn = TI - 5, kCells = TI + 5, kWin = TI + 1;   // (shadow the per-field values)
+    constexpr int kThreads = WIDE ? TI : 3 * TI, kWarps = kThreads / 32;
+    constexpr int kLw = (3 * kWin + kThreads - 1) / kThreads;   // rounds of the window load
+    constexpr int kCand = WIDE ? kThreads - 1 : 2 * kTI;        // the thread that offers the argmax candidate
+    __shared__ StageSmem<TI, WIDE> S;
+    EulerSmem<TI, WIDE>& sm = S.e;
     pdl_wait();
     const int n = a.n, nb = int(gridDim.x), b = int(blockIdx.x), tid = threadIdx.x;
     const int c0 = b * kOwn, j0 = c0 - 2;        // first owned cell, first interface
@@ -230,10 +315,10 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         tg[q] = ghost_src(q < 3 ? q - 3 : n + q - 3, n, a.bc);
         gwin = gwin || (tg[q] >= lo && tg[q] <= hi);
     }
-    double lw[2];
+    double lw[kLw];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int q = tid + t * 3 * kTI, m = q / kWin, g = w0 + q % kWin;
+    for (int t = 0; t < kLw; ++t) {
+        const int q = tid + t * kThreads, m = q / kWin, g = w0 + q % kWin;
         lw[t] = q < 3 * kWin && g >= 0 && g < n ? a.lam[int64_t(m) * n + g] : 0.0;
     }
     // the input records' argmax words (uniform loads); where the argmax cell lies in the
@@ -264,7 +349,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             if (p == a.lam_slot) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    if (tid + r * 3 * kTI < nb) pv[r] = __ldcg(R + tid + r * 3 * kTI);
+                    if (tid + r * kThreads < nb) pv[r] = __ldcg(R + tid + r * kThreads);
             } else {
                 abc[p] = __ldcg(R + rec_abar(nb));
             }
@@ -272,7 +357,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         }
     }
     __syncthreads();
-    for (int c = tid; c < kCells; c += 3 * kTI) {
+    for (int c = tid; c < kCells; c += kThreads) {
         const int g = j0 - 3 + c;
         const int src = ghost_src(g, n, a.bc);
         double s[3];
@@ -302,14 +387,14 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         }
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int q = tid + t * 3 * kTI;
+    for (int t = 0; t < kLw; ++t) {
+        const int q = tid + t * kThreads;
         if (q < 3 * kWin) S.lamw[q / kWin][q % kWin] = lw[t];
     }
     if (need) {
         // the pending records' inputs: ghost slots summed over the edge blocks, and abar =
         // the partials summed in block order (strided runs, then the warps)
-        const int kw = tid / kTI;
+        const int kw = tid / 32;
 #pragma unroll
         for (int p = 0; p < kVjpPend; ++p) {
             if (a.prec[p] < 0) continue;
@@ -319,9 +404,9 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
                     double v = 0.0;
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        if (tid + r * 3 * kTI < nb) v += pv[r];
+                        if (tid + r * kThreads < nb) v += pv[r];
                     const double* R = a.rec + a.prec[p] * a.rec_stride;
-                    for (int q = tid + 12 * kTI; q < nb; q += 3 * kTI) v += __ldcg(R + q);
+                    for (int q = tid + 4 * kThreads; q < nb; q += kThreads) v += __ldcg(R + q);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                     if ((tid & 31) == 0) S.pred[p][kw] = v;
@@ -335,7 +420,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     __syncthreads();
     // the block's lowest candidate: offered for the global argmax (the lowest index on ties),
     // with d(|u| + c)/dU of its state left in the record (|x|' = 0 at 0)
-    if (tid == 2 * kTI && S.cand < n) {
+    if (tid == kCand && S.cand < n) {
         const int lc = S.cand - j0 + 3;
         atomicMax(&a.ctl[a.rec_out], ~unsigned(S.cand));
         const double rho = sm.U[0][lc], mom = sm.U[1][lc], E = sm.U[2][lc];
@@ -350,7 +435,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         slot[2] = kk * gm1;
     }
 
-    const int k = tid / kTI, i = tid % kTI, j = j0 + i;
+    const int k = WIDE ? 0 : tid / kTI, i = WIDE ? tid : tid % kTI, j = j0 + i;
     // ---- the corrections pending on the inputs (block-uniform branches) ------------------
     if (tid < kVjpPend * kEnt * 3) {
         // entry e of record p, component mm: e < 6 the first ghost slot of a target cell in the
@@ -363,7 +448,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
             const int im = p == 0 ? imp[0] : (p == 1 ? imp[1] : imp[2]);
             const bool im_in = im >= lo && im <= hi;
             double abar = 0.0;
-            if (im_in) abar = p == a.lam_slot ? (S.pred[p][0] + S.pred[p][1]) + S.pred[p][2] : S.pred[p][0];
+            if (im_in) abar = p == a.lam_slot ? warp_sum<kWarps>(S.pred[p]) : S.pred[p][0];
             const double dabar = a.rec_d[a.prec[p]] * abar;
             if (im_in && p == a.lam_slot && e == 0 && mm == 0 && im / kOwn == b)
                 a.rec[a.prec[p] * a.rec_stride + rec_abar(nb)] = abar;      // for the later readers (one writer: the owner of im)
@@ -410,11 +495,10 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     const bool live = j >= 0 && j <= n;
     const bool owned = live && ((j >= c0 && j < c0 + kOwn) || (j == n && b == nb - 1));
     const int cl = i + 2, cr = i + 3;            // cells j-1, j
-    double ut = 0, Ht = 0, c = 0, rc = 0, b1 = 0, wl = 0, wr = 0, rS = 0;
-    double L0 = 0, L1 = 0, L2 = 0, R1 = 0, R2 = 0;
-    double fp[5] = {}, fm[5] = {};
+    double ut = 0, Ht = 0, c = 0, rc = 0, b1 = 0, b2 = 0, wl = 0, wr = 0, rS = 0;
+    double Fb[3] = {0.0, 0.0, 0.0};
     if (live) {
-        // Roe state and row k of L, column k of R (R[0][k] = 1)
+        // Roe state (R[0][k] = 1) and the cotangents of the interface flux
         const double sl = sm.sq[cl], sr = sm.sq[cr];
         rS = rcp_nr(sl + sr);
         wl = sl * rS;
@@ -425,124 +509,154 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
         rc = rsqrt(c2);
         c = c2 * rc;
         b1 = gm1 * rc * rc;
-        const double b2 = 0.5 * ut * ut * b1;
-        if (k == 0) {
-            L0 = 0.5 * fma(ut, rc, b2); L1 = -0.5 * fma(b1, ut, rc); L2 = 0.5 * b1;
-            R1 = ut - c; R2 = fma(-ut, c, Ht);
-        } else if (k == 1) {
-            L0 = 1.0 - b2; L1 = b1 * ut; L2 = -b1;
-            R1 = ut; R2 = 0.5 * ut * ut;
-        } else {
-            L0 = 0.5 * fma(-ut, rc, b2); L1 = -0.5 * fma(b1, ut, -rc); L2 = 0.5 * b1;
-            R1 = ut + c; R2 = fma(ut, c, Ht);
-        }
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
-            fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
-        }
-    }
-    if (live) {
-        double fpb[5], fmb[5];
-        double Fb[3];
+        b2 = 0.5 * ut * ut * b1;
         for (int m = 0; m < 3; ++m) Fb[m] = (S.lamw[m][i + 1] - S.lamw[m][i]) * a.rdx;   // cells j, j - 1
-        const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
-        const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, fpb) +
-                          zn_vjp(fm, ghb, a.eps4, a.kappa, fmb);
-        double Lb[3] = {0, 0, 0};
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            const double gpb = fpb[s], gmb = fmb[4 - s];     // cotangents of the projected h+_s, h-_{s+1}
-#pragma unroll
-            for (int m = 0; m < 3; ++m) Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
-            sm.red[k][s][i] = gpb;
-            sm.red[k][5 + s][i] = gmb;
-        }
-        sm.red[k][10][i] = 0.5 * L0; sm.red[k][11][i] = 0.5 * L1; sm.red[k][12][i] = 0.5 * L2;
-        const double Rb1 = Fb[1] * gh, Rb2 = Fb[2] * gh;
-        double b2b, b1b, rcb, utb, cb, Htb;
-        if (k == 0) {
-            b2b = 0.5 * Lb[0]; b1b = 0.5 * fma(-ut, Lb[1], Lb[2]); rcb = 0.5 * fma(ut, Lb[0], -Lb[1]);
-            utb = 0.5 * fma(rc, Lb[0], -b1 * Lb[1]) + fma(-c, Rb2, Rb1); cb = fma(-ut, Rb2, -Rb1); Htb = Rb2;
-        } else if (k == 1) {
-            b2b = -Lb[0]; b1b = fma(ut, Lb[1], -Lb[2]); rcb = 0.0;
-            utb = fma(b1, Lb[1], fma(ut, Rb2, Rb1)); cb = 0.0; Htb = 0.0;
-        } else {
-            b2b = 0.5 * Lb[0]; b1b = 0.5 * fma(-ut, Lb[1], Lb[2]); rcb = 0.5 * fma(-ut, Lb[0], Lb[1]);
-            utb = -0.5 * fma(rc, Lb[0], b1 * Lb[1]) + fma(c, Rb2, Rb1); cb = fma(ut, Rb2, Rb1); Htb = Rb2;
-        }
-        sm.red[k][13][i] = b2b; sm.red[k][14][i] = b1b; sm.red[k][15][i] = rcb;
-        sm.red[k][16][i] = utb; sm.red[k][17][i] = cb; sm.red[k][18][i] = Htb;
     }
-    __syncthreads();
-    // stencil positions 2k, 2k+1: the cotangents of h+- there, (hbar+ +- hbar-)/2 summed over
-    // the three fields (row m of each field's left eigenvector times its projected cotangent),
-    // and, for an owned interface, its share sum_s U_s . (hbar+ - hbar-)_s / 2 of the
-    // LF-speed cotangent
     double ab = 0.0;
-    double hL[3][3];
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) hL[f][m] = live ? sm.red[f][10 + m][i] : 0.0;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int s = 2 * k + t;
-        double gp[3] = {0.0, 0.0, 0.0}, gm[3] = {0.0, 0.0, 0.0};
+    if constexpr (!WIDE) {
+        // one thread per (interface, field k): the field's projection, both reconstructions
+        // and their reverse; the fields' results meet in shared memory
         if (live) {
-            if (s <= 4)
+            double L0, L1, L2, R1, R2;
+            field_lr(k, ut, Ht, c, rc, b1, b2, L0, L1, L2, R1, R2);
+            double fp[5], fm[5], fpb[5], fmb[5];
 #pragma unroll
-                for (int f = 0; f < 3; ++f) gp[f] = sm.red[f][s][i];
-            if (s >= 1)
+            for (int s = 0; s < 5; ++s) {
+                fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
+                fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
+            }
+            const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
+            const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, fpb) +
+                              zn_vjp(fm, ghb, a.eps4, a.kappa, fmb);
+            double Lb[3] = {0, 0, 0};
 #pragma unroll
-                for (int f = 0; f < 3; ++f) gm[f] = sm.red[f][4 + s][i];
+            for (int s = 0; s < 5; ++s) {
+                const double gpb = fpb[s], gmb = fmb[4 - s];     // cotangents of the projected h+_s, h-_{s+1}
+#pragma unroll
+                for (int m = 0; m < 3; ++m) Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
+                sm.red[k][s][i] = gpb;
+                sm.red[k][5 + s][i] = gmb;
+            }
+            sm.red[k][10][i] = 0.5 * L0; sm.red[k][11][i] = 0.5 * L1; sm.red[k][12][i] = 0.5 * L2;
+            double q[6];
+            field_lr_reverse(k, Lb, Fb[1] * gh, Fb[2] * gh, ut, c, rc, b1, q);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) sm.red[k][13 + t][i] = q[t];
         }
+        __syncthreads();
+        // stencil positions 2k, 2k+1: the cotangents of h+- there, (hbar+ +- hbar-)/2 summed over
+        // the three fields (row m of each field's left eigenvector times its projected cotangent),
+        // and, for an owned interface, its share sum_s U_s . (hbar+ - hbar-)_s / 2 of the
+        // LF-speed cotangent
+        double hL[3][3];
 #pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) hL[f][m] = live ? sm.red[f][10 + m][i] : 0.0;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int s = 2 * k + t;
+            double gp[3] = {0.0, 0.0, 0.0}, gm[3] = {0.0, 0.0, 0.0};
+            if (live) {
+                if (s <= 4)
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) gp[f] = sm.red[f][s][i];
+                if (s >= 1)
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) gm[f] = sm.red[f][4 + s][i];
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                // (position 5 has no plus-side point, position 0 no minus-side one)
+                const double hpb = s <= 4 ? fma(gp[2], hL[2][m], fma(gp[1], hL[1][m], gp[0] * hL[0][m])) : 0.0;
+                const double hmb = s >= 1 ? fma(gm[2], hL[2][m], fma(gm[1], hL[1][m], gm[0] * hL[0][m])) : 0.0;
+                const double sumF = hpb + hmb, dh = hpb - hmb;
+                if (owned) ab = fma(sm.U[m][i + s], dh, ab);
+                S.cF[s][m][i] = sumF;
+                S.cD[s][m][i] = dh;
+            }
+        }
+        if (k > 0) {
+            // the Roe average reversed: warp 1 gives the left cell, warp 2 the right
+            double Ub[3] = {0.0, 0.0, 0.0};
+            if (live) {
+                double sc[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][13 + q][i] + sm.red[1][13 + q][i]) + sm.red[2][13 + q][i];
+                const int cc = k == 1 ? cl : cr;
+                roe_reverse_cell(sc, ut, Ht, rc, b1, rS, gm1, a.gamma, k == 1 ? wl : wr, sm.u[cc], sm.H[cc], sm.r[cc],
+                                 sm.sq[cc], Ub);
+            }
+            for (int m = 0; m < 3; ++m) S.cR[k - 1][m][i] = Ub[m];
+        }
+    } else {
+        // one thread per interface: the three fields in turn, their cotangents summed in
+        // registers in the same order as the per-field threads sum them in shared memory
+        double hpb[5][3], hmb[5][3];           // halved cotangents of h+ at cells i+s, of h- at cells i+s+1
+        double sc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int s = 0; s < 5; ++s)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) hpb[s][m] = hmb[s][m] = 0.0;
+        if (live) {
+#pragma unroll 1
+            for (int kf = 0; kf < 3; ++kf) {
+                double L0, L1, L2, R1, R2;
+                field_lr(kf, ut, Ht, c, rc, b1, b2, L0, L1, L2, R1, R2);
+                double fp[5], fm[5], fpb[5], fmb[5];
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    fp[s] = fma(L2, sm.hp[2][i + s], fma(L1, sm.hp[1][i + s], L0 * sm.hp[0][i + s]));
+                    fm[4 - s] = fma(L2, sm.hm[2][i + s + 1], fma(L1, sm.hm[1][i + s + 1], L0 * sm.hm[0][i + s + 1]));
+                }
+                const double ghb = fma(R2, Fb[2], fma(R1, Fb[1], Fb[0]));
+                const double gh = zn_vjp(fp, ghb, a.eps4, a.kappa, fpb) +
+                                  zn_vjp(fm, ghb, a.eps4, a.kappa, fmb);
+                const double hL[3] = {0.5 * L0, 0.5 * L1, 0.5 * L2};
+                double Lb[3] = {0, 0, 0};
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const double gpb = fpb[s], gmb = fmb[4 - s];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        Lb[m] = fma(gpb, sm.hp[m][i + s], fma(gmb, sm.hm[m][i + s + 1], Lb[m]));
+                        hpb[s][m] = fma(gpb, hL[m], hpb[s][m]);
+                        hmb[s][m] = fma(gmb, hL[m], hmb[s][m]);
+                    }
+                }
+                double q[6];
+                field_lr_reverse(kf, Lb, Fb[1] * gh, Fb[2] * gh, ut, c, rc, b1, q);
+#pragma unroll
+                for (int t = 0; t < 6; ++t) sc[t] += q[t];
+            }
+        }
+        // stencil positions 0..5, as above
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const double hp = s <= 4 ? hpb[s][m] : 0.0, hm = s >= 1 ? hmb[s - 1][m] : 0.0;
+                const double sumF = hp + hm, dh = hp - hm;
+                if (owned) ab = fma(sm.U[m][i + s], dh, ab);
+                S.cF[s][m][i] = sumF;
+                S.cD[s][m][i] = dh;
+            }
+        // the Roe average reversed to both input cells
+        double Ul[3] = {0.0, 0.0, 0.0}, Ur[3] = {0.0, 0.0, 0.0};
+        if (live) {
+            roe_reverse_cell(sc, ut, Ht, rc, b1, rS, gm1, a.gamma, wl, sm.u[cl], sm.H[cl], sm.r[cl], sm.sq[cl], Ul);
+            roe_reverse_cell(sc, ut, Ht, rc, b1, rS, gm1, a.gamma, wr, sm.u[cr], sm.H[cr], sm.r[cr], sm.sq[cr], Ur);
+        }
         for (int m = 0; m < 3; ++m) {
-            // (position 5 has no plus-side point, position 0 no minus-side one)
-            const double hpb = s <= 4 ? fma(gp[2], hL[2][m], fma(gp[1], hL[1][m], gp[0] * hL[0][m])) : 0.0;
-            const double hmb = s >= 1 ? fma(gm[2], hL[2][m], fma(gm[1], hL[1][m], gm[0] * hL[0][m])) : 0.0;
-            const double sumF = hpb + hmb, dh = hpb - hmb;
-            if (owned) ab = fma(sm.U[m][i + s], dh, ab);
-            S.cF[s][m][i] = sumF;
-            S.cD[s][m][i] = dh;
+            S.cR[0][m][i] = Ul[m];
+            S.cR[1][m][i] = Ur[m];
         }
-    }
-    if (k > 0) {
-        // Roe average (warps 1 and 2 both reverse it; 1 gives the left cell, 2 the right):
-        // b2 = u~^2 b1 / 2, b1 = (gamma-1) rc^2, rc = 1/c, c = sqrt((gamma-1)(H~ - u~^2/2))
-        double Ur = 0.0, Um = 0.0, UE = 0.0;
-        if (live) {
-            double sc[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) sc[q] = (sm.red[0][13 + q][i] + sm.red[1][13 + q][i]) + sm.red[2][13 + q][i];
-            double b2b = sc[0], b1b = sc[1], rcb = sc[2], utb = sc[3], cb = sc[4], Htb = sc[5];
-            utb = fma(b2b * ut, b1, utb);
-            b1b = fma(b2b * 0.5 * ut, ut, b1b);
-            rcb = fma(b1b * 2.0 * gm1, rc, rcb);
-            cb = fma(-rcb * rc, rc, cb);
-            const double cq = cb * gm1 * 0.5 * rc;
-            Htb += cq;
-            utb = fma(-cq, ut, utb);
-            // u~ = wl uL + wr uR, H~ likewise, wl = sqrt(rhoL)/(sqrt(rhoL) + sqrt(rhoR))
-            const int cc = k == 1 ? cl : cr;
-            const double w = k == 1 ? wl : wr, uc = sm.u[cc], Hc = sm.H[cc], r = sm.r[cc];
-            const double ub = utb * w, Hb = Htb * w;
-            const double sqb = fma(utb, uc - ut, Htb * (Hc - Ht)) * rS;
-            // u = mom/rho, H = (gamma E - (gamma-1) mom^2/(2 rho))/rho, sqrt(rho)
-            Ur = fma(-uc * r, ub, fma(r * fma(gm1 * 0.5 * uc, uc, -Hc), Hb, (0.5 * sqb) * (sm.sq[cc] * r)));
-            Um = r * fma(-gm1 * uc, Hb, ub);
-            UE = a.gamma * r * Hb;
-        }
-        S.cR[k - 1][0][i] = Ur;
-        S.cR[k - 1][1][i] = Um;
-        S.cR[k - 1][2][i] = UE;
     }
     // deterministic per-block partial of the LF-speed cotangent (sm.red is free again)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ab += __shfl_down_sync(0xffffffffu, ab, o);
     __syncthreads();
-    if (i == 0) S.red[k] = ab;
+    if ((tid & 31) == 0) S.red[tid >> 5] = ab;
     // the ghost contributions of the owned interfaces: slot q <-> cell -3 + q (q < 3) or
     // n + q - 3, summed per part (flux, LF, Roe) and component in a fixed order over the
     // positions s; only the first block and the last two can own such interfaces
@@ -564,7 +678,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     }
     __syncthreads();
     double* Rout = a.rec + a.rec_out * a.rec_stride;
-    if (tid == 0) Rout[b] = (S.red[0] + S.red[1]) + S.red[2];
+    if (tid == 0) Rout[b] = warp_sum<kWarps>(S.red);
     // ... and their share of the cells the ghosts map to, d (J_F^T flux + alpha LF + Roe)
     // with that cell's state: one value per slot and component
     if (edge && tid < 18) {
@@ -577,42 +691,52 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     // the gather of the owned cells: thread (m, lc) sums component m of cell c0 + lc over the
     // positions s of interfaces c0 + lc + 3 - s (fixed order), exchanges the flux parts and
     // applies row m of J_F^T
-    const int m = tid / kOwn, lc = tid % kOwn, cell = c0 + lc;
-    const bool mine = tid < 3 * kOwn && cell < n;
-    double Fs = 0.0, Ds = 0.0, Rs = 0.0;
-    if (mine) {
+    constexpr int kGR = (3 * kOwn + kThreads - 1) / kThreads;   // rounds of the gather
+    double Dsr[kGR], Rsr[kGR];
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            Fs += S.cF[s][m][lc + 5 - s];
-            Ds += S.cD[s][m][lc + 5 - s];
+    for (int r = 0; r < kGR; ++r) {
+        const int t = tid + r * kThreads, m = t / kOwn, lc = t % kOwn, cell = c0 + lc;
+        const bool mine = t < 3 * kOwn && cell < n;
+        double Fs = 0.0, Ds = 0.0, Rs = 0.0;
+        if (mine) {
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+                Fs += S.cF[s][m][lc + 5 - s];
+                Ds += S.cD[s][m][lc + 5 - s];
+            }
+            Rs = S.cR[1][m][lc + 2] + S.cR[0][m][lc + 3];
         }
-        Rs = S.cR[1][m][lc + 2] + S.cR[0][m][lc + 3];
+        if (t < 3 * kOwn) S.sF[m][lc] = Fs;
+        Dsr[r] = Ds;
+        Rsr[r] = Rs;
     }
-    if (tid < 3 * kOwn) S.sF[m][lc] = Fs;
     __syncthreads();
-    if (mine) {
+#pragma unroll
+    for (int r = 0; r < kGR; ++r) {
+        const int t = tid + r * kThreads, m = t / kOwn, lc = t % kOwn, cell = c0 + lc;
+        if (!(t < 3 * kOwn && cell < n)) continue;
         const int cc = lc + 5;
         const double part = jft_row_q(m, S.sF[0][lc], S.sF[1][lc], S.sF[2][lc], sm.U[1][cc], sm.u[cc], sm.r[cc],
                                       sm.Ep[cc], gm1);
-        const double Ub = fma(alpha, Ds, part) + Rs;
+        const double Ub = fma(alpha, Dsr[r], part) + Rsr[r];
         const int64_t idx = int64_t(m) * n + cell;
         double v = a.d * Ub;
         const double* X[3] = {a.X1, a.X2, a.X3};
         const double cx[3] = {a.c1, a.c2, a.c3};
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            if (!X[t]) continue;
+        for (int q = 0; q < 3; ++q) {
+            if (!X[q]) continue;
             double x;
-            if (a.x_slot[t] == -2) {
+            if (a.x_slot[q] == -2) {
                 x = S.lamw[m][lc + 3];                  // the cotangent input, corrected
             } else {
-                x = X[t][idx];
-                const int p = a.x_slot[t];
+                x = X[q][idx];
+                const int p = a.x_slot[q];
                 if (p >= 0)
                     for (int e = 0; e < kEnt; ++e)
                         if (S.pcell[p][e] == cell) x = fma(S.pa[p][e], S.pb[p][e][m], x);
             }
-            v = fma(cx[t], x, v);
+            v = fma(cx[q], x, v);
         }
         a.out[idx] = v;
     }
@@ -631,10 +755,10 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     if (tid >= 32 && tid < 38) S.tgt[tid - 32] = ghost_src(tid < 35 ? tid - 35 : n + tid - 35, n, a.bc);
     double v = 0.0;
 #pragma unroll 4
-    for (int q = tid; q < nb; q += 3 * kTI) v += __ldcg(Rout + q);
+    for (int q = tid; q < nb; q += kThreads) v += __ldcg(Rout + q);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (i == 0) S.red[k] = v;
+    if ((tid & 31) == 0) S.red[tid >> 5] = v;
     if (tid < 18) {
         const double* G = Rout + rec_ghost(nb);             // blocks 0, nb - 2, nb - 1 (where distinct)
         double cq = __ldcg(G + tid);
@@ -651,7 +775,7 @@ __global__ void __launch_bounds__(3 * kTI) vjp_stage_euler(VjpArgs a) {
     __syncthreads();
     // one update per touched cell and component: the first slot of each target cell sums the
     // slots with that target in slot order, plus the LF-speed term if it is also the argmax
-    const double abar = (S.red[0] + S.red[1]) + S.red[2];
+    const double abar = warp_sum<kWarps>(S.red);
     const int im = S.im;
     if (tid < 18) {
         const int q = tid / 3, mm = tid % 3, tgt = S.tgt[q];
@@ -780,10 +904,10 @@ static cudaError_t euler_interface_pad(size_t* pad) {
         e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (e != cudaSuccess) return e;
-        const long budget = long(per_sm) / 2 - long(reserved) - long(sizeof(StageSmem)) - 1024;
+        const long budget = long(per_sm) / 2 - long(reserved) - long(sizeof(StageSmem<kTI, false>)) - 1024;
         size_t pd = budget > 0 ? size_t(budget) : 0;
         if (pd > 0) {
-            e = cudaFuncSetAttribute(vjp_stage_euler, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pd));
+            e = cudaFuncSetAttribute(vjp_stage_euler<kTI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(pd));
             if (e != cudaSuccess) return e;
         }
         pads[dev & 63] = pd;
@@ -811,10 +935,13 @@ cudaError_t launch_vjp(int system, const VjpArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = launch_pdl(vjp_gather_advection, dim3(gc), dim3(kGather), 0, s, a);
         return e;
     }
+    if (a.n >= kWideMinCells)
+        return launch_pdl(vjp_stage_euler<kTIWide, true>, dim3(unsigned((a.n + kTIWide - 6) / (kTIWide - 5))),
+                          dim3(kTIWide), 0, s, a);
     size_t pad = 0;
     cudaError_t e = euler_interface_pad(&pad);
     if (e == cudaSuccess)
-        e = launch_pdl(vjp_stage_euler, dim3(unsigned((a.n + kOwn - 1) / kOwn)), dim3(3 * kTI), pad, s, a);
+        e = launch_pdl(vjp_stage_euler<kTI, false>, dim3(unsigned((a.n + kOwn - 1) / kOwn)), dim3(3 * kTI), pad, s, a);
     return e;
 }
 

@@ -57,8 +57,10 @@ def test_rhs_vjp_elementwise_against_oracle_jacobian(wz, orc, system, bc, n):
     assert np.abs(out.cpu().numpy() - want).max() <= 1e-10 * scale
 
 
-@pytest.mark.parametrize("system,n,bc", [(1, 300, 1), (1, 257, 0), (0, 500, 0), (1, 4099, 1)])
+@pytest.mark.parametrize("system,n,bc", [(1, 300, 1), (1, 257, 0), (0, 500, 0), (1, 4099, 1),
+                                         (1, 12289, 0), (1, 65536, 1)])
 def test_rhs_vjp_dot_product(wz, orc, system, n, bc):
+    """(Lines of 10240 cells and more take the one-thread-per-interface stage kernel.)"""
     p, P = _problem(wz, orc, system, n, 10.0 / n, bc)
     U = inputs.euler1d_ic(n, seed=4) if system == 1 else _state(0, n, 4)
     g = np.random.default_rng(2)
@@ -75,11 +77,11 @@ def test_rhs_vjp_dot_product(wz, orc, system, n, bc):
         assert b == pytest.approx(a, rel=1e-10, abs=1e-12 * np.abs(lam).sum() * np.abs(Jv).max())
 
 
-@pytest.mark.parametrize("system,bc", [(1, 0), (1, 1), (0, 0)])
-def test_rk3_step_vjp_dot_product(wz, orc, system, bc):
+@pytest.mark.parametrize("system,bc,n", [(1, 0, 240), (1, 1, 240), (0, 0, 240), (1, 0, 16384), (1, 1, 16384)])
+def test_rk3_step_vjp_dot_product(wz, orc, system, bc, n):
     """One RK3 step of the smooth adjoint workload (no rounding-flat fields, whose exact
-    tangent is noise-driven with eps = 1e-40)."""
-    n = 240
+    tangent is noise-driven with eps = 1e-40); 16384 cells take the one-thread-per-interface
+    stage kernel."""
     p, P = _problem(wz, orc, system, n, 10.0 / n, bc)
     U = inputs.adjoint_ic(n, seed=6) if system == 1 else _state(0, n, 6)
     dt = 0.4 * p.dx / (orc.max_wavespeed(P, U) if system == 1 else 1.0)
@@ -138,10 +140,11 @@ def test_rk3_step_keep_matches_in_place_step(wz, system, bc):
         wz.wenozn_rk3_step_keep(p, U, U, dt, S1, S2, A, ws)
 
 
-def test_chained_keep_and_reverse_equal_the_single_steps(wz):
+@pytest.mark.parametrize("n", [640, 20000])
+def test_chained_keep_and_reverse_equal_the_single_steps(wz, n):
     """wenozn_rk3_run_keep / wenozn_rk3_vjp_run against wenozn_rk3_step_keep /
-    wenozn_rk3_step_vjp_stages step by step, bit for bit."""
-    n, m = 640, 9
+    wenozn_rk3_step_vjp_stages step by step, bit for bit (both forms of the stage kernel)."""
+    m = 9
     p = wz.wenozn_problem_init(1, n, 1, 10.0 / n, 1.0, bc_x=0)
     U0 = dev(inputs.adjoint_ic(n, seed=16))
     dt = 0.3 * p.dx
@@ -202,16 +205,20 @@ def _wave_speeds(U, gamma=1.4):
     return np.abs(u) + np.sqrt(gamma * (gamma - 1.0) * (E - 0.5 * m * u) / rho)
 
 
-@pytest.mark.parametrize("bc,target", [(1, 0), (1, 199), (1, 26), (1, 27), (1, 29), (0, 1), (0, 198), (0, 54)])
-def test_reverse_with_the_lf_argmax_at_a_correction_target(wz, orc, bc, target):
+@pytest.mark.parametrize("n,bc,target", [(200, 1, 0), (200, 1, 199), (200, 1, 26), (200, 1, 27), (200, 1, 29),
+                                         (200, 0, 1), (200, 0, 198), (200, 0, 54),
+                                         (20000, 1, 0), (20000, 1, 19999), (20000, 1, 58), (20000, 1, 59),
+                                         (20000, 0, 1), (20000, 0, 19998), (20000, 0, 118)])
+def test_reverse_with_the_lf_argmax_at_a_correction_target(wz, orc, n, bc, target):
     """The LF speed's argmax planted (a one-cell pressure spike that holds it through every
     stage input) at a cell the deferred corrections touch: a ghost-cell target at either
     boundary (outflow: cells 0, n-1; periodic: 0..2, n-3..n-1), or a cell in the windows of
-    two neighbouring blocks (27 owned cells each: 24..29 and 51..56 lie in two).  Two
-    reverse steps in one chained call (six stage launches: every pending slot is read)
-    against the oracle's binary128 forward-mode derivative, and bit for bit against the
-    step-by-step reverse (each call completing in place)."""
-    n, m = 200, 2
+    two neighbouring blocks (n = 200, per-field kernel, 27 owned cells a block: 24..29 and
+    51..56 lie in two; n = 20000, one-thread-per-interface kernel, 59 owned cells: 56..61 and
+    115..120).  Two reverse steps in one chained call (six stage launches: every pending slot
+    is read) against the oracle's binary128 forward-mode derivative, and bit for bit against
+    the step-by-step reverse (each call completing in place)."""
+    m = 2
     p, P = _problem(wz, orc, 1, n, 10.0 / n, bc)
     W = inputs.adjoint_ic(n, seed=9)
     rho, mom = W[0, 0], W[1, 0]
