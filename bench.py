@@ -37,12 +37,13 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_GFLOPS = 2 * FP64_LANES_PER_SM * SMS * SM_MAX_MHZ / 1e3   # 1258.6
 
-# DRAM bytes (read + write) of one 4096x4096 x-flux launch from the ncu capture summarised in
-# profiles/flux_kernel_euler2d_2560.md (scaled by the interface count), valid only for the
-# kernel sources with this hash prefix; any other source reports null.
-TRAFFIC_CAPTURE = {"sha256_16": "3a2bac444ff487eb", "n": 4096, "bytes": 962.3e6, "capture_n": 2560,
-                   "profile": "profiles/flux_kernel_euler2d_2560.md",
-                   "fp64_pipe": {"x": 0.891, "y": 0.892}}   # ncu FP64-pipe busy, same capture
+# DRAM bytes (read + write) of one 4096x4096 launch of the step's flux kernel (both sweeps of
+# a stage) from the ncu capture summarised in profiles/flux_xy_kernel_euler2d_2560.md (scaled
+# by the interface count), valid only for the kernel sources with this hash prefix; any other
+# source reports null.
+TRAFFIC_CAPTURE = {"sha256_16": "8caed8a5cce072a2", "n": 4096, "bytes": 2040.8e6, "capture_n": 2560,
+                   "profile": "profiles/flux_xy_kernel_euler2d_2560.md",
+                   "fp64_pipe": {"xy": 0.892, "x": 0.891, "y": 0.892}}   # ncu FP64-pipe busy, same captures
 
 
 def hbm_peak() -> tuple:
@@ -329,7 +330,8 @@ def bench_reconstruct(wenozn, seed: int, n: int = 1 << 27, reps: int = 10) -> di
 
 def bench_euler2d(wenozn, inputs, seed: int, n: int, K: int, reps: int = 5) -> dict:
     """The headline workload on an n x n grid: K chained RK3 steps after 3 warm-up steps
-    (CUDA events on the launching stream), and the x-flux kernel alone for its FP64 fraction."""
+    (CUDA events on the launching stream), and the flux kernel of a stage alone (both sweeps
+    in one launch, as the step runs it; and each sweep alone) for its FP64 fraction."""
     import torch
     p = wenozn.wenozn_problem_init(wenozn.WENOZN_EULER_2D, n, n, 1.0 / n, 1.0 / n)
     U = torch.from_numpy(inputs.euler2d_ic(n, n, seed)).cuda()
@@ -346,7 +348,7 @@ def bench_euler2d(wenozn, inputs, seed: int, n: int, K: int, reps: int = 5) -> d
     alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
     wenozn.wenozn_max_wavespeed(p, U, alpha)
     kern = {}
-    for d in (0, 1):
+    for d in (2, 0, 1):
         buf = torch.empty(wenozn.flux_shape(p, d), dtype=torch.float64, device="cuda")
         wenozn.wenozn_flux(p, U, alpha, d, buf)
         torch.cuda.synchronize()
@@ -357,10 +359,12 @@ def bench_euler2d(wenozn, inputs, seed: int, n: int, K: int, reps: int = 5) -> d
         torch.cuda.synchronize()
         kern[d] = e0.elapsed_time(e1) / reps
     fl = algorithmic_flops(n, n)
+    xy = fl["x_flux"] + fl["y_flux"]
     return {"workload": f"2D Euler {n}x{n} seeded four-quadrant Riemann problem (seed {seed}), outflow, "
                         f"CFL 0.5, {K} chained SSP-RK3 steps",
             "metric": "cell-updates/s", "value": n * n / (ms / 1e3), "ms_per_step": round(ms, 4),
             "step_frac": round(fl["step"] / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
+            "xy_flux": {"ms": round(kern[2], 4), "frac": round(xy / (kern[2] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "x_flux": {"ms": round(kern[0], 4), "frac": round(fl["x_flux"] / (kern[0] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "y_flux": {"ms": round(kern[1], 4), "frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4)},
             "device_status": status}
@@ -693,10 +697,11 @@ def main():
     # ---- dominant kernels, timed live on the launching stream ------------------------
     alpha = torch.zeros(2, dtype=torch.float64, device="cuda")
     wenozn.wenozn_max_wavespeed(p, U, alpha)
-    fx = torch.empty(wenozn.flux_shape(p, 0), dtype=torch.float64, device="cuda")
-    fy = torch.empty(wenozn.flux_shape(p, 1), dtype=torch.float64, device="cuda")
+    # the step's flux kernel (both sweeps of a stage in one launch, direction 2), and each
+    # sweep alone for the split
     kern = {}
-    for d, buf in ((0, fx), (1, fy)):
+    for d in (2, 0, 1):
+        buf = torch.empty(wenozn.flux_shape(p, d), dtype=torch.float64, device="cuda")
         wenozn.wenozn_flux(p, U, alpha, d, buf)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -706,9 +711,9 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         kern[d] = a.elapsed_time(b) / args.kernel_reps
-    del fx, fy
+        del buf
     fl = algorithmic_flops(n, n)
-    achieved = fl["x_flux"] / (kern[0] / 1e3) / 1e9
+    achieved = (fl["x_flux"] + fl["y_flux"]) / (kern[2] / 1e3) / 1e9
     # the FP64 rate pure FMA register arithmetic reaches on this GPU, beside the nominal peak
     probe = max(wenozn.wenozn_fp64_fma_rate(1 << 17, stream) for _ in range(3))
     captured = kernel_source_hash() == TRAFFIC_CAPTURE["sha256_16"] and n == TRAFFIC_CAPTURE["n"]
@@ -716,9 +721,10 @@ def main():
     hbm_gbs, hbm_src = hbm_peak()
     roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
-                "kernel": "flux_kernel<4,0> (x-direction interface fluxes)",
+                "kernel": "flux_xy_kernel (a stage's x and y interface fluxes in one launch, as the step runs them)",
                 "peak_source": "derived: 2 FP64 FMA/SM/clk x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s FP64)",
-                "kernel_ms": {"x_flux": round(kern[0], 3), "y_flux": round(kern[1], 3)},
+                "kernel_ms": {"xy_flux": round(kern[2], 3), "x_flux": round(kern[0], 3), "y_flux": round(kern[1], 3)},
+                "x_flux_frac": round(fl["x_flux"] / (kern[0] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
                 "y_flux_frac": round(fl["y_flux"] / (kern[1] / 1e3) / 1e9 / FP64_PEAK_GFLOPS, 4),
                 "step_frac": round(fl["step"] * world * args.steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS / world, 4),
                 "algorithmic_flops_per_cell_update": round(fl["per_cell_update"], 1),
@@ -735,8 +741,8 @@ def main():
                                    "kernel_sources_sha256_16": TRAFFIC_CAPTURE["sha256_16"],
                                    "sources_match": captured},
                 "dram": None if traffic is None else {
-                    "gbs": round(traffic / (kern[0] / 1e3) / 1e9, 1), "peak_gbs": hbm_gbs,
-                    "frac": round(traffic / (kern[0] / 1e3) / 1e9 / hbm_gbs, 5), "peak_source": hbm_src}}
+                    "gbs": round(traffic / (kern[2] / 1e3) / 1e9, 1), "peak_gbs": hbm_gbs,
+                    "frac": round(traffic / (kern[2] / 1e3) / 1e9 / hbm_gbs, 5), "peak_source": hbm_src}}
 
     # ---- end to end: host buffers, copies inside the timed region --------------------
     # One library call (wenozn_rk3_stream_host) takes the K steps' states from pinned host
@@ -805,7 +811,7 @@ def main():
                            "l2": "inputs larger than L2 (512 MiB per state buffer at 4096^2), no flush",
                            "device_status": status},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched, "euler1d": euler1d, "euler2d_1024": euler2d_1024, "reconstruct": reconstruct, "variants": variants, "adjoint": adjoint,
-                "gpu_launches": 9 * args.steps + 1, "clocks": clk}
+                "gpu_launches": 6 * args.steps + 1, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

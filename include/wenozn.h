@@ -164,7 +164,10 @@ wenozn_status wenozn_max_wavespeed(const wenozn_problem* p, const double* U, dou
  *           wenozn_max_wavespeed writes them; ignored for advection, which splits with |a|
  *           (and by the local-LF and Steger-Warming splittings, which need none).
  *   dir   : 0 = x, Fout[nvar][ny][nx+1] with Fout[k][j][i] at x_{i-1/2} of row j;
- *           1 = y (2D only), Fout[nvar][ny+1][nx] with Fout[k][j][i] at y_{j-1/2}.
+ *           1 = y (2D only), Fout[nvar][ny+1][nx] with Fout[k][j][i] at y_{j-1/2};
+ *           2 = both (2D only), in one launch, the form wenozn_rhs and the RK3 steps use:
+ *           the x fluxes as for 0, then the y fluxes as for 1, at
+ *           Fout + nvar * ny * (nx + 1).
  *   Fout  : device, overwritten; must not overlap U. */
 wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double* alpha,
                           int32_t dir, double* Fout, void* stream);

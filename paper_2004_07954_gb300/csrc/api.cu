@@ -137,7 +137,7 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     wenozn_status st = check_problem(p);
     if (st != WENOZN_OK) return st;
     if (!U || !Fout || U == Fout || (p->system != WENOZN_ADVECTION_1D && !alpha)) return WENOZN_EINVAL;
-    if (dir != 0 && !(dir == 1 && p->system == WENOZN_EULER_2D)) return WENOZN_EINVAL;
+    if (dir != 0 && !((dir == 1 || dir == 2) && p->system == WENOZN_EULER_2D)) return WENOZN_EINVAL;
     FluxArgs fa;
     fa.U = U;
     fa.alpha_bits = reinterpret_cast<const unsigned long long*>(alpha);
@@ -152,6 +152,13 @@ wenozn_status wenozn_flux(const wenozn_problem* p, const double* U, const double
     fa.adv_speed = p->adv_speed;
     fa.Fout = Fout;
     fa.bc = dir == 0 ? p->bc_x : p->bc_y;
+    if (dir == 2) {
+        // both sweeps in one launch, as wenozn_rhs and the RK3 steps run them
+        FluxArgs fy = fa;
+        fa.bc = p->bc_x;
+        fy.Fout = Fout + int64_t(4) * p->ny * (int64_t(p->nx) + 1);
+        return cuda_status(launch_flux_xy(fa, fy, static_cast<cudaStream_t>(stream)));
+    }
     return cuda_status(launch_flux(p->system, dir, fa, static_cast<cudaStream_t>(stream)));
 }
 

@@ -32,20 +32,19 @@ template <> struct Tile<3, 0, true> { static constexpr int TI = 64, TA = 1, THRE
 template <> struct Tile<4, 0, false> { static constexpr int TI = 128, TA = 4, THREADS = 256; };
 template <> struct Tile<4, 1, false> { static constexpr int TI = 32, TA = 16, THREADS = 256; };
 
+// One tile of a sweep: tile ta along the sweep direction, tile tc across it.
 template <int NV, int DIR, bool SMALL, int GEN>
-__global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(FluxArgs a) {
+__device__ __forceinline__ void flux_tile(const FluxArgs& a, int ta, int tc, double* smem) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
     constexpr int kThreads = Tile<NV, DIR, SMALL>::THREADS;
     constexpr int CL = TI + 5;            // cells per line in the tile
     constexpr int NC = CL * TA;           // cells per tile
-    extern __shared__ double smem[];
     const CellPlanes<NV> sp(smem, NC);
-    pdl_wait();
 
     const int n = DIR == 0 ? a.nx : a.ny;           // cells along the sweep
     const int nlines = DIR == 0 ? a.ny : a.nx;
-    const int j0 = (DIR == 0 ? blockIdx.x : blockIdx.y) * TI;   // first interface of the tile
-    const int l0 = (DIR == 0 ? blockIdx.y : blockIdx.x) * TA;   // first line of the tile
+    const int j0 = ta * TI;                         // first interface of the tile
+    const int l0 = tc * TA;                         // first line of the tile
     const int64_t nc = int64_t(a.nx) * a.ny;
     // cells this tile's interfaces use along the sweep (the last tile of a line may hold
     // fewer than TI interfaces, e.g. only the boundary interface n)
@@ -125,11 +124,61 @@ __global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(
 }
 
 template <int NV, int DIR, bool SMALL, int GEN>
+__global__ void __launch_bounds__(Tile<NV, DIR, SMALL>::THREADS, 2) flux_kernel(FluxArgs a) {
+    extern __shared__ double smem[];
+    pdl_wait();
+    flux_tile<NV, DIR, SMALL, GEN>(a, DIR == 0 ? blockIdx.x : blockIdx.y, DIR == 0 ? blockIdx.y : blockIdx.x, smem);
+}
+
+// Both sweeps of a 2D stage in one grid, so that they share one tail: blocks [0, nbx) take
+// the x tiles (along the sweep fastest, as flux_kernel<4, 0>), the others the y tiles
+// (across the sweep fastest, as flux_kernel<4, 1>).
+template <int GEN>
+__global__ void __launch_bounds__(256, 2) flux_xy_kernel(FluxArgs ax, FluxArgs ay, int x_along, int nbx, int y_across) {
+    static_assert(Tile<4, 0>::THREADS == 256 && Tile<4, 1>::THREADS == 256, "one block size for both sweeps");
+    extern __shared__ double smem[];
+    pdl_wait();
+    const int b = int(blockIdx.x);
+    if (b < nbx) {
+        flux_tile<4, 0, false, GEN>(ax, b % x_along, b / x_along, smem);
+    } else {
+        const int q = b - nbx;
+        flux_tile<4, 1, false, GEN>(ay, q / y_across, q % y_across, smem);
+    }
+}
+
+template <int NV, int DIR, bool SMALL, int GEN>
+constexpr size_t tile_smem() {
+    return size_t((Tile<NV, DIR, SMALL>::TI + 5) * Tile<NV, DIR, SMALL>::TA) *
+           (GEN != 0 ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCellDefault) * sizeof(double);
+}
+
+template <int GEN>
+cudaError_t launch_xy(const FluxArgs& ax, const FluxArgs& ay, cudaStream_t s) {
+    constexpr size_t sx = tile_smem<4, 0, false, GEN>(), sy = tile_smem<4, 1, false, GEN>();
+    constexpr size_t smem = sx > sy ? sx : sy;
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(flux_xy_kernel<GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(bit);
+    }
+    const int x_along = (ax.nx + 1 + Tile<4, 0>::TI - 1) / Tile<4, 0>::TI;
+    const int nbx = x_along * ((ax.ny + Tile<4, 0>::TA - 1) / Tile<4, 0>::TA);
+    const int y_across = (ay.nx + Tile<4, 1>::TA - 1) / Tile<4, 1>::TA;
+    const int nby = y_across * ((ay.ny + 1 + Tile<4, 1>::TI - 1) / Tile<4, 1>::TI);
+    return launch_pdl(flux_xy_kernel<GEN>, dim3(unsigned(nbx + nby)), dim3(256), smem, s, ax, ay, x_along, nbx,
+                      y_across);
+}
+
+template <int NV, int DIR, bool SMALL, int GEN>
 cudaError_t launch_one(const FluxArgs& a, cudaStream_t s) {
     constexpr int TI = Tile<NV, DIR, SMALL>::TI, TA = Tile<NV, DIR, SMALL>::TA;
-    constexpr int NC = (TI + 5) * TA;
-    constexpr size_t smem =
-        size_t(NC) * (GEN != 0 ? CellPlanes<NV>::kPerCellGeneric : CellPlanes<NV>::kPerCellDefault) * sizeof(double);
+    constexpr size_t smem = tile_smem<NV, DIR, SMALL, GEN>();
     // the dynamic shared-memory limit is a per-device function attribute
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;
@@ -173,6 +222,12 @@ cudaError_t launch_flux_t(int system, int dir, const FluxArgs& a, cudaStream_t s
 }
 
 }  // namespace
+
+cudaError_t launch_flux_xy(const FluxArgs& ax, const FluxArgs& ay, cudaStream_t s) {
+    if (ax.weights == 0 && ax.split == 0) return launch_xy<0>(ax, ay, s);
+    const bool diff = ax.split == 0 || ax.split == 3;
+    return diff ? launch_xy<1>(ax, ay, s) : launch_xy<2>(ax, ay, s);
+}
 
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s) {
     if (a.weights == 0 && (system == 0 || a.split == 0)) return launch_flux_t<0>(system, dir, a, s);

@@ -95,11 +95,11 @@ inline cudaError_t launch_fluxes(const wenozn_problem& p, const double* U, const
                                  cudaStream_t s) {
     FluxArgs fa = flux_args(p, U, alpha_bits, alpha_f_bits);
     fa.Fout = fx;
-    cudaError_t e = launch_flux(p.system, 0, fa, s);
-    if (e != cudaSuccess || p.system != WENOZN_EULER_2D) return e;
-    fa.Fout = gy;
-    fa.bc = p.bc_y;
-    return launch_flux(p.system, 1, fa, s);
+    if (p.system != WENOZN_EULER_2D) return launch_flux(p.system, 0, fa, s);
+    FluxArgs fy = fa;
+    fy.Fout = gy;
+    fy.bc = p.bc_y;
+    return launch_flux_xy(fa, fy, s);
 }
 
 inline UpdateArgs update_args(const wenozn_problem& p, Ctrl* ctrl, const double* fx, const double* gy) {

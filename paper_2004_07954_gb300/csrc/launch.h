@@ -49,6 +49,8 @@ inline bool zn_constants_ok(double eps, double A) {
 // The WENO-ZN weights carry A as kappa = 2 / sqrt(A) (A > 0, checked on entry).
 inline double zn_kappa(double A) { return 2.0 / std::sqrt(A); }
 cudaError_t launch_flux(int system, int dir, const FluxArgs& a, cudaStream_t s);
+// both sweeps of a 2D stage (x fluxes into ax.Fout, y fluxes into ay.Fout) in one launch
+cudaError_t launch_flux_xy(const FluxArgs& ax, const FluxArgs& ay, cudaStream_t s);
 
 // Flux difference, SSP-RK3 stage combination and the next stage's LF speeds.
 struct UpdateArgs {

@@ -231,6 +231,10 @@ def wenozn_flux(p: wenozn_problem, U: torch.Tensor, alpha: torch.Tensor | None, 
 
 
 def flux_shape(p: wenozn_problem, direction: int):
+    """Shape of wenozn_flux's output: one direction's planes, or (direction 2) the x fluxes
+    followed by the y fluxes as one flat array."""
+    if direction == 2:
+        return (p.nvar * (p.ny * (p.nx + 1) + (p.ny + 1) * p.nx),)
     return (p.nvar, p.ny, p.nx + 1) if direction == 0 else (p.nvar, p.ny + 1, p.nx)
 
 

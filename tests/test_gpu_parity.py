@@ -181,6 +181,29 @@ def test_rhs_parity(wz, orc, system, nx, ny, bc):
     assert S.status() == 0
 
 
+@pytest.mark.parametrize("nx,ny,bc", [(37, 21, 1), (70, 130, 0), (129, 64, 1), (256, 33, 0)])
+def test_flux_sweeps_and_both_in_one_launch(wz, orc, nx, ny, bc):
+    """wenozn_flux: the x sweep, the y sweep and both in one launch (the form the RHS and the
+    RK3 steps run) give the same interface fluxes bit for bit, and their differences are the
+    oracle's right-hand side."""
+    U = _rand_state(2, nx, ny, seed=nx + 2 * ny)
+    p = gpu_problem(wz, 2, nx, ny, dx=1.0 / nx, dy=1.0 / ny, bc=bc)
+    t = dev(U)
+    a = torch.zeros(2, dtype=torch.float64, device="cuda")
+    wz.wenozn_max_wavespeed(p, t, a)
+    out = [torch.empty(wz.flux_shape(p, d), dtype=torch.float64, device="cuda") for d in (0, 1, 2)]
+    for d in (0, 1, 2):
+        wz.wenozn_flux(p, t, a, d, out[d])
+    X, Y, both = (host(o) for o in out)
+    assert np.array_equal(both[:X.size].reshape(X.shape), X)
+    assert np.array_equal(both[X.size:].reshape(Y.shape), Y)
+    L = -(X[:, :, 1:] - X[:, :, :-1]) * nx - (Y[:, 1:, :] - Y[:, :-1, :]) * ny
+    assert rel_linf(L, orc.rhs(orc_problem(orc, p), U)) <= STEP_TOL
+    with pytest.raises(wz.WenoznError):
+        p1 = gpu_problem(wz, 1, nx)
+        wz.wenozn_flux(p1, dev(_rand_state(1, nx, 1, seed=1)), a, 2, out[2])
+
+
 # ------------------------------------------------------------------ one RK3 step
 @pytest.mark.parametrize("system,nx,ny,bc", RHS_CASES)
 def test_rk3_step_parity(wz, orc, system, nx, ny, bc):
