@@ -131,6 +131,28 @@ def test_newer_entry_points_reject_bad_arguments_on_host(wz):
     assert L.wenozn_fp64_fma_rate(1 << 10, None, None) == wz.WENOZN_EINVAL
 
 
+def test_flux_directions_checked_on_host(wz):
+    """wenozn_flux: direction 0 for every system, 1 and 2 (both sweeps in one launch) for 2D
+    Euler only, a speed array required except for advection; flux_shape gives the layout of
+    each direction (direction 2: the x fluxes then the y fluxes, one flat array)."""
+    L = wz.lib()
+    A, B = ctypes.c_void_p(256), ctypes.c_void_p(1 << 20)
+    p0 = wz.wenozn_problem_init(wz.WENOZN_ADVECTION_1D, 64, 1, 0.1, 0)
+    p1 = wz.wenozn_problem_init(wz.WENOZN_EULER_1D, 64, 1, 0.1, 0)
+    p2 = wz.wenozn_problem_init(wz.WENOZN_EULER_2D, 16, 12, 0.1, 0.1)
+    for p in (p0, p1):
+        for d in (1, 2, -1, 3):
+            assert L.wenozn_flux(ctypes.byref(p), A, A, d, B, None) == wz.WENOZN_EINVAL
+    for d in (-1, 3):
+        assert L.wenozn_flux(ctypes.byref(p2), A, A, d, B, None) == wz.WENOZN_EINVAL
+    assert L.wenozn_flux(ctypes.byref(p2), A, None, 2, B, None) == wz.WENOZN_EINVAL     # no speeds
+    assert L.wenozn_flux(ctypes.byref(p2), A, A, 2, A, None) == wz.WENOZN_EINVAL        # Fout == U
+    assert L.wenozn_flux(ctypes.byref(p2), A, A, 2, None, None) == wz.WENOZN_EINVAL
+    assert wz.flux_shape(p2, 0) == (4, 12, 17)
+    assert wz.flux_shape(p2, 1) == (4, 13, 16)
+    assert wz.flux_shape(p2, 2) == (4 * 12 * 17 + 4 * 13 * 16,)
+
+
 def test_status_strings_and_version(wz):
     for code in range(6):
         assert wz.wenozn_status_string(code)
